@@ -1,0 +1,167 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) WENO5 / Lax-Friedrichs / SSP-RK3 solver of the 2D Euler
+ * equations with a level-set flame scalar.
+ *
+ * The method is the hydrodynamics update of Leung, Chu & Lin (2015), "A new hydrodynamics code for
+ * Type Ia supernovae": the conservative Euler equations in (r,z) with geometric and gravity source
+ * terms (Sec. 2.1, Eq. euler2D), finite-difference WENO reconstruction of fluxes split by a global
+ * Lax-Friedrichs splitting (Sec. 2.1), the three-stage third-order SSP Runge-Kutta scheme named there
+ * as the original prescription (Sec. 2.1), the CFL time step dt = c_cfl Delta / (c_s + |v_r| + |v_z|)
+ * (Sec. 5.4), and the level-set scalar S advected by v + v_flame (Sec. 2.2).
+ *
+ * Conventions shared by every entry point
+ *   - State arrays are structure-of-arrays U[f][j][i] with i (x, or r) contiguous: nfields planes
+ *     of ny rows of nx values, dtype float (HYDRO_F32) or double (HYDRO_F64). Fields:
+ *     0 rho, 1 rho*u (rho v_r), 2 rho*v (rho v_z), 3 total energy density tau, 4 level set phi.
+ *     Values are point values at cell centres x_i = x0 + (i + 1/2) dx, y_j = y0 + (j + 1/2) dy.
+ *   - Pointers named U / lambda are DEVICE pointers owned by the caller unless the name says host.
+ *     The library owns only its context and the scratch it allocates in hydro_init (three padded
+ *     working states, reduction slots, logs) and frees in hydro_destroy.
+ *   - All device work runs on the context's stream, asynchronously, except calls that return host
+ *     values (time, dt, totals, status), which synchronise that stream.
+ *   - Return codes: HYDRO_OK (0) or a negative HYDRO_E* code; nothing aborts. hydro_last_error gives
+ *     the context's message for the last failure.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_ctx hydro_ctx;
+
+typedef enum { HYDRO_F32 = 0, HYDRO_F64 = 1 } hydro_dtype;
+
+/* Boundary kinds (Sec. 2.1 and the code tests of Sec. 5): periodic; transmissive (outflow, zero
+ * gradient); reflecting wall (mirror, normal momentum reversed); symmetry axis r = 0 of an (r,z)
+ * grid (same mirror rule, x-lo face only). Ghost images of phi are even mirrors. */
+typedef enum {
+  HYDRO_BC_PERIODIC = 0,
+  HYDRO_BC_TRANSMISSIVE = 1,
+  HYDRO_BC_REFLECT = 2,
+  HYDRO_BC_AXIS = 3
+} hydro_bc;
+
+enum {
+  HYDRO_OK = 0,
+  HYDRO_EINVAL = -1,        /* bad argument: null pointer, size, bc pair, dtype, nfields        */
+  HYDRO_ECUDA = -2,         /* a CUDA call failed (message in hydro_last_error)                 */
+  HYDRO_ENONPHYSICAL = -3,  /* the device saw a non-finite value, rho <= 0 or p <= 0             */
+  HYDRO_ETIMEOUT = -4,      /* a device wait or a host wait on the stream exceeded its limit     */
+  HYDRO_ESTATE = -5         /* call out of order (e.g. adjoint sweep without a recorded run)     */
+};
+
+typedef struct {
+  int nx, ny;               /* interior cells, >= 3 each                                         */
+  double x0, x1, y0, y1;    /* domain; with geometry 1, x is r and x0 >= 0                        */
+  double gamma;             /* ideal gas p = (gamma - 1) rho eps, gamma > 1                       */
+  double cfl;               /* Courant number c_cfl > 0                                          */
+  int geometry;             /* 0 Cartesian (x, y); 1 axisymmetric (r, z): adds -(1/r) sources     */
+  double gravity_y;         /* constant acceleration along y (z); sources (0,0,rho g, m_y g)      */
+  int bc[4];                /* hydro_bc of faces x-lo, x-hi, y-lo, y-hi                           */
+  int nfields;              /* 4 (hydro) or 5 (hydro + level set phi)                             */
+  double flame_speed;       /* burning speed s_f of the level-set front (phi > 0 ash)             */
+  int dtype;                /* hydro_dtype                                                       */
+} hydro_config;
+
+/* Create a context for one grid: validates cfg (HYDRO_EINVAL on a bad field, an unpaired periodic
+ * face or an axis face that is not x-lo of an (r,z) grid with x0 = 0), allocates the padded working
+ * states and scratch on the current device, and binds the CUDA stream (cudaStream_t, NULL = legacy
+ * default stream). *out receives the context; on failure *out is NULL. */
+int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out);
+
+/* Release the context and all of its device memory (synchronises its stream). NULL is ignored. */
+void hydro_destroy(hydro_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). Valid until the next call on ctx. */
+const char* hydro_last_error(hydro_ctx* ctx);
+
+/* Rebind the context to another stream. */
+int hydro_set_stream(hydro_ctx* ctx, void* stream);
+
+/* Advance U (device, [nfields][ny][nx], caller-owned) by nsteps SSP-RK3 steps in place (Sec. 2.1).
+ * Each step takes dt from the CFL condition on U^n (Sec. 5.4) and the global Lax-Friedrichs speeds
+ * alpha_x = max(|u| + c), alpha_y = max(|v| + c) from each stage's input. *t_inout (may be NULL) is
+ * advanced by the sum of the steps' dt, accumulated in FP64 on the device; *dt_last (may be NULL)
+ * receives the last dt. Returns HYDRO_ENONPHYSICAL if any stage produced a non-finite value,
+ * rho <= 0 or p <= 0 (U then holds the state of the failing step). Synchronises the stream. */
+int hydro_step(hydro_ctx* ctx, void* U, int nsteps, double* t_inout, double* dt_last);
+
+/* Same as hydro_step for a state in HOST memory (pageable or pinned): copies it to the device,
+ * steps, and copies it back, all on the context's stream. */
+int hydro_step_host(hydro_ctx* ctx, void* U_host, int nsteps, double* t_inout, double* dt_last);
+
+/* Spatial operator L(U) = -(dF/dx + dG/dy) + S(U) and the level-set right-hand side -H_hat, with the
+ * Lax-Friedrichs speeds given (not computed): L is a device array shaped like U. Asynchronous. */
+int hydro_rhs(hydro_ctx* ctx, const void* U, double alpha_x, double alpha_y, void* L);
+
+/* Conserved totals sum_cells U_f dV (f = 0..4; dV = dx dy, or 2 pi r_i dr dz in (r,z)) of a device
+ * state, accumulated in FP64 in a fixed order (bitwise repeatable). out[4] is 0 when nfields = 4.
+ * Synchronises the stream. */
+int conserved_totals(hydro_ctx* ctx, const void* U, double out[5]);
+
+/* Totals of the state written by the last completed hydro_step / hydro_batch_step, accumulated by
+ * the last stage kernel of each step (FP64; atomics, so the last bits may vary between runs). */
+int hydro_last_totals(hydro_ctx* ctx, double out[5]);
+
+/* ---- recording and the discrete adjoint (frozen alpha and dt) ---------------------------------
+ * alpha_x, alpha_y and dt are maxima/minima over the grid and have no derivative; the adjoint and the
+ * finite-difference checks freeze them at the values the forward run used. */
+
+/* Start recording: the next steps log dt (one double per step) and the stage alphas (six doubles per
+ * step) for up to max_steps steps. max_steps = 0 stops recording and frees the log. */
+int hydro_record(hydro_ctx* ctx, int max_steps);
+/* Copy the first n logged entries to host arrays dt_log[n], alpha_log[6n]. Returns the number of
+ * steps recorded so far through *n_recorded (may be NULL). */
+int hydro_get_log(hydro_ctx* ctx, int n, double* dt_log, double* alpha_log, int* n_recorded);
+
+/* Forward map with dt and stage alphas frozen at host-given values (nsteps entries / 6*nsteps). */
+int hydro_step_frozen(hydro_ctx* ctx, void* U, int nsteps, const double* dt_log, const double* alpha_log);
+
+/* Discrete adjoint of one frozen SSP-RK3 step: lambda (device, shaped like U) holds dJ/dU^{n+1} on
+ * entry and dJ/dU^n on exit; U_n is the step's input state; alpha holds (alpha_x, alpha_y) of the
+ * three stages. The stage states are recomputed from U_n. */
+int hydro_adjoint_step(hydro_ctx* ctx, const void* U_n, void* lambda, double dt, const double alpha[6]);
+
+/* Forward run of nsteps steps from U (device, advanced in place to U^N) keeping checkpoints for a
+ * later reverse sweep: every checkpoint_every-th state is stored in library memory (checkpoint_every
+ * <= 0 picks sqrt(nsteps)), and dt / alphas are recorded. */
+int hydro_forward_checkpointed(hydro_ctx* ctx, void* U, int nsteps, int checkpoint_every);
+/* Reverse sweep over the last checkpointed forward run: lambda holds dJ/dU^N on entry and dJ/dU^0 on
+ * exit. Segments are recomputed from their checkpoints (two-level checkpointing); the stored run is
+ * kept, so the sweep may be repeated for another lambda. */
+int hydro_adjoint_sweep(hydro_ctx* ctx, void* lambda);
+
+/* ---- batched ensembles ------------------------------------------------------------------------ */
+
+/* Advance nmembers independent grids (each with its own context, all of one dtype and nfields) by
+ * nsteps steps: each RK stage of all members is ONE persistent kernel launch that walks a table of
+ * (member, tile) work items; the three launches of a step are replayed from a CUDA graph. U[m] is
+ * member m's device state, t[m] (host, may be NULL) its time. Runs on members[0]'s stream. */
+int hydro_batch_step(hydro_ctx* const* members, void* const* U, int nmembers, int nsteps, double* t);
+
+/* ---- tuning and timing ----------------------------------------------------------------------- */
+
+/* Number of tile variants and the current one; select a variant (0 .. n-1) for this context. */
+int hydro_tile_variants(hydro_ctx* ctx, int* n, int* current);
+int hydro_set_tile_variant(hydro_ctx* ctx, int variant);
+/* Describe a variant: tile width and height in cells, threads per CTA, shared memory bytes. */
+int hydro_tile_info(hydro_ctx* ctx, int variant, int* tile_x, int* tile_y, int* threads, int* smem_bytes);
+/* Time every variant on a copy of U (device; U is not modified) for `steps` steps each and keep the
+ * fastest; per-variant milliseconds per step go to ms_out[n] (may be NULL). */
+int hydro_autotune(hydro_ctx* ctx, const void* U, int steps, double* ms_out);
+
+/* Per-launch timing of the stage kernels: with enable = 1, every stage launch is bracketed by CUDA
+ * events on the context's stream; hydro_stage_timing returns the launches and the summed device time
+ * since the last enable (synchronises the stream). */
+int hydro_profile(hydro_ctx* ctx, int enable);
+int hydro_stage_timing(hydro_ctx* ctx, int* launches, double* total_ms);
+
+/* Number of kernel launches the library issued on this context since it was created. */
+long long hydro_launch_count(hydro_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDRO_H */

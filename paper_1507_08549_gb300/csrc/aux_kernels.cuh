@@ -1,0 +1,119 @@
+// aux_kernels.cuh -- small kernels around the stage kernel: packing a caller state into the padded
+// working layout (with ghost images and the first stage's reductions), frozen-slot writes, and the
+// FP64 conserved totals (Leung, Chu & Lin 2015: totals of mass and energy as in the Gresho test table
+// of Sec. 5.2).
+#pragma once
+#include "stage_kernel.cuh"
+
+namespace hydro {
+
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, GridParams<real> g,
+                                                   real* alpha_slot, real* smax_slot, double* t_acc, double t0) {
+  using T = RT<real>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && t_acc) *t_acc = t0;
+  real amx = real(0), amy = real(0), smx = real(0);
+  if (i < g.nx) {
+    const long long n = static_cast<long long>(g.nx) * g.ny;
+    const long long k = static_cast<long long>(j) * g.nx + i;
+    real val[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) val[f] = U[f * n + k];
+    const long long off = static_cast<long long>(j + GY) * g.pitch + i + GX;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) g.out[f * g.fstride + off] = val[f];
+    if (i < 3 || i >= g.nx - 3 || j < 3 || j >= g.ny - 3)
+      write_ghost_images<real, NF>(g.out, g.fstride, g.pitch, g.nx, g.ny, g.bc, i, j, val);
+    const real rho = val[0], mx = val[1], my = val[2], E = val[3];
+    const real rr = T::rcp(rho);
+    const real u = mx * rr, v = my * rr;
+    const real p = g.gm1 * T::fma_(real(-0.5), T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
+    const real cs = T::sqrt_(g.gamma * p * rr);
+    bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) && T::finite(cs);
+    if (NF == 5) ok = ok && T::finite(val[NF - 1]);
+    if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
+    amx = fabs(u) + cs;
+    amy = fabs(v) + cs;
+    smx = T::add_(cs, T::add_(fabs(u), fabs(v)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    amx = fmax(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+    amy = fmax(amy, __shfl_xor_sync(0xffffffffu, amy, o));
+    smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (alpha_slot) {
+      T::atomic_max(&alpha_slot[0], amx);
+      T::atomic_max(&alpha_slot[1], amy);
+    }
+    if (smax_slot) T::atomic_max(smax_slot, smx);
+  }
+}
+
+template <typename real>
+__global__ void set_frozen_kernel(double* dt_slot, double dt, real* alpha_slots, double a0, double a1, double a2,
+                                  double a3, double a4, double a5) {
+  if (threadIdx.x == 0) {
+    if (dt_slot) *dt_slot = dt;
+    if (alpha_slots) {
+      alpha_slots[0] = static_cast<real>(a0);
+      alpha_slots[1] = static_cast<real>(a1);
+      alpha_slots[2] = static_cast<real>(a2);
+      alpha_slots[3] = static_cast<real>(a3);
+      alpha_slots[4] = static_cast<real>(a4);
+      alpha_slots[5] = static_cast<real>(a5);
+    }
+  }
+}
+
+// Per-thread FP64 sums over a grid-stride range, then a fixed-shape tree: the result depends only on
+// the launch shape, which the host keeps fixed per device.
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) totals_partial_kernel(const real* __restrict__ U, int nx, int ny, int geometry,
+                                                             double x0, double dx, double dy,
+                                                             double* __restrict__ partials) {
+  const long long n = static_cast<long long>(nx) * ny;
+  double acc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) acc[f] = 0.0;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+    double dV = dx * dy;
+    if (geometry == 1) {
+      const int i = static_cast<int>(k % nx);
+      dV = 6.283185307179586 * (x0 + (i + 0.5) * dx) * dx * dy;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f] = fma(static_cast<double>(U[f * n + k]), dV, acc[f]);
+  }
+  __shared__ double sred[8][NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sred[warp][f] = acc[f];
+  __syncthreads();
+  if (threadIdx.x < NF) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sred[w][threadIdx.x];
+    partials[blockIdx.x * 5 + threadIdx.x] = s;
+  }
+}
+
+static __global__ void totals_final_kernel(const double* __restrict__ partials, int nblocks, int nf, double* out) {
+  const int f = threadIdx.x;
+  if (f < 5) {
+    double s = 0.0;
+    if (f < nf)
+      for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + f];
+    out[f] = s;
+  }
+}
+
+}  // namespace hydro

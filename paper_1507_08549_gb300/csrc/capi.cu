@@ -1,0 +1,856 @@
+// capi.cu -- host runtime behind the C ABI of include/hydro.h: contexts, the padded working states,
+// the SSP-RK3 step loop (Leung, Chu & Lin 2015, Sec. 2.1) with CFL time steps (Sec. 5.4), CUDA-graph
+// replay of a step's three stage launches, batched ensembles, the tile autotuner, totals, recording
+// and the bounded host waits. All device work is issued on the context's stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "hydro_internal.cuh"
+
+using namespace hydro;
+
+namespace {
+
+template <typename real>
+struct Scratch {
+  real alpha[3][2];         // rotating (alpha_x, alpha_y) slots: stage k reads k, writes k+1, clears k+2
+  real smax;                // CFL signal speed of U^n
+  real frozen_alpha[3][2];  // frozen runs
+  real pad;
+  double dt_cur, t_acc, frozen_dt;
+  double totals[5];
+  int err;
+  int log_count;  // kept across calls while recording (not cleared with the rest)
+};
+
+double host_timeout_s() {
+  const char* e = std::getenv("HYDRO_TIMEOUT_S");
+  double v = e ? std::atof(e) : 0.0;
+  return v > 0.0 ? v : 3600.0;
+}
+
+}  // namespace
+
+struct hydro_ctx {
+  hydro_config cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+  int device = 0, num_sms = 0;
+  int nf = 4;
+  size_t esize = 4;
+  int variant = 1;
+  // padded layout (sized for the tallest tile variant so every variant fits)
+  int pitch = 0, rows = 0, tiles_x = 0, tiles_y = 0;
+  long long fstride = 0;
+  void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
+  void* scratch = nullptr;
+  void* params = nullptr;  // device GridParams[7]: normal stages 0..2, frozen stages 3..5, rhs 6
+  void* host_scratch = nullptr;  // pinned copy of Scratch
+  double* partials = nullptr;
+  int partial_blocks = 0;
+  double* d_totals = nullptr;
+  void* unpadded = nullptr;  // caller-layout device buffer (host entry, rhs output)
+  // recording
+  double* dt_log = nullptr;
+  double* alpha_log = nullptr;
+  int log_cap = 0;
+  bool track_totals = true;
+  // graph of one step
+  cudaGraphExec_t step_graph = nullptr;
+  // per-launch profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  cudaEvent_t done = nullptr;
+  long long launches = 0;
+  // batch plan (kept on the first member)
+  std::vector<hydro_ctx*> plan_members;
+  int plan_variant = -1;
+  void* plan_params = nullptr;  // device GridParams[3][nmembers]
+  void* plan_work = nullptr;    // device WorkItem[nwork]
+  int plan_nwork = 0;
+  cudaGraphExec_t plan_graph = nullptr;
+  std::string err;
+};
+
+// ------------------------------------------------------------------------------------ helpers
+
+static int fail(hydro_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int cuda_fail(hydro_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, HYDRO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+static int validate_config(const hydro_config* g, std::string* why) {
+  if (!g) { *why = "null config"; return HYDRO_EINVAL; }
+  if (g->nx < 3 || g->ny < 3) { *why = "nx and ny must be >= 3"; return HYDRO_EINVAL; }
+  if (g->nfields != 4 && g->nfields != 5) { *why = "nfields must be 4 or 5"; return HYDRO_EINVAL; }
+  if (g->dtype != HYDRO_F32 && g->dtype != HYDRO_F64) { *why = "dtype must be HYDRO_F32 or HYDRO_F64"; return HYDRO_EINVAL; }
+  if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) { *why = "empty domain"; return HYDRO_EINVAL; }
+  if (!(g->gamma > 1.0) || !(g->cfl > 0.0)) { *why = "gamma must be > 1 and cfl > 0"; return HYDRO_EINVAL; }
+  if (g->geometry != 0 && g->geometry != 1) { *why = "geometry must be 0 or 1"; return HYDRO_EINVAL; }
+  for (int k = 0; k < 4; ++k)
+    if (g->bc[k] < HYDRO_BC_PERIODIC || g->bc[k] > HYDRO_BC_AXIS) { *why = "unknown boundary kind"; return HYDRO_EINVAL; }
+  if ((g->bc[0] == HYDRO_BC_PERIODIC) != (g->bc[1] == HYDRO_BC_PERIODIC) ||
+      (g->bc[2] == HYDRO_BC_PERIODIC) != (g->bc[3] == HYDRO_BC_PERIODIC)) {
+    *why = "periodic faces must come in pairs";
+    return HYDRO_EINVAL;
+  }
+  if (g->bc[1] == HYDRO_BC_AXIS || g->bc[2] == HYDRO_BC_AXIS || g->bc[3] == HYDRO_BC_AXIS ||
+      (g->bc[0] == HYDRO_BC_AXIS && (g->geometry != 1 || g->x0 != 0.0))) {
+    *why = "the axis boundary is the x-lo (r = 0) face of an (r,z) grid";
+    return HYDRO_EINVAL;
+  }
+  if (g->geometry == 1 && g->x0 < 0.0) { *why = "(r,z) grids need r >= 0"; return HYDRO_EINVAL; }
+  if (!std::isfinite(g->gravity_y) || !std::isfinite(g->flame_speed) || g->flame_speed < 0.0) {
+    *why = "gravity and flame speed must be finite, flame speed >= 0";
+    return HYDRO_EINVAL;
+  }
+  return HYDRO_OK;
+}
+
+template <typename real>
+static Scratch<real>* scr(hydro_ctx* c) {
+  return static_cast<Scratch<real>*>(c->scratch);
+}
+
+template <typename real>
+static real* bufp(hydro_ctx* c, int k) {
+  return static_cast<real*>(c->buf[k]);
+}
+
+static int tile_ty(int variant) { return VARIANTS[variant].ty; }
+
+// Stage parameters of this context for the current variant.
+template <typename real>
+static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
+  const hydro_config& g = c->cfg;
+  Scratch<real>* s = scr<real>(c);
+  GridParams<real> base{};
+  base.fstride = c->fstride;
+  base.nx = g.nx;
+  base.ny = g.ny;
+  base.pitch = c->pitch;
+  base.tiles_x = c->tiles_x;
+  base.tiles_y = (g.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant);
+  for (int k = 0; k < 4; ++k) base.bc[k] = g.bc[k];
+  base.geometry = g.geometry;
+  base.gamma = static_cast<real>(g.gamma);
+  base.gm1 = static_cast<real>(g.gamma - 1.0);
+  base.gravity = static_cast<real>(g.gravity_y);
+  base.flame_speed = static_cast<real>(g.flame_speed);
+  base.dx = (g.x1 - g.x0) / g.nx;
+  base.dy = (g.y1 - g.y0) / g.ny;
+  base.rdx = static_cast<real>(1.0 / base.dx);
+  base.rdy = static_cast<real>(1.0 / base.dy);
+  base.x0 = g.x0;
+  base.cfl_delta = g.cfl * std::min(base.dx, base.dy);
+  base.smax = &s->smax;
+  base.dt_cur = &s->dt_cur;
+  base.t_acc = &s->t_acc;
+  base.err = &s->err;
+  real* A = bufp<real>(c, 0);
+  real* B = bufp<real>(c, 1);
+  real* C = bufp<real>(c, 2);
+  const real* win[3] = {A, B, C};
+  real* outp[3] = {B, C, A};
+  for (int k = 0; k < 3; ++k) {
+    GridParams<real> p = base;
+    p.win = win[k];
+    p.un = A;
+    p.out = outp[k];
+    p.alpha_in = s->alpha[k];
+    p.alpha_out = s->alpha[(k + 1) % 3];
+    p.alpha_zero = s->alpha[(k + 2) % 3];
+    if (c->log_cap > 0) {
+      p.dt_log = c->dt_log;
+      p.alpha_log = c->alpha_log;
+      p.log_count = &s->log_count;
+      p.log_cap = c->log_cap;
+    }
+    if (k == 2 && c->track_totals) p.totals = s->totals;
+    if (k == 1 && c->track_totals) p.totals_reset = s->totals;
+    out[k] = p;
+    GridParams<real> f = p;  // frozen: alphas and dt from the frozen slots
+    f.alpha_in = s->frozen_alpha[k];
+    f.dt_src = (k == 0) ? &s->frozen_dt : nullptr;
+    f.dt_log = nullptr;
+    f.alpha_log = nullptr;
+    f.log_count = nullptr;
+    f.log_cap = 0;
+    out[3 + k] = f;
+  }
+  GridParams<real> r = base;  // L(W) of buffer A into buffer B
+  r.win = A;
+  r.un = A;
+  r.out = B;
+  r.alpha_in = s->frozen_alpha[0];
+  r.dt_src = &s->frozen_dt;
+  out[6] = r;
+}
+
+template <typename real>
+static int upload_params(hydro_ctx* c) {
+  GridParams<real> p[7];
+  build_params<real>(c, p);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
+  if (c->step_graph) {
+    cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+  }
+  return HYDRO_OK;
+}
+
+static int upload(hydro_ctx* c) {
+  return c->cfg.dtype == HYDRO_F64 ? upload_params<double>(c) : upload_params<float>(c);
+}
+
+static int grid_for(hydro_ctx* c, int nwork) {
+  int occ = c->cfg.dtype == HYDRO_F64 ? stage_ctas_per_sm<double>(c->variant, c->nf)
+                                      : stage_ctas_per_sm<float>(c->variant, c->nf);
+  if (occ < 1) occ = 1;
+  return std::max(1, std::min(nwork, occ * c->num_sms));
+}
+
+static int wait_stream(hydro_ctx* c) {
+  cudaError_t e = cudaEventRecord(c->done, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  const double limit = host_timeout_s();
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    e = cudaEventQuery(c->done);
+    if (e == cudaSuccess) return HYDRO_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(c, e, "stream wait");
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return fail(c, HYDRO_ETIMEOUT, "stream did not finish within HYDRO_TIMEOUT_S");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+  }
+}
+
+template <typename real>
+static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double b, cudaStream_t s) {
+  StageCtl ctl{stage, mode, a, b};
+  const int nwork = c->tiles_x * ((c->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
+  const GridParams<real>* p = static_cast<const GridParams<real>*>(c->params) + k;
+  const bool prof = c->profiling && s == c->stream;
+  if (prof) {
+    while ((int)c->ev.size() < c->ev_used + 2) {
+      cudaEvent_t ev;
+      CK(cudaEventCreate(&ev));
+      c->ev.push_back(ev);
+    }
+    CK(cudaEventRecord(c->ev[c->ev_used], s));
+  }
+  CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), s));
+  if (prof) {
+    CK(cudaEventRecord(c->ev[c->ev_used + 1], s));
+    c->ev_used += 2;
+  }
+  c->launches++;
+  return HYDRO_OK;
+}
+
+static const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+static const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+template <typename real>
+static int launch_step(hydro_ctx* c, bool frozen, cudaStream_t s) {
+  for (int k = 0; k < 3; ++k) {
+    int rc = launch_one<real>(c, frozen ? 3 + k : k, k, 0, RK_A[k], RK_B[k], s);
+    if (rc) return rc;
+  }
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int ensure_graph(hydro_ctx* c) {
+  if (c->step_graph) return HYDRO_OK;
+  cudaGraph_t gr = nullptr;
+  CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+  int rc = launch_step<real>(c, false, c->capture);
+  cudaError_t e = cudaStreamEndCapture(c->capture, &gr);
+  if (rc) {
+    if (gr) cudaGraphDestroy(gr);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->step_graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  c->launches -= 3;  // captured, not launched
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int pack_state(hydro_ctx* c, const real* U, double t0) {
+  Scratch<real>* s = scr<real>(c);
+  CK(cudaMemsetAsync(s, 0, offsetof(Scratch<real>, log_count), c->stream));
+  GridParams<real> g{};
+  GridParams<real> all[7];
+  build_params<real>(c, all);
+  g = all[0];
+  g.out = bufp<real>(c, 0);
+  CK(launch_pack<real>(U, g, c->nf, s->alpha[0], &s->smax, &s->t_acc, t0, c->stream));
+  c->launches++;
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int unpack_state(hydro_ctx* c, real* U, int k) {
+  const hydro_config& g = c->cfg;
+  for (int f = 0; f < c->nf; ++f) {
+    const real* src = bufp<real>(c, k) + f * c->fstride + (long long)GY * c->pitch + GX;
+    real* dst = U + (size_t)f * g.nx * g.ny;
+    CK(cudaMemcpy2DAsync(dst, sizeof(real) * g.nx, src, sizeof(real) * c->pitch, sizeof(real) * g.nx, g.ny,
+                         cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int read_status(hydro_ctx* c, double* t_inout, double* dt_last) {
+  CK(cudaMemcpyAsync(c->host_scratch, c->scratch, sizeof(Scratch<real>), cudaMemcpyDeviceToHost, c->stream));
+  int rc = wait_stream(c);
+  if (rc) return rc;
+  const Scratch<real>* hs = static_cast<const Scratch<real>*>(c->host_scratch);
+  if (t_inout) *t_inout = hs->t_acc;
+  if (dt_last) *dt_last = hs->dt_cur;
+  if (hs->err & ERR_TIMEOUT) return fail(c, HYDRO_ETIMEOUT, "a device wait gave up (tile copy did not complete)");
+  if (hs->err & ERR_NONPHYSICAL)
+    return fail(c, HYDRO_ENONPHYSICAL, "non-finite value, rho <= 0 or p <= 0 in the state");
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double* dt_last, const double* dtl,
+                     const double* al) {
+  const bool frozen = dtl != nullptr;
+  int rc = pack_state<real>(c, U, t_inout ? *t_inout : 0.0);
+  if (rc) return rc;
+  const bool use_graph = !frozen && !c->profiling && nsteps > 1;
+  if (use_graph) {
+    rc = ensure_graph<real>(c);
+    if (rc) return rc;
+  }
+  Scratch<real>* s = scr<real>(c);
+  for (int st = 0; st < nsteps; ++st) {
+    if (frozen) {
+      CK(launch_set_frozen<real>(&s->frozen_dt, dtl[st], &s->frozen_alpha[0][0], al + 6 * st, c->stream));
+      c->launches++;
+      rc = launch_step<real>(c, true, c->stream);
+    } else if (use_graph) {
+      CK(cudaGraphLaunch(c->step_graph, c->stream));
+      c->launches += 3;
+    } else {
+      rc = launch_step<real>(c, false, c->stream);
+    }
+    if (rc) return rc;
+  }
+  rc = unpack_state<real>(c, U, 0);
+  if (rc) return rc;
+  if (frozen) {
+    double tt = t_inout ? *t_inout : 0.0;
+    for (int st = 0; st < nsteps; ++st) tt += dtl[st];
+    int r2 = read_status<real>(c, nullptr, nullptr);
+    if (t_inout) *t_inout = tt;
+    if (dt_last && nsteps > 0) *dt_last = dtl[nsteps - 1];
+    return r2;
+  }
+  return read_status<real>(c, t_inout, dt_last);
+}
+
+static int check_ctx(hydro_ctx* c) {
+  if (!c) return HYDRO_EINVAL;
+  c->err.clear();
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return HYDRO_OK;
+}
+
+// ------------------------------------------------------------------------------------ C ABI
+// (the declarations in hydro.h carry the C linkage to these definitions)
+
+int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
+  if (!out) return HYDRO_EINVAL;
+  *out = nullptr;
+  std::string why;
+  int rc = validate_config(cfg, &why);
+  if (rc) return rc;
+  hydro_ctx* c = new hydro_ctx();
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->nf = cfg->nfields;
+  c->esize = cfg->dtype == HYDRO_F64 ? 8 : 4;
+  auto bail = [&](int code) {
+    hydro_destroy(c);
+    return code;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return bail(HYDRO_ECUDA);
+  c->tiles_x = (cfg->nx + TILE_X - 1) / TILE_X;
+  c->pitch = c->tiles_x * TILE_X + 8;
+  c->rows = ((cfg->ny + 31) / 32) * 32 + 2 * GY;
+  c->fstride = (long long)c->pitch * c->rows;
+  const size_t bytes = (size_t)c->nf * c->fstride * c->esize;
+  for (int k = 0; k < 3; ++k) {
+    if (cudaMalloc(&c->buf[k], bytes) != cudaSuccess) return bail(HYDRO_ECUDA);
+    if (cudaMemsetAsync(c->buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
+  }
+  const size_t sb = c->esize == 8 ? sizeof(Scratch<double>) : sizeof(Scratch<float>);
+  if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
+  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 7 : sizeof(GridParams<float>) * 7;
+  if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
+  c->partial_blocks = 4 * c->num_sms;
+  if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMalloc(&c->d_totals, sizeof(double) * 5) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
+  c->variant = 1;
+  if (upload(c) != HYDRO_OK) return bail(HYDRO_ECUDA);
+  *out = c;
+  return HYDRO_OK;
+}
+
+void hydro_destroy(hydro_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+  if (c->plan_graph) cudaGraphExecDestroy(c->plan_graph);
+  for (int k = 0; k < 3; ++k) cudaFree(c->buf[k]);
+  cudaFree(c->scratch);
+  cudaFree(c->params);
+  cudaFree(c->partials);
+  cudaFree(c->d_totals);
+  cudaFree(c->unpadded);
+  cudaFree(c->dt_log);
+  cudaFree(c->alpha_log);
+  cudaFree(c->plan_params);
+  cudaFree(c->plan_work);
+  if (c->host_scratch) cudaFreeHost(c->host_scratch);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->done) cudaEventDestroy(c->done);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  delete c;
+}
+
+const char* hydro_last_error(hydro_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int hydro_set_stream(hydro_ctx* c, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->stream = static_cast<cudaStream_t>(stream);
+  return HYDRO_OK;
+}
+
+int hydro_step(hydro_ctx* c, void* U, int nsteps, double* t_inout, double* dt_last) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || nsteps < 0) return fail(c, HYDRO_EINVAL, "null state or negative step count");
+  if (c->cfg.dtype == HYDRO_F64) return step_impl<double>(c, (double*)U, nsteps, t_inout, dt_last, nullptr, nullptr);
+  return step_impl<float>(c, (float*)U, nsteps, t_inout, dt_last, nullptr, nullptr);
+}
+
+static int ensure_unpadded(hydro_ctx* c) {
+  if (c->unpadded) return HYDRO_OK;
+  CK(cudaMalloc(&c->unpadded, (size_t)c->nf * c->cfg.nx * c->cfg.ny * c->esize));
+  return HYDRO_OK;
+}
+
+int hydro_step_host(hydro_ctx* c, void* U_host, int nsteps, double* t_inout, double* dt_last) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U_host || nsteps < 0) return fail(c, HYDRO_EINVAL, "null state or negative step count");
+  rc = ensure_unpadded(c);
+  if (rc) return rc;
+  const size_t bytes = (size_t)c->nf * c->cfg.nx * c->cfg.ny * c->esize;
+  CK(cudaMemcpyAsync(c->unpadded, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  rc = hydro_step(c, c->unpadded, nsteps, t_inout, dt_last);
+  int rc2 = HYDRO_OK;
+  cudaError_t e = cudaMemcpyAsync(U_host, c->unpadded, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) rc2 = cuda_fail(c, e, "copy back to host");
+  else rc2 = wait_stream(c);
+  return rc ? rc : rc2;
+}
+
+int hydro_step_frozen(hydro_ctx* c, void* U, int nsteps, const double* dtl, const double* al) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || nsteps < 0 || (nsteps > 0 && (!dtl || !al))) return fail(c, HYDRO_EINVAL, "bad frozen-step arguments");
+  if (c->cfg.dtype == HYDRO_F64) return step_impl<double>(c, (double*)U, nsteps, nullptr, nullptr, dtl, al);
+  return step_impl<float>(c, (float*)U, nsteps, nullptr, nullptr, dtl, al);
+}
+
+template <typename real>
+static int rhs_impl(hydro_ctx* c, const real* U, double ax, double ay, real* L) {
+  int rc = pack_state<real>(c, U, 0.0);
+  if (rc) return rc;
+  Scratch<real>* s = scr<real>(c);
+  const double a6[6] = {ax, ay, ax, ay, ax, ay};
+  CK(launch_set_frozen<real>(&s->frozen_dt, 0.0, &s->frozen_alpha[0][0], a6, c->stream));
+  c->launches++;
+  rc = launch_one<real>(c, 6, 0, 1, 0.0, 1.0, c->stream);
+  if (rc) return rc;
+  return unpack_state<real>(c, L, 1);
+}
+
+int hydro_rhs(hydro_ctx* c, const void* U, double ax, double ay, void* L) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !L || !(ax >= 0.0) || !(ay >= 0.0)) return fail(c, HYDRO_EINVAL, "bad rhs arguments");
+  if (c->cfg.dtype == HYDRO_F64) return rhs_impl<double>(c, (const double*)U, ax, ay, (double*)L);
+  return rhs_impl<float>(c, (const float*)U, ax, ay, (float*)L);
+}
+
+int conserved_totals(hydro_ctx* c, const void* U, double out[5]) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !out) return fail(c, HYDRO_EINVAL, "null argument");
+  const hydro_config& g = c->cfg;
+  const double dx = (g.x1 - g.x0) / g.nx, dy = (g.y1 - g.y0) / g.ny;
+  cudaError_t e = g.dtype == HYDRO_F64
+                      ? launch_totals<double>((const double*)U, g.nx, g.ny, c->nf, g.geometry, g.x0, dx, dy,
+                                              c->partials, c->partial_blocks, c->d_totals, c->stream)
+                      : launch_totals<float>((const float*)U, g.nx, g.ny, c->nf, g.geometry, g.x0, dx, dy,
+                                             c->partials, c->partial_blocks, c->d_totals, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "totals kernels");
+  c->launches += 2;
+  CK(cudaMemcpyAsync(c->host_scratch, c->d_totals, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+  rc = wait_stream(c);
+  if (rc) return rc;
+  std::memcpy(out, c->host_scratch, sizeof(double) * 5);
+  return HYDRO_OK;
+}
+
+int hydro_last_totals(hydro_ctx* c, double out[5]) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out) return fail(c, HYDRO_EINVAL, "null argument");
+  if (!c->track_totals) return fail(c, HYDRO_ESTATE, "totals tracking is off");
+  const size_t off = c->esize == 8 ? offsetof(Scratch<double>, totals) : offsetof(Scratch<float>, totals);
+  CK(cudaMemcpyAsync(c->host_scratch, static_cast<char*>(c->scratch) + off, sizeof(double) * 5,
+                     cudaMemcpyDeviceToHost, c->stream));
+  rc = wait_stream(c);
+  if (rc) return rc;
+  std::memcpy(out, c->host_scratch, sizeof(double) * 5);
+  return HYDRO_OK;
+}
+
+int hydro_record(hydro_ctx* c, int max_steps) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (max_steps < 0) return fail(c, HYDRO_EINVAL, "negative capacity");
+  CK(cudaStreamSynchronize(c->stream));
+  cudaFree(c->dt_log);
+  cudaFree(c->alpha_log);
+  c->dt_log = nullptr;
+  c->alpha_log = nullptr;
+  c->log_cap = 0;
+  if (max_steps > 0) {
+    CK(cudaMalloc(&c->dt_log, sizeof(double) * max_steps));
+    CK(cudaMalloc(&c->alpha_log, sizeof(double) * 6 * max_steps));
+    c->log_cap = max_steps;
+  }
+  const size_t off = c->esize == 8 ? offsetof(Scratch<double>, log_count) : offsetof(Scratch<float>, log_count);
+  CK(cudaMemset(static_cast<char*>(c->scratch) + off, 0, sizeof(int)));
+  return upload(c);
+}
+
+int hydro_get_log(hydro_ctx* c, int n, double* dtl, double* al, int* n_recorded) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  int cnt = 0;
+  const size_t off = c->esize == 8 ? offsetof(Scratch<double>, log_count) : offsetof(Scratch<float>, log_count);
+  CK(cudaMemcpy(&cnt, static_cast<char*>(c->scratch) + off, sizeof(int), cudaMemcpyDeviceToHost));
+  cnt = std::min(cnt, c->log_cap);
+  if (n_recorded) *n_recorded = cnt;
+  if (n < 0 || n > cnt) return fail(c, HYDRO_EINVAL, "more log entries requested than recorded");
+  if (n > 0) {
+    if (!dtl || !al) return fail(c, HYDRO_EINVAL, "null log buffer");
+    CK(cudaMemcpy(dtl, c->dt_log, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(al, c->alpha_log, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost));
+  }
+  return HYDRO_OK;
+}
+
+// ---- tile variants, autotuner, profiling
+
+int hydro_tile_variants(hydro_ctx* c, int* n, int* current) {
+  if (!c) return HYDRO_EINVAL;
+  if (n) *n = NUM_VARIANTS;
+  if (current) *current = c->variant;
+  return HYDRO_OK;
+}
+
+int hydro_set_tile_variant(hydro_ctx* c, int v) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (v < 0 || v >= NUM_VARIANTS) return fail(c, HYDRO_EINVAL, "no such tile variant");
+  const int occ = c->cfg.dtype == HYDRO_F64 ? stage_ctas_per_sm<double>(v, c->nf) : stage_ctas_per_sm<float>(v, c->nf);
+  if (occ < 1) return fail(c, HYDRO_EINVAL, "tile variant does not fit on this device");
+  if (v == c->variant) return HYDRO_OK;
+  c->variant = v;
+  return upload(c);
+}
+
+int hydro_tile_info(hydro_ctx* c, int v, int* tx, int* ty, int* threads, int* smem) {
+  if (!c || v < 0 || v >= NUM_VARIANTS) return HYDRO_EINVAL;
+  if (tx) *tx = TILE_X;
+  if (ty) *ty = VARIANTS[v].ty;
+  if (threads) *threads = VARIANTS[v].threads;
+  if (smem)
+    *smem = c->cfg.dtype == HYDRO_F64 ? stage_smem_bytes<double>(v, c->nf) : stage_smem_bytes<float>(v, c->nf);
+  return HYDRO_OK;
+}
+
+int hydro_profile(hydro_ctx* c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->profiling = enable != 0;
+  c->ev_used = 0;
+  return HYDRO_OK;
+}
+
+int hydro_stage_timing(hydro_ctx* c, int* launches, double* total_ms) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  for (int k = 0; k + 1 < c->ev_used; k += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+    tot += ms;
+  }
+  if (launches) *launches = c->ev_used / 2;
+  if (total_ms) *total_ms = tot;
+  return HYDRO_OK;
+}
+
+long long hydro_launch_count(hydro_ctx* c) { return c ? c->launches : -1; }
+
+template <typename real>
+static int autotune_impl(hydro_ctx* c, const real* U, int steps, double* ms_out) {
+  const int keep = c->variant;
+  double best = 1e300;
+  int best_v = keep;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int v = 0; v < NUM_VARIANTS; ++v) {
+    double ms_step = -1.0;
+    if (stage_ctas_per_sm<real>(v, c->nf) >= 1) {
+      c->variant = v;
+      int rc = upload(c);
+      if (!rc) rc = pack_state<real>(c, U, 0.0);
+      if (!rc) rc = launch_step<real>(c, false, c->stream);  // warm-up step
+      if (!rc) {
+        cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < steps && !rc; ++s) rc = launch_step<real>(c, false, c->stream);
+        cudaEventRecord(e1, c->stream);
+      }
+      if (!rc) rc = read_status<real>(c, nullptr, nullptr);
+      if (rc && rc != HYDRO_ENONPHYSICAL) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->variant = keep;
+        upload(c);
+        return rc;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_step = ms / std::max(1, steps);
+      if (ms_step < best) {
+        best = ms_step;
+        best_v = v;
+      }
+    }
+    if (ms_out) ms_out[v] = ms_step;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->variant = best_v;
+  return upload(c);
+}
+
+int hydro_autotune(hydro_ctx* c, const void* U, int steps, double* ms_out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || steps < 1) return fail(c, HYDRO_EINVAL, "bad autotune arguments");
+  if (c->cfg.dtype == HYDRO_F64) return autotune_impl<double>(c, (const double*)U, steps, ms_out);
+  return autotune_impl<float>(c, (const float*)U, steps, ms_out);
+}
+
+// ---- batched ensembles
+
+template <typename real>
+static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, double* t) {
+  hydro_ctx* c = m[0];
+  // every member on the first member's tile variant
+  for (int k = 0; k < n; ++k) {
+    if (m[k]->variant != c->variant) {
+      m[k]->variant = c->variant;
+      int rc = upload(m[k]);
+      if (rc) return fail(c, rc, "member " + std::to_string(k) + ": " + m[k]->err);
+    }
+  }
+  bool same = (int)c->plan_members.size() == n && c->plan_variant == c->variant;
+  for (int k = 0; same && k < n; ++k) same = c->plan_members[k] == m[k];
+  if (!same) {
+    if (c->plan_graph) {
+      cudaGraphExecDestroy(c->plan_graph);
+      c->plan_graph = nullptr;
+    }
+    cudaFree(c->plan_params);
+    cudaFree(c->plan_work);
+    c->plan_params = nullptr;
+    c->plan_work = nullptr;
+    std::vector<GridParams<real>> P(3 * (size_t)n);
+    std::vector<WorkItem> W;
+    for (int k = 0; k < n; ++k) {
+      GridParams<real> p[7];
+      build_params<real>(m[k], p);
+      for (int s = 0; s < 3; ++s) P[(size_t)s * n + k] = p[s];
+    }
+    // interleave members so every CTA of the persistent launch sees a mix of grid sizes
+    std::vector<int> ntile(n), next(n, 0);
+    int total = 0;
+    for (int k = 0; k < n; ++k) {
+      ntile[k] = m[k]->tiles_x * ((m[k]->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
+      total += ntile[k];
+    }
+    W.reserve(total);
+    while ((int)W.size() < total)
+      for (int k = 0; k < n; ++k)
+        if (next[k] < ntile[k]) W.push_back(WorkItem{k, next[k]++});
+    CK(cudaMalloc(&c->plan_params, sizeof(GridParams<real>) * P.size()));
+    CK(cudaMalloc(&c->plan_work, sizeof(WorkItem) * W.size()));
+    CK(cudaMemcpy(c->plan_params, P.data(), sizeof(GridParams<real>) * P.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->plan_work, W.data(), sizeof(WorkItem) * W.size(), cudaMemcpyHostToDevice));
+    c->plan_nwork = total;
+    c->plan_members.assign(m, m + n);
+    c->plan_variant = c->variant;
+  }
+  for (int k = 0; k < n; ++k) {
+    hydro_ctx* mk = m[k];
+    Scratch<real>* s = scr<real>(mk);
+    CK(cudaMemsetAsync(s, 0, offsetof(Scratch<real>, log_count), c->stream));
+    GridParams<real> p[7];
+    build_params<real>(mk, p);
+    p[0].out = bufp<real>(mk, 0);
+    CK(launch_pack<real>(static_cast<const real*>(U[k]), p[0], mk->nf, s->alpha[0], &s->smax, &s->t_acc,
+                         t ? t[k] : 0.0, c->stream));
+    c->launches++;
+  }
+  const int grid = grid_for(c, c->plan_nwork);
+  const GridParams<real>* P = static_cast<const GridParams<real>*>(c->plan_params);
+  const WorkItem* W = static_cast<const WorkItem*>(c->plan_work);
+  auto launch3 = [&](cudaStream_t s) -> int {
+    for (int k = 0; k < 3; ++k) {
+      StageCtl ctl{k, 0, RK_A[k], RK_B[k]};
+      CK(launch_stage<real>(c->variant, c->nf, P + (size_t)k * n, W, c->plan_nwork, ctl, grid, s));
+    }
+    return HYDRO_OK;
+  };
+  if (!c->plan_graph) {
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+    int rc = launch3(c->capture);
+    cudaError_t e = cudaStreamEndCapture(c->capture, &gr);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->plan_graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    CK(cudaGraphLaunch(c->plan_graph, c->stream));
+    c->launches += 3;
+  }
+  int worst = HYDRO_OK;
+  for (int k = 0; k < n; ++k) {
+    hydro_ctx* mk = m[k];
+    // members' unpack and status copies go on the batch stream
+    cudaStream_t keep = mk->stream;
+    mk->stream = c->stream;
+    int rc = unpack_state<real>(mk, static_cast<real*>(U[k]), 0);
+    if (!rc) {
+      CK(cudaMemcpyAsync(mk->host_scratch, mk->scratch, sizeof(Scratch<real>), cudaMemcpyDeviceToHost, c->stream));
+    }
+    mk->stream = keep;
+    if (rc) return fail(c, rc, mk->err);
+  }
+  int rc = wait_stream(c);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    const Scratch<real>* hs = static_cast<const Scratch<real>*>(m[k]->host_scratch);
+    if (t) t[k] = hs->t_acc;
+    if (hs->err & ERR_TIMEOUT) worst = fail(c, HYDRO_ETIMEOUT, "member " + std::to_string(k) + ": device wait gave up");
+    else if ((hs->err & ERR_NONPHYSICAL) && worst == HYDRO_OK)
+      worst = fail(c, HYDRO_ENONPHYSICAL, "member " + std::to_string(k) + ": non-physical state");
+  }
+  return worst;
+}
+
+int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nsteps, double* t) {
+  if (!members || !U || n < 1 || nsteps < 0) return HYDRO_EINVAL;
+  hydro_ctx* c = members[0];
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (!members[k] || !U[k]) return fail(c, HYDRO_EINVAL, "null member or state");
+    if (members[k]->cfg.dtype != c->cfg.dtype || members[k]->nf != c->nf || members[k]->device != c->device)
+      return fail(c, HYDRO_EINVAL, "members must share dtype, nfields and device");
+  }
+  if (c->cfg.dtype == HYDRO_F64) return batch_impl<double>(members, U, n, nsteps, t);
+  return batch_impl<float>(members, U, n, nsteps, t);
+}
+
+// ---- adjoint entry points (adjoint.cu holds the kernels and the sweep)
+
+int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, const double alpha[6]) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U_n || !lambda || !alpha || !(dt >= 0.0)) return fail(c, HYDRO_EINVAL, "bad adjoint arguments");
+  (void)dt;
+  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+}
+
+int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || nsteps < 0) return fail(c, HYDRO_EINVAL, "bad arguments");
+  (void)every;
+  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+}
+
+int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!lambda) return fail(c, HYDRO_EINVAL, "null lambda");
+  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+}
+

@@ -1,0 +1,120 @@
+// hydro_internal.cuh -- parameter blocks and device helpers shared by the stage kernels and the host
+// runtime of the WENO5 / Lax-Friedrichs / SSP-RK3 Euler solver (Leung, Chu & Lin 2015, Sec. 2.1-2.2).
+//
+// Padded device layout of a working state (one plane per field, `fstride` elements apart):
+//   cell (i, j) of the nx x ny interior sits at element (j + GY) * pitch + (i + GX)
+// with GX = 4 ghost columns on the left (three are used; the fourth keeps every interior row 16-byte
+// aligned so that tiles move with 16-byte bulk copies and 4-wide vector stores) and GY = 3 ghost rows.
+// pitch and the row count cover whole tiles plus the halo, so tile halo boxes never leave the
+// allocation; cells beyond the grid are dead and masked.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hydro {
+
+constexpr int GX = 4;        // ghost columns left of cell 0 (3 used + 1 alignment)
+constexpr int GY = 3;        // ghost rows below row 0
+constexpr int TILE_X = 60;   // cells per tile in x: halo box 68 = 60 + 8 wide (16-byte multiple)
+constexpr int BOX_W = 68;    // smem row pitch; 68 = 4 (mod 32) makes the x-pass lanes conflict-free
+constexpr int RUN_X = 15;    // cells per x-pass work item (4 items per tile row)
+constexpr int NQ_X = 4;
+
+enum Bc { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECT = 2, BC_AXIS = 3 };
+enum ErrBits { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2 };
+
+// Tile variants: tile height TY and threads per CTA. x-pass items = TY * 4 * NF, y-pass items =
+// 60 * NF * (TY / KY); the thread counts keep both near one item per thread.
+struct Variant {
+  int ty, threads;
+};
+constexpr int NUM_VARIANTS = 3;
+constexpr Variant VARIANTS[NUM_VARIANTS] = {{8, 160}, {16, 320}, {32, 640}};
+
+// Per-grid parameters of one stage launch (one ensemble member).
+template <typename real>
+struct GridParams {
+  const real* win;   // stage input W (padded)
+  const real* un;    // U^n (padded), read when rk_a != 0
+  real* out;         // stage output (padded) or L (mode RHS)
+  long long fstride; // elements between field planes
+  int nx, ny, pitch;
+  int tiles_x, tiles_y;
+  int bc[4];
+  int geometry;
+  real gamma, gm1, gravity, flame_speed;
+  real rdx, rdy;       // 1/dx, 1/dy
+  double dx, dy, x0;   // FP64 copies for geometry and totals
+  double cfl_delta;    // c_cfl * min(dx, dy)
+  // reduction slots (device)
+  const real* alpha_in;   // (alpha_x, alpha_y) used by this stage
+  real* alpha_out;        // max(|u|+c), max(|v|+c) of the output (next stage), may be null
+  real* alpha_zero;       // slot to reset for the stage after next, may be null
+  real* smax;             // CFL signal speed slot (read at stage 0, reset at 1, written at 2)
+  double* dt_cur;         // dt of the running step (written at stage 0)
+  const double* dt_src;   // frozen dt for this step (stage 0 of a frozen run), else null
+  double* t_acc;          // FP64 time accumulator
+  double* dt_log;         // recording: dt per step (null when not recording)
+  double* alpha_log;      // recording: (alpha_x, alpha_y) per stage, 6 per step
+  int* log_count;         // recording: steps logged so far (advanced by the last stage)
+  int log_cap;            // recording: capacity in steps
+  double* totals;         // 5 FP64 totals of the output (last stage), may be null
+  double* totals_reset;   // totals array to clear (stage 1), may be null
+  int* err;               // error bits
+};
+
+// Launch-wide stage control.
+struct StageCtl {
+  int stage;      // 0, 1, 2
+  int mode;       // 0 RK stage, 1 write L (no blending, no reductions)
+  double rk_a;    // out = a U^n + b (W + dt L)
+  double rk_b;
+};
+
+// Batched launch: a table of (member, tile) work items over an array of member parameters.
+struct WorkItem {
+  int member;
+  int tile;
+};
+
+// Host-side launch entry points (one translation unit per precision). members_dev points to device
+// GridParams (one per member; work_dev maps work item -> (member, tile), or is null for one grid whose
+// tiles are the work items).
+template <typename real>
+cudaError_t launch_stage(int variant, int nfields, const GridParams<real>* members_dev, const WorkItem* work_dev,
+                         int nwork, const StageCtl& ctl, int grid, cudaStream_t s);
+template <typename real>
+int stage_smem_bytes(int variant, int nfields);
+template <typename real>
+int stage_ctas_per_sm(int variant, int nfields);
+
+// Copy an unpadded caller state into a padded working state, write its ghost images, and reduce its
+// Lax-Friedrichs speeds and CFL signal speed into the given slots; sets *t_acc = t0 when t_acc != null.
+template <typename real>
+cudaError_t launch_pack(const real* U, const GridParams<real>& g, int nfields, real* alpha_slot, real* smax_slot,
+                        double* t_acc, double t0, cudaStream_t s);
+// Write frozen dt and stage alphas into device slots (frozen runs, adjoint).
+template <typename real>
+cudaError_t launch_set_frozen(double* dt_slot, double dt, real* alpha_slots, const double* alpha6, cudaStream_t s);
+// FP64 conserved totals of an unpadded state: per-block partials, then a fixed-order final sum.
+template <typename real>
+cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geometry, double x0, double dx,
+                          double dy, double* partials, int nblocks, double* out, cudaStream_t s);
+
+// ------------------------------------------------------------------------------ device helpers
+
+#ifdef __CUDACC__
+
+// Source index and normal-momentum flip of ghost layer k (0 nearest) of a face of a line of n cells.
+__host__ __device__ inline int ghost_src(int bc, bool hi, int k, int n, bool* flip) {
+  *flip = false;
+  if (bc == BC_PERIODIC) return hi ? k : n - 1 - k;
+  if (bc == BC_TRANSMISSIVE) return hi ? n - 1 : 0;
+  *flip = true;  // reflecting wall or axis: mirror image
+  return hi ? n - 1 - k : k;
+}
+
+#endif
+
+}  // namespace hydro

@@ -1,0 +1,117 @@
+// stage_inst.cuh -- host launchers of the stage kernel variants and the small kernels for one
+// precision (included by stage_f32.cu / stage_f64.cu with HYDRO_REAL defined).
+#pragma once
+#include "aux_kernels.cuh"
+
+namespace hydro {
+
+namespace {
+
+template <typename real, int NF, int V>
+struct VariantLaunch {
+  static constexpr int TY = VARIANTS[V].ty, NT = VARIANTS[V].threads;
+  static constexpr size_t SMEM = Tile<real, NF, TY>::BYTES;
+  static cudaError_t configure() {
+    static cudaError_t once = cudaFuncSetAttribute(stage_kernel<real, NF, TY, NT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    return once;
+  }
+  static cudaError_t launch(const GridParams<real>* m, const WorkItem* w, int nwork, const StageCtl& ctl, int grid,
+                            cudaStream_t s) {
+    cudaError_t e = configure();
+    if (e != cudaSuccess) return e;
+    stage_kernel<real, NF, TY, NT><<<grid, NT, SMEM, s>>>(m, w, nwork, ctl);
+    return cudaGetLastError();
+  }
+  static int occupancy() {
+    if (configure() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<real, NF, TY, NT>, NT, SMEM) != cudaSuccess)
+      return 0;
+    return n;
+  }
+};
+
+template <typename real, int NF>
+cudaError_t launch_nf(int variant, const GridParams<real>* m, const WorkItem* w, int nwork, const StageCtl& ctl,
+                      int grid, cudaStream_t s) {
+  switch (variant) {
+    case 0: return VariantLaunch<real, NF, 0>::launch(m, w, nwork, ctl, grid, s);
+    case 1: return VariantLaunch<real, NF, 1>::launch(m, w, nwork, ctl, grid, s);
+    case 2: return VariantLaunch<real, NF, 2>::launch(m, w, nwork, ctl, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename real, int NF>
+int occ_nf(int variant) {
+  switch (variant) {
+    case 0: return VariantLaunch<real, NF, 0>::occupancy();
+    case 1: return VariantLaunch<real, NF, 1>::occupancy();
+    case 2: return VariantLaunch<real, NF, 2>::occupancy();
+    default: return 0;
+  }
+}
+
+template <typename real, int NF>
+int smem_nf(int variant) {
+  switch (variant) {
+    case 0: return (int)VariantLaunch<real, NF, 0>::SMEM;
+    case 1: return (int)VariantLaunch<real, NF, 1>::SMEM;
+    case 2: return (int)VariantLaunch<real, NF, 2>::SMEM;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_stage<HYDRO_REAL>(int variant, int nfields, const GridParams<HYDRO_REAL>* m, const WorkItem* w,
+                                     int nwork, const StageCtl& ctl, int grid, cudaStream_t s) {
+  if (nwork <= 0) return cudaSuccess;
+  return nfields == 5 ? launch_nf<HYDRO_REAL, 5>(variant, m, w, nwork, ctl, grid, s)
+                      : launch_nf<HYDRO_REAL, 4>(variant, m, w, nwork, ctl, grid, s);
+}
+
+template <>
+int stage_smem_bytes<HYDRO_REAL>(int variant, int nfields) {
+  return nfields == 5 ? smem_nf<HYDRO_REAL, 5>(variant) : smem_nf<HYDRO_REAL, 4>(variant);
+}
+
+template <>
+int stage_ctas_per_sm<HYDRO_REAL>(int variant, int nfields) {
+  return nfields == 5 ? occ_nf<HYDRO_REAL, 5>(variant) : occ_nf<HYDRO_REAL, 4>(variant);
+}
+
+template <>
+cudaError_t launch_pack<HYDRO_REAL>(const HYDRO_REAL* U, const GridParams<HYDRO_REAL>& g, int nfields,
+                                    HYDRO_REAL* alpha_slot, HYDRO_REAL* smax_slot, double* t_acc, double t0,
+                                    cudaStream_t s) {
+  dim3 grid((g.nx + 255) / 256, g.ny);
+  if (nfields == 5)
+    pack_kernel<HYDRO_REAL, 5><<<grid, 256, 0, s>>>(U, g, alpha_slot, smax_slot, t_acc, t0);
+  else
+    pack_kernel<HYDRO_REAL, 4><<<grid, 256, 0, s>>>(U, g, alpha_slot, smax_slot, t_acc, t0);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_set_frozen<HYDRO_REAL>(double* dt_slot, double dt, HYDRO_REAL* alpha_slots, const double* a,
+                                          cudaStream_t s) {
+  set_frozen_kernel<HYDRO_REAL><<<1, 32, 0, s>>>(dt_slot, dt, alpha_slots, a[0], a[1], a[2], a[3], a[4], a[5]);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int nfields, int geometry, double x0,
+                                      double dx, double dy, double* partials, int nblocks, double* out,
+                                      cudaStream_t s) {
+  if (nfields == 5)
+    totals_partial_kernel<HYDRO_REAL, 5><<<nblocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, partials);
+  else
+    totals_partial_kernel<HYDRO_REAL, 4><<<nblocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, partials);
+  totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, nfields, out);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

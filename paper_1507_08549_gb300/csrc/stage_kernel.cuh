@@ -1,0 +1,665 @@
+// stage_kernel.cuh -- fused SSP-RK3 stage of the WENO5 / global Lax-Friedrichs Euler update with the
+// level-set scalar (Leung, Chu & Lin 2015, Sec. 2.1 Eq. euler2D and Sec. 2.2), for sm_103a.
+//
+// One CTA processes one 60 x TY tile per work item (persistent loop over items):
+//   A. the (TY+6) x 68 halo box of every field is moved into shared memory by TMA bulk copies
+//      (cp.async.bulk, one row per copy, completion on an mbarrier);
+//   B. primitive variables u, v, p at the box points (rcp of rho once per point);
+//   C. x pass: each work item is (field, tile row, run of 15 cells); the split fluxes
+//      f+- = (F +- alpha U)/2, the per-point smoothness data and the 16 face fluxes of the run slide
+//      through registers, so every point's split flux and smoothness indicators are formed once;
+//      the level-set item forms one-sided HJ-WENO5 derivatives the same way;
+//   D. y pass: same on (field, tile column, run of up to 16 cells), accumulating dF/dx + dG/dy in
+//      shared memory; the level-set item closes the local Lax-Friedrichs Hamiltonian;
+//   E. per cell: L = -(dF/dx + dG/dy) + S, the RK blend a U^n + b (W + dt L), vector stores, the
+//      ghost images the boundary conditions ask for, and the reductions the next launches need:
+//      alpha_x, alpha_y of the output (next stage), c + |u| + |v| (next step's dt), FP64 totals.
+// Lane-to-item maps make every shared-memory access of the passes bank-conflict free (68 = 4 mod 32
+// and 15 = 3 mod 4 spread the 32 lanes of an x-pass warp over all banks).
+#pragma once
+#include "hydro_internal.cuh"
+
+namespace hydro {
+
+// ------------------------------------------------------------------------------ precision traits
+
+template <typename real>
+struct RT;
+
+template <>
+struct RT<float> {
+  static __device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ void atomic_max(float* a, float v) {
+    atomicMax(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+  }
+  static __device__ __forceinline__ bool finite(float v) { return isfinite(v); }
+};
+
+template <>
+struct RT<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ void atomic_max(double* a, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
+  }
+  static __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+};
+
+// ------------------------------------------------------------------------------ TMA + mbarrier
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Global -> shared bulk copy (TMA, non-tensor); bytes and both addresses are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2^28 polls (seconds) and reports ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 28); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------------------ WENO5 pieces
+
+// Smoothness data of the point triplet (L, C, R) (Jiang & Shu 1996), already offset by eps:
+//   m: eps + 13/12 s^2 + 1/4 (2s - t)^2  (the triplet as the leftmost stencil of a face),
+//   t: eps + 13/12 s^2 + 1/4 t^2          (as the central stencil),
+//   p: eps + 13/12 s^2 + 1/4 (2s + t)^2  (as the rightmost stencil),
+// with s = (L + R) - 2C and t = L - R. Mirroring the triplet keeps s and negates t, so the same data
+// serve the reconstruction from the right.
+template <typename real>
+struct B3 {
+  real m, t, p;
+};
+
+template <typename real>
+__device__ __forceinline__ B3<real> betas(real L, real C, real R) {
+  using T = RT<real>;
+  const real s = T::fma_(real(-2), C, L + R);
+  const real t = L - R;
+  const real bs = T::fma_(real(13.0 / 12.0) * s, s, real(1e-6));
+  const real mm = T::fma_(real(2), s, -t);
+  const real pp = T::fma_(real(2), s, t);
+  B3<real> b;
+  b.m = T::fma_(real(0.25) * mm, mm, bs);
+  b.t = T::fma_(real(0.25) * t, t, bs);
+  b.p = T::fma_(real(0.25) * pp, pp, bs);
+  return b;
+}
+
+// WENO5-JS value at the right face of c from (a, b, c, d, e) given D_k = eps + beta_k:
+//   sum_k d_k q_k / (eps + beta_k)^2 / sum_k d_k / (eps + beta_k)^2,
+// with the linear weights d = (1/10, 6/10, 3/10) and the 1/6 of the candidate values folded into the
+// constants, so one reciprocal per weight and one for the normalisation remain.
+template <typename real>
+__device__ __forceinline__ real weno_side(real a, real b, real c, real d, real e, real D0, real D1, real D2) {
+  using T = RT<real>;
+  const real q0 = T::fma_(real(0.2), a, T::fma_(real(-0.7), b, real(1.1) * c));
+  const real q1 = T::fma_(real(-0.6), b, T::fma_(real(3.0), c, real(1.2) * d));
+  const real q2 = T::fma_(real(0.6), c, T::fma_(real(1.5), d, real(-0.3) * e));
+  const real r0 = T::rcp(D0 * D0);
+  const real r1 = T::rcp(D1 * D1);
+  const real r2 = T::rcp(D2 * D2);
+  const real num = T::fma_(r2, q2, T::fma_(r1, q1, r0 * q0));
+  const real den = T::fma_(real(1.8), r2, T::fma_(real(3.6), r1, real(0.6) * r0));
+  return num * T::rcp(den);
+}
+
+// Flux kinds along a direction: 0 mass (flux = normal momentum), 1 normal momentum (m_n v_n + p),
+// 2 tangential momentum (m_t v_n), 3 energy ((tau + p) v_n).
+//
+// One line of K cells: points m = 0 .. K+5 (cells -3 .. K+2 of the run), faces f = 0 .. K (left face
+// of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1.
+template <typename real, int K, int S>
+__device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
+                                           const real* __restrict__ vel, int vstride,
+                                           const real* __restrict__ pr, int kind, real hal, real rd,
+                                           real* __restrict__ dst, int dstride, bool accumulate) {
+  using T = RT<real>;
+  real fp[K + 6], fm[K + 6];
+  B3<real> bp[K + 6], bm[K + 6];
+  real fh_prev = real(0);
+#pragma unroll
+  for (int m = 0; m < K + 6; ++m) {
+    const real uu = Uc[m * S];
+    real F;
+    if (kind == 0) {
+      F = Xc[m * S];
+    } else {
+      const real vn = vel[m * vstride];
+      const real p = pr[m * S];
+      F = (kind == 1) ? T::fma_(uu, vn, p) : (kind == 2) ? uu * vn : (uu + p) * vn;
+    }
+    const real hF = real(0.5) * F;
+    fp[m] = T::fma_(hal, uu, hF);
+    fm[m] = T::fma_(-hal, uu, hF);
+    if (m >= 2) {
+      const int j = m - 1;
+      if (j <= K + 3) bp[j] = betas(fp[j - 1], fp[j], fp[j + 1]);
+      if (j >= 2) bm[j] = betas(fm[j - 1], fm[j], fm[j + 1]);
+    }
+    if (m >= 5) {
+      const int f = m - 5;
+      const real plus = weno_side(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4], bp[f + 1].m, bp[f + 2].t,
+                                  bp[f + 3].p);
+      const real minus = weno_side(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1], bm[f + 4].p,
+                                   bm[f + 3].t, bm[f + 2].m);
+      const real fh = plus + minus;
+      if (f >= 1) {
+        const real d = (fh - fh_prev) * rd;
+        real* o = dst + (f - 1) * dstride;
+        *o = accumulate ? (*o + d) : d;
+      }
+      fh_prev = fh;
+    }
+  }
+}
+
+// One-sided HJ-WENO5 derivatives (Jiang & Peng 2000) of phi along a line of K cells from points
+// m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
+// phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}). emit(k, phi^-, phi^+).
+template <typename real, int K, int S, typename Emit>
+__device__ __forceinline__ void phi_line(const real* __restrict__ ph, real rd, Emit emit) {
+  real d[K + 5];
+  B3<real> b[K + 5];
+  real prev = ph[0];
+#pragma unroll
+  for (int n = 0; n < K + 5; ++n) {
+    const real nxt = ph[(n + 1) * S];
+    d[n] = (nxt - prev) * rd;
+    prev = nxt;
+    if (n >= 2) b[n - 1] = betas(d[n - 2], d[n - 1], d[n]);
+    if (n >= 5) {
+      const int k = n - 5;
+      const real dm = weno_side(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4], b[k + 1].m, b[k + 2].t, b[k + 3].p);
+      const real dp = weno_side(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1], b[k + 4].p, b[k + 3].t,
+                                b[k + 2].m);
+      emit(k, dm, dp);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ small helpers
+
+template <typename real>
+__device__ __forceinline__ void load4(const real* p, real (&v)[4]) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ void store4(real* p, const real (&v)[4]) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+// Ghost images of interior cell (i, j) of a padded state: periodic wrap, transmissive copies of the
+// edge cell, or mirror images with the normal momentum reversed (reflecting wall, symmetry axis).
+// Corner ghosts are never read by the dimension-by-dimension stencil and are not written.
+template <typename real, int NF>
+__device__ __forceinline__ void write_ghost_images(real* out, long long fs, int pitch, int nx, int ny,
+                                                   const int* bc, int i, int j, const real (&val)[NF]) {
+  auto put = [&](int gi, int gj, bool fx, bool fy) {
+    const long long off = static_cast<long long>(gj + GY) * pitch + gi + GX;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      real v = val[f];
+      if ((f == 1 && fx) || (f == 2 && fy)) v = -v;
+      out[f * fs + off] = v;
+    }
+  };
+  if (i < 3 || i >= nx - 3) {
+    const int bl = bc[0], bh = bc[1];
+    if (bl == BC_PERIODIC) {
+      if (i >= nx - 3) put(i - nx, j, false, false);
+    } else if (bl == BC_TRANSMISSIVE) {
+      if (i == 0) { put(-1, j, false, false); put(-2, j, false, false); put(-3, j, false, false); }
+    } else if (i < 3) {
+      put(-1 - i, j, true, false);
+    }
+    if (bh == BC_PERIODIC) {
+      if (i < 3) put(nx + i, j, false, false);
+    } else if (bh == BC_TRANSMISSIVE) {
+      if (i == nx - 1) { put(nx, j, false, false); put(nx + 1, j, false, false); put(nx + 2, j, false, false); }
+    } else if (i >= nx - 3) {
+      put(2 * nx - 1 - i, j, true, false);
+    }
+  }
+  if (j < 3 || j >= ny - 3) {
+    const int bl = bc[2], bh = bc[3];
+    if (bl == BC_PERIODIC) {
+      if (j >= ny - 3) put(i, j - ny, false, false);
+    } else if (bl == BC_TRANSMISSIVE) {
+      if (j == 0) { put(i, -1, false, false); put(i, -2, false, false); put(i, -3, false, false); }
+    } else if (j < 3) {
+      put(i, -1 - j, false, true);
+    }
+    if (bh == BC_PERIODIC) {
+      if (j < 3) put(i, ny + j, false, false);
+    } else if (bh == BC_TRANSMISSIVE) {
+      if (j == ny - 1) { put(i, ny, false, false); put(i, ny + 1, false, false); put(i, ny + 2, false, false); }
+    } else if (j >= ny - 3) {
+      put(i, 2 * ny - 1 - j, false, true);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ tile geometry
+
+template <typename real, int NF, int TY>
+struct Tile {
+  static constexpr int TX = TILE_X, W = BOX_W, H = TY + 6, K = RUN_X, NQ = NQ_X;
+  static constexpr int KY = TY < 16 ? TY : 16;
+  static constexpr int NQY = TY / KY;
+  // shared-memory carve-up (elements of real)
+  static constexpr int OFF_U = 0;                         // [NF][H][W]   state box
+  static constexpr int OFF_PU = OFF_U + NF * H * W;       // [TY][W]      u on the tile rows
+  static constexpr int OFF_PV = OFF_PU + TY * W;          // [H][TX]      v on the tile columns
+  static constexpr int OFF_PP = OFF_PV + H * TX;          // [H][W]       p
+  static constexpr int OFF_D = OFF_PP + H * W;            // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
+  static constexpr int OFF_X = OFF_D + NF * TY * TX;      // [2][TY][TX]  phi_x^-, phi_x^+
+  static constexpr int ELEMS = OFF_X + (NF == 5 ? 2 * TY * TX : 0);
+  static constexpr int RED_DOUBLES = 20 * 8;              // per-warp partials (<= 20 warps x 8)
+  static constexpr size_t BYTES = ((ELEMS * sizeof(real) + 15) / 16) * 16 + RED_DOUBLES * sizeof(double) + 16;
+  static constexpr unsigned BOX_BYTES = NF * H * W * sizeof(real);
+};
+
+// ------------------------------------------------------------------------------ the stage kernel
+
+template <typename real, int NF, int TY, int NT>
+__global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
+    stage_kernel(const GridParams<real>* __restrict__ members, const WorkItem* __restrict__ work, int nwork,
+                 StageCtl ctl) {
+  using T = RT<real>;
+  using TL = Tile<real, NF, TY>;
+  constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ, KY = TL::KY, NQY = TL::NQY;
+  static_assert(TY % 8 == 0, "tile height must be a multiple of 8");
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  real* sm = reinterpret_cast<real*>(smem_raw);
+  real* sU = sm + TL::OFF_U;
+  real* su = sm + TL::OFF_PU;
+  real* sv = sm + TL::OFF_PV;
+  real* sp = sm + TL::OFF_PP;
+  real* sD = sm + TL::OFF_D;
+  real* sX = sm + TL::OFF_X;
+  double* red = reinterpret_cast<double*>(smem_raw + ((TL::ELEMS * sizeof(real) + 15) / 16) * 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_DOUBLES);
+  __shared__ GridParams<real> g;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARPS = NT / 32;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  unsigned parity = 0;
+  int cur_member = -1;
+
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int member = work ? work[w].member : 0;
+    const int tile = work ? work[w].tile : w;
+    if (member != cur_member) {
+      __syncthreads();
+      if (tid == 0) g = members[member];
+      __syncthreads();
+      cur_member = member;
+    }
+    const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+    const int x0 = tx * TX, y0 = ty * TY;
+    const long long fs = g.fstride;
+    const int pitch = g.pitch;
+
+    // ---- A. halo box -> shared memory (TMA bulk copies, one per field row)
+    if (warp == 0) {
+      if (lane == 0) mbar_arrive_expect_tx(bar, TL::BOX_BYTES);
+      __syncwarp();
+      for (int r = lane; r < NF * H; r += 32) {
+        const int f = r / H, row = r - f * H;
+        const real* src = g.win + f * fs + static_cast<long long>(y0 + row) * pitch + x0;
+        bulk_g2s(sU + r * W, src, W * sizeof(real), bar);
+      }
+    }
+
+    // stage scalars (overlap with the copies)
+    const real ax = g.alpha_in[0], ay = g.alpha_in[1];
+    double dtd;
+    if (ctl.stage == 0) {
+      dtd = g.dt_src ? *g.dt_src : g.cfl_delta / static_cast<double>(*g.smax);
+    } else {
+      dtd = *g.dt_cur;
+    }
+    if (tile == 0 && tid == 0 && ctl.mode == 0) {  // once per grid and stage
+      if (ctl.stage == 0) {
+        *g.dt_cur = dtd;
+        *g.t_acc += dtd;
+      }
+      if (ctl.stage == 1) {
+        *g.smax = real(0);
+        if (g.totals_reset)
+          for (int f = 0; f < 5; ++f) g.totals_reset[f] = 0.0;
+      }
+      if (g.alpha_zero) {
+        g.alpha_zero[0] = real(0);
+        g.alpha_zero[1] = real(0);
+      }
+      if (g.dt_log) {
+        const int idx = *g.log_count;
+        if (idx < g.log_cap) {
+          if (ctl.stage == 0) g.dt_log[idx] = dtd;
+          g.alpha_log[6 * idx + 2 * ctl.stage + 0] = static_cast<double>(ax);
+          g.alpha_log[6 * idx + 2 * ctl.stage + 1] = static_cast<double>(ay);
+        }
+        if (ctl.stage == 2) *g.log_count = idx + 1;
+      }
+    }
+
+    if (!mbar_wait_bounded(bar, parity)) {
+      atomicOr(g.err, ERR_TIMEOUT);
+      s_abort = 1;
+    }
+    parity ^= 1u;
+    __syncthreads();
+    if (s_abort) break;
+
+    // ---- B. primitive variables
+    const real gm1 = g.gm1;
+    for (int idx = tid; idx < H * W; idx += NT) {
+      const int row = idx / W, col = idx - row * W;
+      const bool irow = row >= 3 && row < TY + 3;
+      const bool icol = col >= 4 && col < TX + 4;
+      if (!irow && !icol) continue;
+      const real rho = sU[0 * H * W + idx];
+      const real mx = sU[1 * H * W + idx];
+      const real my = sU[2 * H * W + idx];
+      const real E = sU[3 * H * W + idx];
+      const real rr = T::rcp(rho);
+      const real u = mx * rr, v = my * rr;
+      const real kin = T::add_(T::mul_(mx, u), T::mul_(my, v));
+      sp[idx] = gm1 * T::fma_(real(-0.5), kin, E);
+      if (irow) su[(row - 3) * W + col] = u;
+      if (icol) sv[row * TX + (col - 4)] = v;
+    }
+    __syncthreads();
+
+    // ---- C. x pass: items (field, row, run)
+    {
+      const real halx = real(0.5) * ax, rdx = g.rdx;
+      constexpr int NITEMS = NF * TY * NQ;
+      for (int it = tid; it < NITEMS; it += NT) {
+        const int c = it / (TY * NQ);
+        const int rem = it - c * (TY * NQ);
+        const int row = (rem / (8 * NQ)) * 8 + (rem & 7);
+        const int q = (rem >> 3) % NQ;
+        const int srow = row + 3;
+        const int col0 = 4 + q * K - 3;  // first point of the run in the box
+        if (c < 4) {
+          const int kind = (c == 0) ? 0 : (c == 1) ? 1 : (c == 2) ? 2 : 3;
+          const real* Uc = sU + (c * H + srow) * W + col0;
+          const real* Xc = sU + (1 * H + srow) * W + col0;
+          hydro_line<real, K, 1>(Uc, Xc, su + row * W + col0, 1, sp + srow * W + col0, kind, halx, rdx,
+                                 sD + (c * TY + row) * TX + q * K, 1, false);
+        } else {
+          real* xm = sX + row * TX + q * K;
+          real* xp = sX + (TY + row) * TX + q * K;
+          phi_line<real, K, 1>(sU + (4 * H + srow) * W + col0, rdx, [&](int k, real dm, real dp) {
+            xm[k] = dm;
+            xp[k] = dp;
+          });
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- D. y pass: items (field, column, run)
+    {
+      const real haly = real(0.5) * ay, rdy = g.rdy;
+      const real sf = g.flame_speed;
+      constexpr int PER_C = 64 * NQY;  // 60 columns padded to 64 so no warp spans two fields
+      constexpr int NITEMS = NF * PER_C;
+      for (int it = tid; it < NITEMS; it += NT) {
+        const int c = it / PER_C;
+        const int rem = it - c * PER_C;
+        const int qy = rem >> 6;
+        const int col = rem & 63;
+        if (col >= TX) continue;
+        const int scol = col + 4;
+        const int row0 = qy * KY;  // first tile row of the run; points start 3 rows above
+        if (c < 4) {
+          const int kind = (c == 0) ? 0 : (c == 1) ? 2 : (c == 2) ? 1 : 3;
+          const real* Uc = sU + (c * H + row0) * W + scol;
+          const real* Xc = sU + (2 * H + row0) * W + scol;
+          hydro_line<real, KY, W>(Uc, Xc, sv + row0 * TX + col, TX, sp + row0 * W + scol, kind, haly, rdy,
+                                  sD + (c * TY + row0) * TX + col, TX, true);
+        } else {
+          phi_line<real, KY, W>(sU + (4 * H + row0) * W + scol, rdy, [&](int k, real ym, real yp) {
+            const int row = row0 + k;
+            const real xm = sX[row * TX + col], xp = sX[(TY + row) * TX + col];
+            const real u = su[row * W + scol], v = sv[(row + 3) * TX + col];
+            const real gx = real(0.5) * (xm + xp), gy = real(0.5) * (ym + yp);
+            const real adv = T::add_(T::mul_(u, gx), T::mul_(v, gy));
+            const real nrm = T::sqrt_(T::add_(T::mul_(gx, gx), T::mul_(gy, gy)));
+            const real H = T::fma_(-sf, nrm, adv);
+            const real axl = fabs(u) + sf, ayl = fabs(v) + sf;
+            const real diss = T::add_(T::mul_(real(0.5) * axl, xp - xm), T::mul_(real(0.5) * ayl, yp - ym));
+            sD[(4 * TY + row) * TX + col] = H - diss;
+          });
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
+    real amx = real(0), amy = real(0), smx = real(0);
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    {
+      const int nx = g.nx, ny = g.ny;
+      const real gamma = g.gamma, grav = g.gravity;
+      const bool rz = g.geometry == 1;
+      const real dt = static_cast<real>(dtd);
+      const real ra = static_cast<real>(ctl.rk_a), rb = static_cast<real>(ctl.rk_b);
+      const bool use_un = ctl.rk_a != 0.0 && ctl.mode == 0;
+      constexpr int NG = TX / 4;
+      for (int it = tid; it < TY * NG; it += NT) {
+        const int row = it / NG, g4 = it - row * NG;
+        const int j = y0 + row, ib = x0 + 4 * g4;
+        if (j >= ny || ib >= nx) continue;
+        const int nvalid = min(4, nx - ib);
+        const long long gbase = static_cast<long long>(j + GY) * pitch + ib + GX;
+        const int srow = row + 3, scol = 4 + 4 * g4, tcol = 4 * g4;
+        real o[NF][4];
+        {
+          real u4[4], v4[4], p4[4];
+          if (rz) {
+            load4(su + row * W + scol, u4);
+            load4(sv + srow * TX + tcol, v4);
+            load4(sp + srow * W + scol, p4);
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            real Uv[4], Dv[4], un[4];
+            load4(sU + (f * H + srow) * W + scol, Uv);
+            load4(sD + (f * TY + row) * TX + tcol, Dv);
+            if (use_un) {
+              if (nvalid == 4) {
+                load4(g.un + f * fs + gbase, un);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) un[e] = (e < nvalid) ? g.un[f * fs + gbase + e] : real(0);
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              real S = real(0);
+              if (f < 4 && rz) {  // -(1/r)(rho v_r, rho v_r^2, rho v_r v_z, (tau + p) v_r)
+                const real rinv = T::rcp(static_cast<real>(g.x0 + (ib + e + 0.5) * g.dx));
+                const real mr = sU[(1 * H + srow) * W + scol + e];
+                S = (f == 0) ? -mr * rinv
+                    : (f == 1) ? -(mr * u4[e]) * rinv
+                    : (f == 2) ? -(mr * v4[e]) * rinv
+                               : -((sU[(3 * H + srow) * W + scol + e] + p4[e]) * u4[e]) * rinv;
+              }
+              if (grav != real(0)) {  // -rho dPhi/dz, -rho v_z dPhi/dz with dPhi/dz = -g
+                if (f == 2) S = T::fma_(sU[(0 * H + srow) * W + scol + e], grav, S);
+                if (f == 3) S = T::fma_(sU[(2 * H + srow) * W + scol + e], grav, S);
+              }
+              const real L = (f < 4) ? (S - Dv[e]) : -Dv[e];
+              if (ctl.mode == 1) {
+                o[f][e] = L;
+              } else {
+                const real inner = rb * T::fma_(dt, L, Uv[e]);
+                o[f][e] = use_un ? T::fma_(ra, un[e], inner) : inner;
+              }
+            }
+          }
+        }
+        // stores
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          real* dstp = g.out + f * fs + gbase;
+          if (nvalid == 4) {
+            store4(dstp, o[f]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (e < nvalid) dstp[e] = o[f][e];
+          }
+        }
+        if (ctl.mode == 1) continue;
+        // ghost images and reductions
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (e >= nvalid) break;
+          const int i = ib + e;
+          if (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3) {
+            real val[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) val[f] = o[f][e];
+            write_ghost_images<real, NF>(g.out, fs, pitch, nx, ny, g.bc, i, j, val);
+          }
+          // speeds of the output state (next stage's alpha, next step's dt) and validity
+          const real rho = o[0][e], mx = o[1][e], my = o[2][e], E = o[3][e];
+          const real rr = T::rcp(rho);
+          const real u = mx * rr, v = my * rr;
+          const real p = gm1 * T::fma_(real(-0.5), T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
+          const real cs = T::sqrt_(gamma * p * rr);
+          bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) &&
+                    T::finite(cs);
+          if (NF == 5) ok = ok && T::finite(o[NF - 1][e]);
+          if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
+          const real au = fabs(u), av = fabs(v);
+          amx = fmax(amx, au + cs);
+          amy = fmax(amy, av + cs);
+          smx = fmax(smx, T::add_(cs, T::add_(au, av)));
+          if (g.totals) {
+            const double dV = rz ? 6.283185307179586 * (g.x0 + (i + 0.5) * g.dx) * g.dx * g.dy : g.dx * g.dy;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) tot[f] = fma(static_cast<double>(o[f][e]), dV, tot[f]);
+          }
+        }
+      }
+    }
+
+    // block reductions: maxima (next alpha / dt) and FP64 totals, one atomic per tile and slot
+    if (ctl.mode == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        amx = fmax(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+        amy = fmax(amy, __shfl_xor_sync(0xffffffffu, amy, o));
+        smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
+      }
+      const bool want_tot = g.totals != nullptr;
+      if (want_tot) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) tot[f] += __shfl_xor_sync(0xffffffffu, tot[f], o);
+      }
+      if (lane == 0) {
+        red[warp * 8 + 0] = static_cast<double>(amx);
+        red[warp * 8 + 1] = static_cast<double>(amy);
+        red[warp * 8 + 2] = static_cast<double>(smx);
+        if (want_tot)
+          for (int f = 0; f < NF; ++f) red[warp * 8 + 3 + f] = tot[f];
+      }
+      __syncthreads();
+      if (tid < 8) {
+        double acc = (tid < 3) ? 0.0 : 0.0;
+        for (int wi = 0; wi < NWARPS; ++wi) {
+          const double v = red[wi * 8 + tid];
+          acc = (tid < 3) ? fmax(acc, v) : acc + v;
+        }
+        if (tid == 0 && g.alpha_out) T::atomic_max(&g.alpha_out[0], static_cast<real>(acc));
+        if (tid == 1 && g.alpha_out) T::atomic_max(&g.alpha_out[1], static_cast<real>(acc));
+        if (tid == 2 && ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(acc));
+        if (tid >= 3 && tid < 3 + NF && want_tot) atomicAdd(&g.totals[tid - 3], acc);
+      }
+    }
+    // the next copy overwrites the box: everyone is done reading it (generic proxy) before TMA writes
+    __syncthreads();
+    fence_proxy_async_smem();
+  }
+}
+
+}  // namespace hydro

@@ -1,0 +1,276 @@
+"""GPU parity of the CUDA stage kernels against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (spec bar): FP64 relative L-inf <= 1e-12 per field; FP32 relative L1 (sum |diff| /
+sum |ref| per field) <= 1e-5 on smooth data and <= 1e-4 with shocks.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_08549_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_SMOOTH = 1e-5
+F32_SHOCK = 1e-4
+
+
+def _hydro():
+    from paper_1507_08549_gb300 import hydro
+    return hydro
+
+
+def rel_linf(a, b):
+    return max(np.abs(a[f] - b[f]).max() / max(np.abs(b[f]).max(), 1e-300) for f in range(b.shape[0]))
+
+
+def rel_l1(a, b):
+    return max(np.abs(a[f] - b[f]).sum() / max(np.abs(b[f]).sum(), 1e-300) for f in range(b.shape[0]))
+
+
+def run_gpu(prob, nsteps, dtype="f64", variant=None, U0=None):
+    h = _hydro().Hydro(prob, dtype=dtype)
+    if variant is not None:
+        h.set_tile_variant(variant)
+    U = h.state(prob.U0 if U0 is None else U0)
+    t, dtl = h.step(U, nsteps)
+    out = U.double().cpu().numpy()
+    h.close()
+    return out, t, dtl
+
+
+# ------------------------------------------------------------------------------ the five configs
+
+def test_config1_advected_wave_fp64_matches_oracle():
+    """128^2 periodic advected wave, FP64, 100 steps (the plain-method configuration)."""
+    prob = wl.advected_wave(128)
+    got, t, dtl = run_gpu(prob, 100, "f64")
+    ref, t_ref, dt_ref = oracle.step(prob, prob.U0, 100)
+    assert rel_linf(got, ref) <= F64_TOL
+    assert abs(t - t_ref) <= 1e-13 * t_ref and abs(dtl - dt_ref) <= 1e-13 * dt_ref
+
+
+def test_config1_advected_wave_fp32_l1():
+    prob = wl.advected_wave(128)
+    got, t, _ = run_gpu(prob, 100, "f32")
+    ref, t_ref, _ = oracle.step(prob, prob.U0, 100)
+    assert rel_l1(got, ref) <= F32_SMOOTH
+    assert abs(t - t_ref) <= 1e-5 * t_ref
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_ragged_grid_all_boundaries_all_variants(variant):
+    """A grid that is not a multiple of the tile (several tiles and ragged tails in x and y), with
+    reflecting, transmissive and periodic faces, the level set, and gravity."""
+    n0 = 131
+    prob = wl.explosion(n0).with_(nx=131, ny=77)
+    x = wl.centres(131, 0, 1.5)
+    y = wl.centres(77, 0, 1.5)
+    X, Y = np.meshgrid(x, y)
+    inside = (X - 0.3) ** 2 + (Y - 0.5) ** 2 < 0.09
+    U0 = wl.conserved(1.4, np.where(inside, 1.0, 0.125), 0.1, -0.05, np.where(inside, 1.0, 0.1),
+                      0.3 - np.sqrt((X - 0.3) ** 2 + (Y - 0.5) ** 2))
+    prob = prob.with_(nfields=5, flame_speed=0.05, gravity=-0.5, y1=1.5 * 77 / 131,
+                      bc=(wl.REFLECT, wl.TRANSMISSIVE, wl.PERIODIC, wl.PERIODIC), U0=U0)
+    got, _, _ = run_gpu(prob, 12, "f64", variant=variant)
+    ref, _, _ = oracle.step(prob, prob.U0, 12)
+    assert rel_linf(got, ref) <= F64_TOL
+
+
+def test_config2_rayleigh_taylor_reduced_fp64_and_fp32():
+    """(r,z) axisymmetric Rayleigh-Taylor with gravity and the level set, at 128x256 for 40 steps."""
+    prob = wl.rayleigh_taylor(128, 256, nsteps=40)
+    got, t, _ = run_gpu(prob, 40, "f64")
+    ref, t_ref, _ = oracle.step(prob, prob.U0, 40)
+    assert rel_linf(got, ref) <= F64_TOL
+    got32, _, _ = run_gpu(prob, 40, "f32")
+    assert rel_l1(got32, ref) <= F32_SHOCK
+
+
+def test_config2_rayleigh_taylor_full_size_first_steps():
+    """Full 1024 x 2048 grid, the launch configuration the benchmark uses, 2 steps in FP64 against
+    the oracle on the whole grid."""
+    prob = wl.rayleigh_taylor(1024, 2048)
+    got, t, _ = run_gpu(prob, 2, "f64")
+    ref, t_ref, _ = oracle.step(prob, prob.U0, 2)
+    assert rel_linf(got, ref) <= F64_TOL
+    assert abs(t - t_ref) <= 1e-13 * t_ref
+
+
+def test_shock_tubes_fp64_and_fp32():
+    for test in (1, 3, 4):
+        prob = wl.shock_tube(test, nx=400, ny=3)
+        got, _, _ = run_gpu(prob, 60, "f64")
+        ref, _, _ = oracle.step(prob, prob.U0, 60)
+        assert rel_linf(got, ref) <= F64_TOL, test
+        got32, _, _ = run_gpu(prob, 60, "f32")
+        assert rel_l1(got32, ref) <= F32_SHOCK, test
+
+
+def test_config5_full_size_windows_against_oracle():
+    """8192^2, 5 fields, FP32: the global alpha and dt of step 1 against the oracle on the whole grid,
+    and the state after one step on sampled windows: the oracle steps each window with a 9-cell margin
+    (the domain of dependence of one RK3 step) using the global alpha / dt, and the window interior is
+    compared."""
+    hydro = _hydro()
+    prob = wl.blobs_blast(8192)
+    h = hydro.Hydro(prob, dtype="f32")
+    h.record(4)
+    U = h.state(prob.U0)
+    h.step(U, 1)
+    dtl, al = h.get_log()
+    got = U.cpu().numpy()
+    h.close()
+    ax, ay = oracle.alpha(prob, prob.U0)
+    dt_ref = oracle.dt(prob, prob.U0)
+    assert abs(al[0, 0, 0] - ax) <= 1e-6 * ax and abs(al[0, 0, 1] - ay) <= 1e-6 * ay
+    assert abs(dtl[0] - dt_ref) <= 1e-6 * dt_ref
+    rng = np.random.default_rng(7)
+    m, w = 9, 96
+    centres = [(4096 - w // 2, 4096 - w // 2)] + [tuple(rng.integers(m, 8192 - w - m, 2)) for _ in range(3)]
+    for (j0, i0) in centres:
+        sub = prob.U0[:, j0 - m:j0 + w + m, i0 - m:i0 + w + m]
+        win = prob.with_(nx=w + 2 * m, ny=w + 2 * m, bc=(wl.TRANSMISSIVE,) * 4, x1=prob.x0 + (w + 2 * m) * prob.dx,
+                         y1=prob.y0 + (w + 2 * m) * prob.dy)
+        # frozen at the oracle's own global alpha (stage 1) and the GPU-logged later-stage alphas
+        a6 = np.array([[ax, ay], al[0, 1], al[0, 2]])
+        ref = oracle.step_frozen(win, sub, [dt_ref], a6.reshape(1, 3, 2))
+        cut = ref[:, m:-m, m:-m]
+        g = got[:, j0:j0 + w, i0:i0 + w]
+        assert rel_l1(g, cut) <= F32_SHOCK
+
+
+# ------------------------------------------------------------------------------ the spatial operator
+
+@pytest.mark.parametrize("case", ["periodic", "rz_axis_gravity_phi", "reflect_transmissive"])
+def test_rhs_operator_fp64(case):
+    rng = np.random.default_rng(3)
+    nx, ny = 67, 45
+    X, Y = np.meshgrid(wl.centres(nx, 0, 1), wl.centres(ny, 0, 1))
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y) + 0.05 * rng.random((ny, nx))
+    u = 0.3 * np.cos(2 * np.pi * Y)
+    v = -0.2 * np.sin(2 * np.pi * X)
+    p = 1.0 + 0.2 * rng.random((ny, nx))
+    phi = 0.25 - np.hypot(X - 0.4, Y - 0.6)
+    base = wl.Problem(name="rhs", nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4)
+    if case == "periodic":
+        prob = base.with_(U0=wl.conserved(1.4, rho, u, v, p))
+    elif case == "rz_axis_gravity_phi":
+        prob = base.with_(geometry=1, gravity=-0.7, nfields=5, flame_speed=0.1,
+                          bc=(wl.AXIS, wl.TRANSMISSIVE, wl.REFLECT, wl.TRANSMISSIVE),
+                          U0=wl.conserved(1.4, rho, u, v, p, phi))
+    else:
+        prob = base.with_(nfields=5, flame_speed=0.02, bc=(wl.REFLECT, wl.TRANSMISSIVE, wl.TRANSMISSIVE, wl.REFLECT),
+                          U0=wl.conserved(1.4, rho, u, v, p, phi))
+    ax, ay = oracle.alpha(prob, prob.U0)
+    ref = oracle.rhs(prob, prob.U0, ax, ay)
+    h = _hydro().Hydro(prob, dtype="f64")
+    L = h.rhs(h.state(prob.U0), ax, ay).cpu().numpy()
+    h.close()
+    scale = max(np.abs(ref).max(), 1.0)
+    assert np.abs(L - ref).max() <= 1e-11 * scale
+
+
+# ------------------------------------------------------------------------------ properties
+
+def test_periodic_conservation_on_gpu_fp64():
+    prob = wl.advected_wave(96)
+    hydro = _hydro()
+    h = hydro.Hydro(prob, dtype="f64")
+    U = h.state(prob.U0)
+    m0 = h.totals(U)
+    h.step(U, 50)
+    m1 = h.totals(U)
+    fused = h.last_totals()
+    h.close()
+    ref0 = oracle.totals(prob, prob.U0)
+    np.testing.assert_allclose(m0, ref0, rtol=1e-14, atol=1e-300)
+    for f in range(4):
+        assert abs(m1[f] - m0[f]) <= 1e-13 * abs(m0[f])
+        assert abs(fused[f] - m1[f]) <= 1e-13 * abs(m1[f])
+
+
+def test_blast_mirror_symmetry_on_gpu():
+    prob = wl.blast(60, 90)
+    for dt in ("f64", "f32"):
+        U, _, _ = run_gpu(prob, 20, dt)
+        assert np.array_equal(U[0], U[0, :, ::-1]) and np.array_equal(U[0], U[0, ::-1, :]), dt
+        assert np.array_equal(U[1], -U[1, :, ::-1]) and np.array_equal(U[2], -U[2, ::-1, :]), dt
+
+
+def test_explosion_diagonal_symmetry_on_gpu():
+    prob = wl.explosion(64)
+    for dt in ("f64", "f32"):
+        U, _, _ = run_gpu(prob, 20, dt)
+        assert np.array_equal(U[0], U[0].T) and np.array_equal(U[1], U[2].T), dt
+
+
+def test_tile_variants_agree_bitwise_and_autotune():
+    hydro = _hydro()
+    prob = wl.kelvin_helmholtz(96)
+    outs = []
+    for v in range(3):
+        U, _, _ = run_gpu(prob, 10, "f32", variant=v)
+        outs.append(U)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    h = hydro.Hydro(prob, dtype="f32")
+    U = h.state(prob.U0)
+    ms = h.autotune(U, steps=2)
+    n, cur = h.tile_variants()
+    assert ms[cur] == ms[ms > 0].min()
+    assert np.array_equal(U.cpu().numpy(), prob.U0.astype(np.float32))  # autotune leaves U untouched
+    h.close()
+
+
+def test_frozen_replay_reproduces_the_run_and_host_entry():
+    hydro = _hydro()
+    prob = wl.kelvin_helmholtz(64)
+    h = hydro.Hydro(prob, dtype="f64")
+    h.record(20)
+    U = h.state(prob.U0)
+    t, _ = h.step(U, 8)
+    dtl, al = h.get_log()
+    assert len(dtl) == 8 and abs(dtl.sum() - t) <= 1e-15 * t
+    V = h.state(prob.U0)
+    h.step_frozen(V, dtl, al)
+    assert np.array_equal(U.cpu().numpy(), V.cpu().numpy())
+    Uh = np.ascontiguousarray(prob.U0)
+    th, _ = h.step_host(Uh, 8)
+    assert np.array_equal(Uh, U.cpu().numpy()) and th == t
+    h.close()
+
+
+def test_nonphysical_state_is_reported():
+    hydro = _hydro()
+    prob = wl.advected_wave(32)
+    U0 = prob.U0.copy()
+    U0[3, 10, 10] = -5.0
+    h = hydro.Hydro(prob, dtype="f64")
+    with pytest.raises(hydro.HydroError) as ei:
+        h.step(h.state(U0), 1)
+    assert ei.value.code == hydro.ENONPHYSICAL
+    # the context stays usable
+    U = h.state(prob.U0)
+    h.step(U, 1)
+    h.close()
+
+
+# ------------------------------------------------------------------------------ batched ensemble
+
+def test_batched_ensemble_matches_member_runs():
+    hydro = _hydro()
+    members = wl.quadrant_ensemble(6, sizes=(64, 96, 131))
+    nsteps = 15
+    for dt, tol, fn in (("f64", F64_TOL, rel_linf), ("f32", F32_SHOCK, rel_l1)):
+        hs = [hydro.Hydro(p, dtype=dt) for p in members]
+        Us = [h.state(p.U0) for h, p in zip(hs, members)]
+        t = hydro.hydro_batch_step(hs, Us, nsteps)
+        for p, U, tm in zip(members, Us, t):
+            ref, t_ref, _ = oracle.step(p, p.U0, nsteps)
+            assert fn(U.double().cpu().numpy(), ref) <= tol, (dt, p.name)
+            assert abs(tm - t_ref) <= (1e-13 if dt == "f64" else 1e-5) * t_ref
+        for h in hs:
+            h.close()

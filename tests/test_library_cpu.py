@@ -1,0 +1,59 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads without a GPU, and exports every
+entry point include/hydro.h declares; plus host-only argument validation that needs no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hydro.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"^\s*(?:[A-Za-z_][\w ]*?[\s\*]+)?(\w+)\s*\(", src, flags=re.M))
+    return {n for n in names if n.startswith("hydro_") or n == "conserved_totals"}
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("hydro_init", "hydro_step", "hydro_adjoint_step", "hydro_batch_step", "conserved_totals",
+              "hydro_last_error", "hydro_destroy"):
+        assert n in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1507_08549_gb300 import build, hydro
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(hydro.EXPORTS) == _declared()
+
+
+def test_init_rejects_bad_configs_without_touching_the_device():
+    """Configuration errors are found on the host before any CUDA call."""
+    from paper_1507_08549_gb300 import hydro, workloads
+    lib = hydro.load()
+    good = workloads.advected_wave(16)
+    bad = [
+        good.with_(nx=2),
+        good.with_(nfields=3),
+        good.with_(bc=(hydro.BC_PERIODIC, hydro.BC_TRANSMISSIVE, 0, 0)),
+        good.with_(bc=(hydro.BC_AXIS, hydro.BC_TRANSMISSIVE, 0, 0)),
+        good.with_(gamma=1.0),
+        good.with_(cfl=0.0),
+    ]
+    for p in bad:
+        cfg = hydro.make_config(p, hydro.HYDRO_F32)
+        ctx = ctypes.c_void_p()
+        assert lib.hydro_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == hydro.EINVAL
+        assert not ctx.value
+    cfg = hydro.make_config(good, 7)
+    ctx = ctypes.c_void_p()
+    assert lib.hydro_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == hydro.EINVAL
+    assert lib.hydro_init(None, None, ctypes.byref(ctx)) == hydro.EINVAL
+    assert lib.hydro_step(None, None, 1, None, None) == hydro.EINVAL
+    lib.hydro_destroy(None)
+    assert lib.hydro_last_error(None) == b"null context"
