@@ -72,6 +72,7 @@ def _load():
         lib.orc_weno5.argtypes = [ctypes.c_double] * 5
         lib.orc_weno5.restype = ctypes.c_double
         lib.orc_weno5_weights.argtypes = [ctypes.c_double] * 5 + [dp]
+        lib.orc_weno5_grad.argtypes = [ctypes.c_double] * 5 + [dp]
         lib.orc_alpha.argtypes = [cp, dp, dp, dp]
         lib.orc_max_speed.argtypes = [cp, dp, dp]
         lib.orc_dt.argtypes = [cp, dp, dp]
@@ -135,6 +136,12 @@ def weno5_weights(a, b, c, d, e) -> np.ndarray:
     w = np.zeros(3)
     _load().orc_weno5_weights(float(a), float(b), float(c), float(d), float(e), _ptr(w))
     return w
+
+
+def weno5_grad(a, b, c, d, e) -> np.ndarray:
+    g = np.zeros(5)
+    _load().orc_weno5_grad(float(a), float(b), float(c), float(d), float(e), _ptr(g))
+    return g
 
 
 def alpha(p, U):

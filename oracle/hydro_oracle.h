@@ -41,6 +41,8 @@ int orc_get_threads(void);
 /* WENO5-JS reconstruction at the right face of c from the left-biased list (a,b,c,d,e). */
 double orc_weno5(double a, double b, double c, double d, double e);
 void orc_weno5_weights(double a, double b, double c, double d, double e, double w[3]);
+/* Gradient of orc_weno5 with respect to its five arguments. */
+void orc_weno5_grad(double a, double b, double c, double d, double e, double g[5]);
 
 /* Global Lax-Friedrichs speeds of a state: max |u|+c and max |v|+c over interior cells. */
 int orc_alpha(const orc_config* c, const double* U, double* ax, double* ay);

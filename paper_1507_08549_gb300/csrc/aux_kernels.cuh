@@ -27,16 +27,11 @@ __global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, G
     if (i < 3 || i >= g.nx - 3 || j < 3 || j >= g.ny - 3)
       write_ghost_images<real, NF>(g.out, g.fstride, g.pitch, g.nx, g.ny, g.bc, i, j, val);
     const real rho = val[0], mx = val[1], my = val[2], E = val[3];
-    const real rr = T::rcp(rho);
-    const real u = mx * rr, v = my * rr;
-    const real p = g.gm1 * T::fma_(real(-0.5), T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
-    const real cs = T::sqrt_(g.gamma * p * rr);
-    bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) && T::finite(cs);
+    real p;
+    Ar<real>::speeds(rho, mx, my, E, g.gamma, g.gm1, p, amx, amy, smx);
+    bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) && T::finite(smx);
     if (NF == 5) ok = ok && T::finite(val[NF - 1]);
     if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
-    amx = fabs(u) + cs;
-    amy = fabs(v) + cs;
-    smx = T::add_(cs, T::add_(fabs(u), fabs(v)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

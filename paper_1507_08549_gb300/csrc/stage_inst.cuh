@@ -12,8 +12,12 @@ struct VariantLaunch {
   static constexpr int TY = VARIANTS[V].ty, NT = VARIANTS[V].threads;
   static constexpr size_t SMEM = Tile<real, NF, TY>::BYTES;
   static cudaError_t configure() {
-    static cudaError_t once = cudaFuncSetAttribute(stage_kernel<real, NF, TY, NT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    static cudaError_t once = [] {
+      cudaError_t e = cudaFuncSetAttribute(stage_kernel<real, NF, TY, NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+      if (e != cudaSuccess) (void)cudaGetLastError();  // a variant too large for the device: not sticky
+      return e;
+    }();
     return once;
   }
   static cudaError_t launch(const GridParams<real>* m, const WorkItem* w, int nwork, const StageCtl& ctl, int grid,

@@ -151,50 +151,199 @@ __device__ __forceinline__ real weno_side(real a, real b, real c, real d, real e
   return num * T::rcp(den);
 }
 
+// ------------------------------------------------------------------------------ arithmetic policy
+//
+// FP32 (the throughput path): fused multiply-adds, approximate reciprocals, smoothness indicators
+// shared between the faces that use the same point triplet.
+// FP64: every operation of the update is the one the plain definition writes, in its order, rounded
+// once (explicit _rn intrinsics, so nothing is contracted or reordered): the same IEEE operations as a
+// straightforward sequential implementation of Eq. euler2D / Sec. 2.2, so FP64 results are
+// reproducible bit for bit by such an implementation.
+template <typename real>
+struct Ar;
+
+template <>
+struct Ar<float> {
+  static constexpr bool kExact = false;
+  using T = RT<float>;
+  static __device__ __forceinline__ void prims(float rho, float mx, float my, float E, float gm1, float& u,
+                                               float& v, float& p) {
+    const float rr = T::rcp(rho);
+    u = mx * rr;
+    v = my * rr;
+    p = gm1 * T::fma_(-0.5f, T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
+  }
+  static __device__ __forceinline__ float flux(int kind, float uu, float X, float vn, float p) {
+    return kind == 0 ? X : (kind == 1) ? T::fma_(uu, vn, p) : (kind == 2) ? T::mul_(uu, vn) : T::mul_(uu + p, vn);
+  }
+  static __device__ __forceinline__ void split(float F, float uu, float alpha, float& fp, float& fm) {
+    const float hF = 0.5f * F, hal = 0.5f * alpha;
+    fp = T::fma_(hal, uu, hF);
+    fm = T::fma_(-hal, uu, hF);
+  }
+  static __device__ __forceinline__ float divided(float a, float b, float rd, double) { return T::mul_(a - b, rd); }
+  static __device__ __forceinline__ float sum(float a, float b) { return T::add_(a, b); }
+  // L = -(dF + dG) + S and the RK blend a U^n + b (W + dt L)
+  static __device__ __forceinline__ float blend(bool use_un, float ra, float rb, float un, float w, float dt,
+                                                float L) {
+    const float inner = rb * T::fma_(dt, L, w);
+    return use_un ? T::fma_(ra, un, inner) : inner;
+  }
+  static __device__ __forceinline__ float source(int f, bool rz, float grav, float rho, float mr, float mz, float E,
+                                                float u, float v, float p, double x0, int i, double dx) {
+    float S = 0.0f;
+    if (rz) {  // -(1/r)(rho v_r, rho v_r^2, rho v_r v_z, (tau + p) v_r)
+      const float rinv = T::rcp(static_cast<float>(x0 + (i + 0.5) * dx));
+      S = (f == 0) ? -mr * rinv : (f == 1) ? -(mr * u) * rinv : (f == 2) ? -(mr * v) * rinv : -((E + p) * u) * rinv;
+    }
+    if (f == 2) S = T::fma_(rho, grav, S);  // -rho dPhi/dz with dPhi/dz = -g
+    if (f == 3) S = T::fma_(mz, grav, S);   // -rho v_z dPhi/dz
+    return S;
+  }
+  static __device__ __forceinline__ float lval(float D, float S) { return S - D; }
+  static __device__ __forceinline__ float hamiltonian(float u, float v, float sf, float xm, float xp, float ym,
+                                                     float yp) {
+    const float gx = 0.5f * (xm + xp), gy = 0.5f * (ym + yp);
+    const float adv = T::add_(T::mul_(u, gx), T::mul_(v, gy));
+    const float nrm = T::sqrt_(T::add_(T::mul_(gx, gx), T::mul_(gy, gy)));
+    const float H = T::fma_(-sf, nrm, adv);
+    const float axl = fabsf(u) + sf, ayl = fabsf(v) + sf;
+    return H - T::add_(T::mul_(0.5f * axl, xp - xm), T::mul_(0.5f * ayl, yp - ym));
+  }
+  // sound speed and the three signal speeds |u|+c, |v|+c, c+|u|+|v|
+  static __device__ __forceinline__ void speeds(float rho, float mx, float my, float E, float gamma, float gm1,
+                                                float& p, float& ax, float& ay, float& sm) {
+    float u, v;
+    prims(rho, mx, my, E, gm1, u, v, p);
+    const float cs = T::sqrt_(gamma * p * T::rcp(rho));
+    const float au = fabsf(u), av = fabsf(v);
+    ax = au + cs;
+    ay = av + cs;
+    sm = T::add_(cs, T::add_(au, av));
+  }
+};
+
+template <>
+struct Ar<double> {
+  static constexpr bool kExact = true;
+  static __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ void prims(double rho, double mx, double my, double E, double gm1, double& u,
+                                               double& v, double& p) {
+    u = dv(mx, rho);
+    v = dv(my, rho);
+    p = ml(gm1, sb(E, ml(0.5, ad(ml(mx, u), ml(my, v)))));
+  }
+  static __device__ __forceinline__ double flux(int kind, double uu, double X, double vn, double p) {
+    return kind == 0 ? X : (kind == 1) ? ad(ml(uu, vn), p) : (kind == 2) ? ml(uu, vn) : ml(ad(uu, p), vn);
+  }
+  static __device__ __forceinline__ void split(double F, double uu, double alpha, double& fp, double& fm) {
+    fp = ml(0.5, ad(F, ml(alpha, uu)));
+    fm = ml(0.5, sb(F, ml(alpha, uu)));
+  }
+  static __device__ __forceinline__ double divided(double a, double b, double, double h) { return dv(sb(a, b), h); }
+  static __device__ __forceinline__ double sum(double a, double b) { return ad(a, b); }
+  static __device__ __forceinline__ double blend(bool use_un, double ra, double rb, double un, double w, double dt,
+                                                 double L) {
+    const double inner = ml(rb, ad(w, ml(dt, L)));
+    return use_un ? ad(ml(ra, un), inner) : inner;
+  }
+  static __device__ __forceinline__ double source(int f, bool rz, double grav, double rho, double mr, double mz,
+                                                 double E, double u, double v, double p, double x0, int i,
+                                                 double dx) {
+    double S = 0.0;
+    if (rz) {
+      const double r = ad(x0, ml(i + 0.5, dx));
+      S = (f == 0) ? dv(-mr, r) : (f == 1) ? dv(-ml(mr, u), r) : (f == 2) ? dv(-ml(mr, v), r) : dv(-ml(ad(E, p), u), r);
+    }
+    if (grav != 0.0) {
+      if (f == 2) S = ad(S, ml(rho, grav));
+      if (f == 3) S = ad(S, ml(mz, grav));
+    }
+    return S;
+  }
+  static __device__ __forceinline__ double lval(double D, double S) { return ad(-D, S); }
+  static __device__ __forceinline__ double hamiltonian(double u, double v, double sf, double xm, double xp, double ym,
+                                                       double yp) {
+    const double gx = ml(0.5, ad(xm, xp)), gy = ml(0.5, ad(ym, yp));
+    const double H = sb(ad(ml(u, gx), ml(v, gy)), ml(sf, __dsqrt_rn(ad(ml(gx, gx), ml(gy, gy)))));
+    const double axl = ad(fabs(u), sf), ayl = ad(fabs(v), sf);
+    return sb(H, ad(ml(ml(0.5, axl), sb(xp, xm)), ml(ml(0.5, ayl), sb(yp, ym))));
+  }
+  static __device__ __forceinline__ void speeds(double rho, double mx, double my, double E, double gamma,
+                                                double gm1, double& p, double& ax, double& ay, double& sm) {
+    double u, v;
+    prims(rho, mx, my, E, gm1, u, v, p);
+    const double cs = __dsqrt_rn(dv(ml(gamma, p), rho));
+    ax = ad(fabs(u), cs);
+    ay = ad(fabs(v), cs);
+    sm = ad(ad(cs, fabs(u)), fabs(v));
+  }
+  // WENO5-JS in the textbook order (candidate values, smoothness indicators, normalised weights).
+  static __device__ __forceinline__ double weno5(double a, double b, double c, double d, double e) {
+    const double q0 = dv(ad(sb(ml(2.0, a), ml(7.0, b)), ml(11.0, c)), 6.0);
+    const double q1 = dv(ad(ad(-b, ml(5.0, c)), ml(2.0, d)), 6.0);
+    const double q2 = dv(sb(ad(ml(2.0, c), ml(5.0, d)), e), 6.0);
+    const double k13 = 13.0 / 12.0;
+    const double s0 = ad(sb(a, ml(2.0, b)), c), t0 = ad(sb(a, ml(4.0, b)), ml(3.0, c));
+    const double s1 = ad(sb(b, ml(2.0, c)), d), t1 = sb(b, d);
+    const double s2 = ad(sb(c, ml(2.0, d)), e), t2 = ad(sb(ml(3.0, c), ml(4.0, d)), e);
+    const double b0 = ad(ml(ml(k13, s0), s0), ml(ml(0.25, t0), t0));
+    const double b1 = ad(ml(ml(k13, s1), s1), ml(ml(0.25, t1), t1));
+    const double b2 = ad(ml(ml(k13, s2), s2), ml(ml(0.25, t2), t2));
+    const double e0 = ad(1e-6, b0), e1 = ad(1e-6, b1), e2 = ad(1e-6, b2);
+    const double a0 = dv(0.1, ml(e0, e0)), a1 = dv(0.6, ml(e1, e1)), a2 = dv(0.3, ml(e2, e2));
+    const double s = ad(ad(a0, a1), a2);
+    return ad(ad(ml(dv(a0, s), q0), ml(dv(a1, s), q1)), ml(dv(a2, s), q2));
+  }
+};
+
 // Flux kinds along a direction: 0 mass (flux = normal momentum), 1 normal momentum (m_n v_n + p),
 // 2 tangential momentum (m_t v_n), 3 energy ((tau + p) v_n).
 //
 // One line of K cells: points m = 0 .. K+5 (cells -3 .. K+2 of the run), faces f = 0 .. K (left face
-// of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1.
+// of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1, where
+// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased).
 template <typename real, int K, int S>
 __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
                                            const real* __restrict__ vel, int vstride,
-                                           const real* __restrict__ pr, int kind, real hal, real rd,
+                                           const real* __restrict__ pr, int kind, real alpha, real rd, double h,
                                            real* __restrict__ dst, int dstride, bool accumulate) {
-  using T = RT<real>;
+  using A = Ar<real>;
   real fp[K + 6], fm[K + 6];
   B3<real> bp[K + 6], bm[K + 6];
   real fh_prev = real(0);
 #pragma unroll
   for (int m = 0; m < K + 6; ++m) {
     const real uu = Uc[m * S];
-    real F;
-    if (kind == 0) {
-      F = Xc[m * S];
-    } else {
-      const real vn = vel[m * vstride];
-      const real p = pr[m * S];
-      F = (kind == 1) ? T::fma_(uu, vn, p) : (kind == 2) ? uu * vn : (uu + p) * vn;
-    }
-    const real hF = real(0.5) * F;
-    fp[m] = T::fma_(hal, uu, hF);
-    fm[m] = T::fma_(-hal, uu, hF);
-    if (m >= 2) {
-      const int j = m - 1;
-      if (j <= K + 3) bp[j] = betas(fp[j - 1], fp[j], fp[j + 1]);
-      if (j >= 2) bm[j] = betas(fm[j - 1], fm[j], fm[j + 1]);
+    const real F = kind == 0 ? A::flux(0, uu, Xc[m * S], real(0), real(0))
+                             : A::flux(kind, uu, real(0), vel[m * vstride], pr[m * S]);
+    A::split(F, uu, alpha, fp[m], fm[m]);
+    if constexpr (!A::kExact) {
+      if (m >= 2) {
+        const int j = m - 1;
+        if (j <= K + 3) bp[j] = betas(fp[j - 1], fp[j], fp[j + 1]);
+        if (j >= 2) bm[j] = betas(fm[j - 1], fm[j], fm[j + 1]);
+      }
     }
     if (m >= 5) {
       const int f = m - 5;
-      const real plus = weno_side(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4], bp[f + 1].m, bp[f + 2].t,
-                                  bp[f + 3].p);
-      const real minus = weno_side(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1], bm[f + 4].p,
-                                   bm[f + 3].t, bm[f + 2].m);
-      const real fh = plus + minus;
+      real plus, minus;
+      if constexpr (A::kExact) {
+        plus = A::weno5(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4]);
+        minus = A::weno5(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1]);
+      } else {
+        plus = weno_side(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4], bp[f + 1].m, bp[f + 2].t, bp[f + 3].p);
+        minus = weno_side(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1], bm[f + 4].p, bm[f + 3].t,
+                          bm[f + 2].m);
+      }
+      const real fh = A::sum(plus, minus);
       if (f >= 1) {
-        const real d = (fh - fh_prev) * rd;
+        const real d = A::divided(fh, fh_prev, rd, h);
         real* o = dst + (f - 1) * dstride;
-        *o = accumulate ? (*o + d) : d;
+        *o = accumulate ? A::sum(*o, d) : d;
       }
       fh_prev = fh;
     }
@@ -205,21 +354,29 @@ __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const re
 // m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
 // phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}). emit(k, phi^-, phi^+).
 template <typename real, int K, int S, typename Emit>
-__device__ __forceinline__ void phi_line(const real* __restrict__ ph, real rd, Emit emit) {
+__device__ __forceinline__ void phi_line(const real* __restrict__ ph, real rd, double h, Emit emit) {
+  using A = Ar<real>;
   real d[K + 5];
   B3<real> b[K + 5];
   real prev = ph[0];
 #pragma unroll
   for (int n = 0; n < K + 5; ++n) {
     const real nxt = ph[(n + 1) * S];
-    d[n] = (nxt - prev) * rd;
+    d[n] = A::divided(nxt, prev, rd, h);
     prev = nxt;
-    if (n >= 2) b[n - 1] = betas(d[n - 2], d[n - 1], d[n]);
+    if constexpr (!A::kExact) {
+      if (n >= 2) b[n - 1] = betas(d[n - 2], d[n - 1], d[n]);
+    }
     if (n >= 5) {
       const int k = n - 5;
-      const real dm = weno_side(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4], b[k + 1].m, b[k + 2].t, b[k + 3].p);
-      const real dp = weno_side(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1], b[k + 4].p, b[k + 3].t,
-                                b[k + 2].m);
+      real dm, dp;
+      if constexpr (A::kExact) {
+        dm = A::weno5(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4]);
+        dp = A::weno5(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1]);
+      } else {
+        dm = weno_side(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4], b[k + 1].m, b[k + 2].t, b[k + 3].p);
+        dp = weno_side(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1], b[k + 4].p, b[k + 3].t, b[k + 2].m);
+      }
       emit(k, dm, dp);
     }
   }
@@ -434,10 +591,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real mx = sU[1 * H * W + idx];
       const real my = sU[2 * H * W + idx];
       const real E = sU[3 * H * W + idx];
-      const real rr = T::rcp(rho);
-      const real u = mx * rr, v = my * rr;
-      const real kin = T::add_(T::mul_(mx, u), T::mul_(my, v));
-      sp[idx] = gm1 * T::fma_(real(-0.5), kin, E);
+      real u, v, p;
+      Ar<real>::prims(rho, mx, my, E, gm1, u, v, p);
+      sp[idx] = p;
       if (irow) su[(row - 3) * W + col] = u;
       if (icol) sv[row * TX + (col - 4)] = v;
     }
@@ -445,7 +601,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
     // ---- C. x pass: items (field, row, run)
     {
-      const real halx = real(0.5) * ax, rdx = g.rdx;
+      const real rdx = g.rdx;
+      const double hx = g.dx;
       constexpr int NITEMS = NF * TY * NQ;
       for (int it = tid; it < NITEMS; it += NT) {
         const int c = it / (TY * NQ);
@@ -458,12 +615,12 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const int kind = (c == 0) ? 0 : (c == 1) ? 1 : (c == 2) ? 2 : 3;
           const real* Uc = sU + (c * H + srow) * W + col0;
           const real* Xc = sU + (1 * H + srow) * W + col0;
-          hydro_line<real, K, 1>(Uc, Xc, su + row * W + col0, 1, sp + srow * W + col0, kind, halx, rdx,
+          hydro_line<real, K, 1>(Uc, Xc, su + row * W + col0, 1, sp + srow * W + col0, kind, ax, rdx, hx,
                                  sD + (c * TY + row) * TX + q * K, 1, false);
         } else {
           real* xm = sX + row * TX + q * K;
           real* xp = sX + (TY + row) * TX + q * K;
-          phi_line<real, K, 1>(sU + (4 * H + srow) * W + col0, rdx, [&](int k, real dm, real dp) {
+          phi_line<real, K, 1>(sU + (4 * H + srow) * W + col0, rdx, hx, [&](int k, real dm, real dp) {
             xm[k] = dm;
             xp[k] = dp;
           });
@@ -474,7 +631,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
     // ---- D. y pass: items (field, column, run)
     {
-      const real haly = real(0.5) * ay, rdy = g.rdy;
+      const real rdy = g.rdy;
+      const double hy = g.dy;
       const real sf = g.flame_speed;
       constexpr int PER_C = 64 * NQY;  // 60 columns padded to 64 so no warp spans two fields
       constexpr int NITEMS = NF * PER_C;
@@ -490,20 +648,14 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const int kind = (c == 0) ? 0 : (c == 1) ? 2 : (c == 2) ? 1 : 3;
           const real* Uc = sU + (c * H + row0) * W + scol;
           const real* Xc = sU + (2 * H + row0) * W + scol;
-          hydro_line<real, KY, W>(Uc, Xc, sv + row0 * TX + col, TX, sp + row0 * W + scol, kind, haly, rdy,
+          hydro_line<real, KY, W>(Uc, Xc, sv + row0 * TX + col, TX, sp + row0 * W + scol, kind, ay, rdy, hy,
                                   sD + (c * TY + row0) * TX + col, TX, true);
         } else {
-          phi_line<real, KY, W>(sU + (4 * H + row0) * W + scol, rdy, [&](int k, real ym, real yp) {
+          phi_line<real, KY, W>(sU + (4 * H + row0) * W + scol, rdy, hy, [&](int k, real ym, real yp) {
             const int row = row0 + k;
             const real xm = sX[row * TX + col], xp = sX[(TY + row) * TX + col];
             const real u = su[row * W + scol], v = sv[(row + 3) * TX + col];
-            const real gx = real(0.5) * (xm + xp), gy = real(0.5) * (ym + yp);
-            const real adv = T::add_(T::mul_(u, gx), T::mul_(v, gy));
-            const real nrm = T::sqrt_(T::add_(T::mul_(gx, gx), T::mul_(gy, gy)));
-            const real H = T::fma_(-sf, nrm, adv);
-            const real axl = fabs(u) + sf, ayl = fabs(v) + sf;
-            const real diss = T::add_(T::mul_(real(0.5) * axl, xp - xm), T::mul_(real(0.5) * ayl, yp - ym));
-            sD[(4 * TY + row) * TX + col] = H - diss;
+            sD[(4 * TY + row) * TX + col] = Ar<real>::hamiltonian(u, v, sf, xm, xp, ym, yp);
           });
         }
       }
@@ -531,7 +683,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         real o[NF][4];
         {
           real u4[4], v4[4], p4[4];
-          if (rz) {
+          if (rz || grav != real(0)) {
             load4(su + row * W + scol, u4);
             load4(sv + srow * TX + tcol, v4);
             load4(sp + srow * W + scol, p4);
@@ -552,25 +704,13 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               real S = real(0);
-              if (f < 4 && rz) {  // -(1/r)(rho v_r, rho v_r^2, rho v_r v_z, (tau + p) v_r)
-                const real rinv = T::rcp(static_cast<real>(g.x0 + (ib + e + 0.5) * g.dx));
-                const real mr = sU[(1 * H + srow) * W + scol + e];
-                S = (f == 0) ? -mr * rinv
-                    : (f == 1) ? -(mr * u4[e]) * rinv
-                    : (f == 2) ? -(mr * v4[e]) * rinv
-                               : -((sU[(3 * H + srow) * W + scol + e] + p4[e]) * u4[e]) * rinv;
+              if (f < 4 && (rz || grav != real(0))) {
+                const real rho = sU[(0 * H + srow) * W + scol + e], mr = sU[(1 * H + srow) * W + scol + e];
+                const real mz = sU[(2 * H + srow) * W + scol + e], E = sU[(3 * H + srow) * W + scol + e];
+                S = Ar<real>::source(f, rz, grav, rho, mr, mz, E, u4[e], v4[e], p4[e], g.x0, ib + e, g.dx);
               }
-              if (grav != real(0)) {  // -rho dPhi/dz, -rho v_z dPhi/dz with dPhi/dz = -g
-                if (f == 2) S = T::fma_(sU[(0 * H + srow) * W + scol + e], grav, S);
-                if (f == 3) S = T::fma_(sU[(2 * H + srow) * W + scol + e], grav, S);
-              }
-              const real L = (f < 4) ? (S - Dv[e]) : -Dv[e];
-              if (ctl.mode == 1) {
-                o[f][e] = L;
-              } else {
-                const real inner = rb * T::fma_(dt, L, Uv[e]);
-                o[f][e] = use_un ? T::fma_(ra, un[e], inner) : inner;
-              }
+              const real L = (f < 4) ? Ar<real>::lval(Dv[e], S) : -Dv[e];
+              o[f][e] = (ctl.mode == 1) ? L : Ar<real>::blend(use_un, ra, rb, un[e], Uv[e], dt, L);
             }
           }
         }
@@ -600,18 +740,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           }
           // speeds of the output state (next stage's alpha, next step's dt) and validity
           const real rho = o[0][e], mx = o[1][e], my = o[2][e], E = o[3][e];
-          const real rr = T::rcp(rho);
-          const real u = mx * rr, v = my * rr;
-          const real p = gm1 * T::fma_(real(-0.5), T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
-          const real cs = T::sqrt_(gamma * p * rr);
+          real p, sx, sy, sm;
+          Ar<real>::speeds(rho, mx, my, E, gamma, gm1, p, sx, sy, sm);
           bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) &&
-                    T::finite(cs);
+                    T::finite(sm);
           if (NF == 5) ok = ok && T::finite(o[NF - 1][e]);
           if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
-          const real au = fabs(u), av = fabs(v);
-          amx = fmax(amx, au + cs);
-          amy = fmax(amy, av + cs);
-          smx = fmax(smx, T::add_(cs, T::add_(au, av)));
+          amx = fmax(amx, sx);
+          amy = fmax(amy, sy);
+          smx = fmax(smx, sm);
           if (g.totals) {
             const double dV = rz ? 6.283185307179586 * (g.x0 + (i + 0.5) * g.dx) * g.dx * g.dy : g.dx * g.dy;
 #pragma unroll
