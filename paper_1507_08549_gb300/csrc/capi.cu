@@ -408,7 +408,7 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
     return bail(HYDRO_ECUDA);
   c->tiles_x = (cfg->nx + TILE_X - 1) / TILE_X;
   c->pitch = c->tiles_x * TILE_X + 8;
-  c->rows = ((cfg->ny + 31) / 32) * 32 + 2 * GY;
+  c->rows = ((cfg->ny + MAX_TY - 1) / MAX_TY) * MAX_TY + 2 * GY;
   c->fstride = (long long)c->pitch * c->rows;
   const size_t bytes = (size_t)c->nf * c->fstride * c->esize;
   for (int k = 0; k < 3; ++k) {

@@ -18,19 +18,20 @@ constexpr int GX = 4;        // ghost columns left of cell 0 (3 used + 1 alignme
 constexpr int GY = 3;        // ghost rows below row 0
 constexpr int TILE_X = 60;   // cells per tile in x: halo box 68 = 60 + 8 wide (16-byte multiple)
 constexpr int BOX_W = 68;    // smem row pitch; 68 = 4 (mod 32) makes the x-pass lanes conflict-free
-constexpr int RUN_X = 15;    // cells per x-pass work item (4 items per tile row)
-constexpr int NQ_X = 4;
+constexpr int RUN = 15;      // cells per line work item, in x and in y (4 items per tile row)
 
 enum Bc { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECT = 2, BC_AXIS = 3 };
 enum ErrBits { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2 };
 
-// Tile variants: tile height TY and threads per CTA. x-pass items = TY * 4 * NF, y-pass items =
-// 60 * NF * (TY / KY); the thread counts keep both near one item per thread.
+// Tile variants: tile height TY (a multiple of the 15-cell run) and threads per CTA. Per field the
+// x pass has 4 runs per row (rows padded to 8-row lane groups) and the y pass one run per 15 rows and
+// column (columns padded to 64); 320 threads give about one item per thread for TY = 15.
 struct Variant {
   int ty, threads;
 };
 constexpr int NUM_VARIANTS = 3;
-constexpr Variant VARIANTS[NUM_VARIANTS] = {{8, 160}, {16, 320}, {32, 640}};
+constexpr int MAX_TY = 30;
+constexpr Variant VARIANTS[NUM_VARIANTS] = {{15, 160}, {15, 320}, {30, 640}};
 
 // Per-grid parameters of one stage launch (one ensemble member).
 template <typename real>

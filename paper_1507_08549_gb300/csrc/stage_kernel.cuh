@@ -305,12 +305,13 @@ struct Ar<double> {
 //
 // One line of K cells: points m = 0 .. K+5 (cells -3 .. K+2 of the run), faces f = 0 .. K (left face
 // of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1, where
-// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased).
-template <typename real, int K, int S>
+// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). Strides are runtime
+// values so the x and y passes run the same instructions.
+template <typename real, int K>
 __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
-                                           const real* __restrict__ vel, int vstride,
-                                           const real* __restrict__ pr, int kind, real alpha, real rd, double h,
-                                           real* __restrict__ dst, int dstride, bool accumulate) {
+                                           const real* __restrict__ vel, const real* __restrict__ pr, int S,
+                                           int VS, int kind, real alpha, real rd, double h,
+                                           real* __restrict__ dst, int DS, bool accumulate) {
   using A = Ar<real>;
   real fp[K + 6], fm[K + 6];
   B3<real> bp[K + 6], bm[K + 6];
@@ -319,7 +320,7 @@ __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const re
   for (int m = 0; m < K + 6; ++m) {
     const real uu = Uc[m * S];
     const real F = kind == 0 ? A::flux(0, uu, Xc[m * S], real(0), real(0))
-                             : A::flux(kind, uu, real(0), vel[m * vstride], pr[m * S]);
+                             : A::flux(kind, uu, real(0), vel[m * VS], pr[m * S]);
     A::split(F, uu, alpha, fp[m], fm[m]);
     if constexpr (!A::kExact) {
       if (m >= 2) {
@@ -342,7 +343,7 @@ __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const re
       const real fh = A::sum(plus, minus);
       if (f >= 1) {
         const real d = A::divided(fh, fh_prev, rd, h);
-        real* o = dst + (f - 1) * dstride;
+        real* o = dst + (f - 1) * DS;
         *o = accumulate ? A::sum(*o, d) : d;
       }
       fh_prev = fh;
@@ -352,9 +353,10 @@ __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const re
 
 // One-sided HJ-WENO5 derivatives (Jiang & Peng 2000) of phi along a line of K cells from points
 // m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
-// phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}). emit(k, phi^-, phi^+).
-template <typename real, int K, int S, typename Emit>
-__device__ __forceinline__ void phi_line(const real* __restrict__ ph, real rd, double h, Emit emit) {
+// phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}), stored to om[k*DS], op[k*DS].
+template <typename real, int K>
+__device__ __forceinline__ void phi_line(const real* __restrict__ ph, int S, real rd, double h,
+                                         real* __restrict__ om, real* __restrict__ op, int DS) {
   using A = Ar<real>;
   real d[K + 5];
   B3<real> b[K + 5];
@@ -377,7 +379,8 @@ __device__ __forceinline__ void phi_line(const real* __restrict__ ph, real rd, d
         dm = weno_side(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4], b[k + 1].m, b[k + 2].t, b[k + 3].p);
         dp = weno_side(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1], b[k + 4].p, b[k + 3].t, b[k + 2].m);
       }
-      emit(k, dm, dp);
+      om[k * DS] = dm;
+      op[k * DS] = dp;
     }
   }
 }
@@ -461,21 +464,42 @@ __device__ __forceinline__ void write_ghost_images(real* out, long long fs, int 
 
 template <typename real, int NF, int TY>
 struct Tile {
-  static constexpr int TX = TILE_X, W = BOX_W, H = TY + 6, K = RUN_X, NQ = NQ_X;
-  static constexpr int KY = TY < 16 ? TY : 16;
-  static constexpr int NQY = TY / KY;
+  static constexpr int TX = TILE_X, W = BOX_W, H = TY + 6, K = RUN, NQ = TX / RUN;
+  static constexpr int NQY = TY / RUN;                   // y runs per column
+  static constexpr int TYP = ((TY + 7) / 8) * 8;        // rows padded to whole 8-row lane groups
+  static constexpr int XI_PER_C = TYP * NQ;             // x-pass items per field (multiple of 32)
+  static constexpr int YI_PER_C = 64 * NQY;             // y-pass items per field (60 columns padded to 64)
+  static constexpr int BOX = NF * H * W;                // elements of one halo box
   // shared-memory carve-up (elements of real)
-  static constexpr int OFF_U = 0;                         // [NF][H][W]   state box
-  static constexpr int OFF_PU = OFF_U + NF * H * W;       // [TY][W]      u on the tile rows
-  static constexpr int OFF_PV = OFF_PU + TY * W;          // [H][TX]      v on the tile columns
-  static constexpr int OFF_PP = OFF_PV + H * TX;          // [H][W]       p
-  static constexpr int OFF_D = OFF_PP + H * W;            // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
-  static constexpr int OFF_X = OFF_D + NF * TY * TX;      // [2][TY][TX]  phi_x^-, phi_x^+
-  static constexpr int ELEMS = OFF_X + (NF == 5 ? 2 * TY * TX : 0);
-  static constexpr int RED_DOUBLES = 20 * 8;              // per-warp partials (<= 20 warps x 8)
-  static constexpr size_t BYTES = ((ELEMS * sizeof(real) + 15) / 16) * 16 + RED_DOUBLES * sizeof(double) + 16;
-  static constexpr unsigned BOX_BYTES = NF * H * W * sizeof(real);
+  static constexpr int OFF_U0 = 0;                      // [NF][H][W]   halo box, buffer 0
+  static constexpr int OFF_U1 = OFF_U0 + BOX;           // [NF][H][W]   halo box, buffer 1
+  static constexpr int OFF_PU = OFF_U1 + BOX;           // [TY][W]      u on the tile rows
+  static constexpr int OFF_PV = OFF_PU + TY * W;        // [H][TX]      v on the tile columns
+  static constexpr int OFF_PP = OFF_PV + H * TX;        // [H][W]       p
+  static constexpr int OFF_D = OFF_PP + H * W;          // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
+  static constexpr int OFF_X = OFF_D + NF * TY * TX;    // [4][TY][TX]  phi_x^-, phi_x^+, phi_y^-, phi_y^+
+  static constexpr int ELEMS = OFF_X + (NF == 5 ? 4 * TY * TX : 0);
+  static constexpr int RED_DOUBLES = 20 * 8;            // per-warp partials (<= 20 warps x 8)
+  static constexpr size_t RED_OFF = ((ELEMS * sizeof(real) + 15) / 16) * 16;
+  static constexpr size_t BYTES = RED_OFF + RED_DOUBLES * sizeof(double) + 32;
+  static constexpr unsigned BOX_BYTES = BOX * sizeof(real);
+  static_assert(TX % RUN == 0 && TY % RUN == 0, "tiles are whole runs");
 };
+
+// Issue the TMA bulk copies of one tile's halo box (warp 0; lane 0 arms the barrier first).
+template <typename real, int NF, int H>
+__device__ __forceinline__ void issue_box(const GridParams<real>& m, int tile, int TY, real* box, uint64_t* bar,
+                                          int lane, unsigned bytes) {
+  const int tx = tile % m.tiles_x, ty = tile / m.tiles_x;
+  const int x0 = tx * TILE_X, y0 = ty * TY;
+  if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+  __syncwarp();
+  for (int r = lane; r < NF * H; r += 32) {
+    const int f = r / H, row = r - f * H;
+    const real* src = m.win + f * m.fstride + static_cast<long long>(y0 + row) * m.pitch + x0;
+    bulk_g2s(box + r * BOX_W, src, BOX_W * sizeof(real), bar);
+  }
+}
 
 // ------------------------------------------------------------------------------ the stage kernel
 
@@ -485,19 +509,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
                  StageCtl ctl) {
   using T = RT<real>;
   using TL = Tile<real, NF, TY>;
-  constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ, KY = TL::KY, NQY = TL::NQY;
-  static_assert(TY % 8 == 0, "tile height must be a multiple of 8");
+  constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
-  real* sU = sm + TL::OFF_U;
   real* su = sm + TL::OFF_PU;
   real* sv = sm + TL::OFF_PV;
   real* sp = sm + TL::OFF_PP;
   real* sD = sm + TL::OFF_D;
   real* sX = sm + TL::OFF_X;
-  double* red = reinterpret_cast<double*>(smem_raw + ((TL::ELEMS * sizeof(real) + 15) / 16) * 16);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_DOUBLES);
+  double* red = reinterpret_cast<double*>(smem_raw + TL::RED_OFF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_DOUBLES);  // two barriers, one per box buffer
   __shared__ GridParams<real> g;
   __shared__ int s_abort;
 
@@ -506,15 +528,26 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   constexpr int NWARPS = NT / 32;
 
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     s_abort = 0;
   }
   __syncthreads();
 
-  unsigned parity = 0;
-  int cur_member = -1;
+  // prologue: the first work item's box
+  if (warp == 0 && static_cast<int>(blockIdx.x) < nwork) {
+    const int w0 = blockIdx.x;
+    const int m0 = work ? work[w0].member : 0;
+    issue_box<real, NF, H>(members[m0], work ? work[w0].tile : w0, TY, sm + TL::OFF_U0, &bar[0], lane,
+                           TL::BOX_BYTES);
+  }
 
-  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+  unsigned parity[2] = {0u, 0u};
+  int cur_member = -1;
+  int it = 0;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++it) {
+    const int b = it & 1;
+    real* sU = sm + (b ? TL::OFF_U1 : TL::OFF_U0);
     const int member = work ? work[w].member : 0;
     const int tile = work ? work[w].tile : w;
     if (member != cur_member) {
@@ -523,21 +556,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       __syncthreads();
       cur_member = member;
     }
+    // prefetch the next item's box into the other buffer (free since the previous tile ended)
+    const int wn = w + gridDim.x;
+    if (warp == 0 && wn < nwork) {
+      const int mn = work ? work[wn].member : 0;
+      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : wn, TY, sm + (b ? TL::OFF_U0 : TL::OFF_U1),
+                             &bar[b ^ 1], lane, TL::BOX_BYTES);
+    }
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int x0 = tx * TX, y0 = ty * TY;
     const long long fs = g.fstride;
     const int pitch = g.pitch;
-
-    // ---- A. halo box -> shared memory (TMA bulk copies, one per field row)
-    if (warp == 0) {
-      if (lane == 0) mbar_arrive_expect_tx(bar, TL::BOX_BYTES);
-      __syncwarp();
-      for (int r = lane; r < NF * H; r += 32) {
-        const int f = r / H, row = r - f * H;
-        const real* src = g.win + f * fs + static_cast<long long>(y0 + row) * pitch + x0;
-        bulk_g2s(sU + r * W, src, W * sizeof(real), bar);
-      }
-    }
 
     // stage scalars (overlap with the copies)
     const real ax = g.alpha_in[0], ay = g.alpha_in[1];
@@ -572,11 +601,12 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       }
     }
 
-    if (!mbar_wait_bounded(bar, parity)) {
+    // ---- A. wait for this tile's halo box
+    if (!mbar_wait_bounded(&bar[b], parity[b])) {
       atomicOr(g.err, ERR_TIMEOUT);
       s_abort = 1;
     }
-    parity ^= 1u;
+    parity[b] ^= 1u;
     __syncthreads();
     if (s_abort) break;
 
@@ -587,94 +617,70 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const bool irow = row >= 3 && row < TY + 3;
       const bool icol = col >= 4 && col < TX + 4;
       if (!irow && !icol) continue;
-      const real rho = sU[0 * H * W + idx];
-      const real mx = sU[1 * H * W + idx];
-      const real my = sU[2 * H * W + idx];
-      const real E = sU[3 * H * W + idx];
       real u, v, p;
-      Ar<real>::prims(rho, mx, my, E, gm1, u, v, p);
+      Ar<real>::prims(sU[0 * H * W + idx], sU[1 * H * W + idx], sU[2 * H * W + idx], sU[3 * H * W + idx], gm1, u,
+                      v, p);
       sp[idx] = p;
       if (irow) su[(row - 3) * W + col] = u;
       if (icol) sv[row * TX + (col - 4)] = v;
     }
     __syncthreads();
 
-    // ---- C. x pass: items (field, row, run)
-    {
-      const real rdx = g.rdx;
-      const double hx = g.dx;
-      constexpr int NITEMS = NF * TY * NQ;
-      for (int it = tid; it < NITEMS; it += NT) {
-        const int c = it / (TY * NQ);
-        const int rem = it - c * (TY * NQ);
-        const int row = (rem / (8 * NQ)) * 8 + (rem & 7);
-        const int q = (rem >> 3) % NQ;
-        const int srow = row + 3;
-        const int col0 = 4 + q * K - 3;  // first point of the run in the box
+    // ---- C/D. x pass then y pass through the same line code: items (field, line, run of 15 cells)
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool xp = pass == 0;
+      const int per_c = xp ? TL::XI_PER_C : TL::YI_PER_C;
+      const real alpha = xp ? ax : ay;
+      const real rd = xp ? g.rdx : g.rdy;
+      const double h = xp ? g.dx : g.dy;
+      for (int item = tid; item < NF * per_c; item += NT) {
+        const int c = item / per_c;
+        const int rem = item - c * per_c;
+        int trow, tcol, brow, bcol;
+        if (xp) {  // lanes: 8 consecutive rows x 4 runs -> all 32 banks (68 = 4 mod 32, 15 = 3 mod 4)
+          trow = (rem / (8 * NQ)) * 8 + (rem & 7);
+          tcol = ((rem >> 3) % NQ) * K;
+          if (trow >= TY) continue;
+          brow = trow + 3;
+          bcol = tcol + 1;
+        } else {  // lanes: consecutive columns
+          tcol = rem & 63;
+          trow = (rem >> 6) * K;
+          if (tcol >= TX) continue;
+          brow = trow;
+          bcol = tcol + 4;
+        }
+        const int S = xp ? 1 : W;
+        const int DS = xp ? 1 : TX;
         if (c < 4) {
-          const int kind = (c == 0) ? 0 : (c == 1) ? 1 : (c == 2) ? 2 : 3;
-          const real* Uc = sU + (c * H + srow) * W + col0;
-          const real* Xc = sU + (1 * H + srow) * W + col0;
-          hydro_line<real, K, 1>(Uc, Xc, su + row * W + col0, 1, sp + srow * W + col0, kind, ax, rdx, hx,
-                                 sD + (c * TY + row) * TX + q * K, 1, false);
+          const int kind = (c == 0) ? 0 : (c == 3) ? 3 : ((c == 1) == xp) ? 1 : 2;
+          const real* Uc = sU + (c * H + brow) * W + bcol;
+          const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
+          const real* vel = xp ? su + trow * W + bcol : sv + brow * TX + tcol;
+          hydro_line<real, K>(Uc, Xc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd, h,
+                              sD + (c * TY + trow) * TX + tcol, DS, !xp);
         } else {
-          real* xm = sX + row * TX + q * K;
-          real* xp = sX + (TY + row) * TX + q * K;
-          phi_line<real, K, 1>(sU + (4 * H + srow) * W + col0, rdx, hx, [&](int k, real dm, real dp) {
-            xm[k] = dm;
-            xp[k] = dp;
-          });
+          real* om = sX + ((xp ? 0 : 2) * TY + trow) * TX + tcol;
+          phi_line<real, K>(sU + (4 * H + brow) * W + bcol, S, rd, h, om, om + TY * TX, DS);
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-
-    // ---- D. y pass: items (field, column, run)
-    {
-      const real rdy = g.rdy;
-      const double hy = g.dy;
-      const real sf = g.flame_speed;
-      constexpr int PER_C = 64 * NQY;  // 60 columns padded to 64 so no warp spans two fields
-      constexpr int NITEMS = NF * PER_C;
-      for (int it = tid; it < NITEMS; it += NT) {
-        const int c = it / PER_C;
-        const int rem = it - c * PER_C;
-        const int qy = rem >> 6;
-        const int col = rem & 63;
-        if (col >= TX) continue;
-        const int scol = col + 4;
-        const int row0 = qy * KY;  // first tile row of the run; points start 3 rows above
-        if (c < 4) {
-          const int kind = (c == 0) ? 0 : (c == 1) ? 2 : (c == 2) ? 1 : 3;
-          const real* Uc = sU + (c * H + row0) * W + scol;
-          const real* Xc = sU + (2 * H + row0) * W + scol;
-          hydro_line<real, KY, W>(Uc, Xc, sv + row0 * TX + col, TX, sp + row0 * W + scol, kind, ay, rdy, hy,
-                                  sD + (c * TY + row0) * TX + col, TX, true);
-        } else {
-          phi_line<real, KY, W>(sU + (4 * H + row0) * W + scol, rdy, hy, [&](int k, real ym, real yp) {
-            const int row = row0 + k;
-            const real xm = sX[row * TX + col], xp = sX[(TY + row) * TX + col];
-            const real u = su[row * W + scol], v = sv[(row + 3) * TX + col];
-            sD[(4 * TY + row) * TX + col] = Ar<real>::hamiltonian(u, v, sf, xm, xp, ym, yp);
-          });
-        }
-      }
-    }
-    __syncthreads();
 
     // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
     real amx = real(0), amy = real(0), smx = real(0);
     double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     {
       const int nx = g.nx, ny = g.ny;
-      const real gamma = g.gamma, grav = g.gravity;
+      const real gamma = g.gamma, grav = g.gravity, sf = g.flame_speed;
       const bool rz = g.geometry == 1;
       const real dt = static_cast<real>(dtd);
       const real ra = static_cast<real>(ctl.rk_a), rb = static_cast<real>(ctl.rk_b);
       const bool use_un = ctl.rk_a != 0.0 && ctl.mode == 0;
       constexpr int NG = TX / 4;
-      for (int it = tid; it < TY * NG; it += NT) {
-        const int row = it / NG, g4 = it - row * NG;
+      for (int it2 = tid; it2 < TY * NG; it2 += NT) {
+        const int row = it2 / NG, g4 = it2 - row * NG;
         const int j = y0 + row, ib = x0 + 4 * g4;
         if (j >= ny || ib >= nx) continue;
         const int nvalid = min(4, nx - ib);
@@ -683,7 +689,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         real o[NF][4];
         {
           real u4[4], v4[4], p4[4];
-          if (rz || grav != real(0)) {
+          const bool need_prims = rz || grav != real(0) || NF == 5;
+          if (need_prims) {
             load4(su + row * W + scol, u4);
             load4(sv + srow * TX + tcol, v4);
             load4(sp + srow * W + scol, p4);
@@ -692,7 +699,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           for (int f = 0; f < NF; ++f) {
             real Uv[4], Dv[4], un[4];
             load4(sU + (f * H + srow) * W + scol, Uv);
-            load4(sD + (f * TY + row) * TX + tcol, Dv);
+            if (f < 4) {
+              load4(sD + (f * TY + row) * TX + tcol, Dv);
+            } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
+              real xm[4], xq[4], ym[4], yq[4];
+              load4(sX + (0 * TY + row) * TX + tcol, xm);
+              load4(sX + (1 * TY + row) * TX + tcol, xq);
+              load4(sX + (2 * TY + row) * TX + tcol, ym);
+              load4(sX + (3 * TY + row) * TX + tcol, yq);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) Dv[e] = Ar<real>::hamiltonian(u4[e], v4[e], sf, xm[e], xq[e], ym[e], yq[e]);
+            }
             if (use_un) {
               if (nvalid == 4) {
                 load4(g.un + f * fs + gbase, un);
