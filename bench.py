@@ -224,7 +224,44 @@ def run(args):
     state_bytes = F * B * cells
     e2e = {"value": world * cells * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes, "steps": ke}
+    # FP32 discrete adjoint of one step (frozen dt / alphas of the step it reverses) and the FP64 plain step
+    adjoint = None
+    if not args.no_adjoint:
+        h.record(2)
+        h.step(U, 1)
+        dtl, al = h.get_log(1)
+        h.record(0)
+        lam = torch.ones_like(U)
+        h.adjoint_step(U, lam, float(dtl[0]), al[0].ravel())  # warm-up (allocates the adjoint buffers)
+        torch.cuda.synchronize()
+        ka = max(1, args.adjoint_steps)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(ka):
+            h.adjoint_step(U, lam, float(dtl[0]), al[0].ravel())
+        a1.record()
+        torch.cuda.synchronize()
+        adj_ms = a0.elapsed_time(a1) / ka
+        adjoint = {"ms_per_step": adj_ms, "dtype": dtype, "steps": ka,
+                   "adjoint_over_forward": adj_ms / (ms / args.steps)}
     h.close()
+    fp64 = None
+    if not args.no_fp64:
+        h64 = hydro.Hydro(prob, dtype="f64")
+        U64 = h64.state(prob.U0)
+        h64.step(U64, 1)
+        torch.cuda.synchronize()
+        k64 = max(1, args.fp64_steps)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        h64.step(U64, k64)
+        b1.record()
+        torch.cuda.synchronize()
+        ms64 = b0.elapsed_time(b1) / k64
+        fp64 = {"ms_per_step": ms64, "value": cells / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                "fp64_over_fp32": ms64 / (ms / args.steps)}
+        h64.close()
+        del U64
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -233,7 +270,8 @@ def run(args):
                            "cells": cells, "steps_simulated": args.steps, "t_end": t_sim,
                            "l2": "state 1.34 GB per copy >> 129 MB L2 (no flush needed)",
                            "tile": info, "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roof, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk}
+                "roofline": roof, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
+                "adjoint": adjoint, "fp64_step": fp64}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -253,6 +291,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")

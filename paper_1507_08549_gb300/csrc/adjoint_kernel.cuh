@@ -1,0 +1,474 @@
+// adjoint_kernel.cuh -- discrete adjoint of one SSP-RK3 stage of the WENO5 / Lax-Friedrichs update
+// with the level set (Leung, Chu & Lin 2015, Sec. 2.1-2.2), dt and the Lax-Friedrichs speeds frozen.
+//
+// A stage maps its input W to V = a U^n + b (W + dt L(W)). Given nu = dJ/dV the adjoint is
+//   dJ/dW = b (nu + dt J_L(W)^T nu),   dJ/dU^n += a nu.
+// J_L^T nu is assembled in three launches:
+//   adj_point_kernel   per interior cell: the point terms -- (r,z) and gravity sources, and the level
+//                      set's local Lax-Friedrichs Hamiltonian, whose adjoint w.r.t. its four one-sided
+//                      derivatives (hb) is stored for the line pass and w.r.t. u, v goes to the cell;
+//   adj_line_kernel    tiles over the padded grid INCLUDING its ghost frame: for every point, the
+//                      face adjoints (nu_f - nu_{f-1}) / h of the six faces whose WENO5 stencils contain
+//                      it, times the WENO5 gradients, through the Lax-Friedrichs split and the Euler
+//                      flux Jacobian; and the level-set adjoint through the HJ-WENO5 gradients;
+//   adj_blend_kernel   per interior cell: folds the ghost-frame adjoints back onto the cells they are
+//                      images of (the adjoint of the boundary fill) and applies the RK blend.
+// nu and hb are zero outside the interior, so faces outside the grid contribute nothing; such faces
+// are skipped (their stencils may reach unfilled corner points).
+#pragma once
+#include "stage_kernel.cuh"
+
+namespace hydro {
+
+// gbar * dW/dv of the WENO5-JS value W(a, b, c, d, e) (Jiang & Shu weights), added to g[0..4].
+template <typename real>
+__device__ __forceinline__ void weno5_grad_acc(real a, real b, real c, real d, real e, real gbar, real& ga,
+                                               real& gb, real& gc, real& gd, real& ge) {
+  const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
+  const real q1 = (-b + real(5) * c + real(2) * d) / real(6);
+  const real q2 = (real(2) * c + real(5) * d - e) / real(6);
+  const real s0 = a - real(2) * b + c, t0 = a - real(4) * b + real(3) * c;
+  const real s1 = b - real(2) * c + d, t1 = b - d;
+  const real s2 = c - real(2) * d + e, t2 = real(3) * c - real(4) * d + e;
+  const real D0 = real(1e-6) + real(13.0 / 12.0) * s0 * s0 + real(0.25) * t0 * t0;
+  const real D1 = real(1e-6) + real(13.0 / 12.0) * s1 * s1 + real(0.25) * t1 * t1;
+  const real D2 = real(1e-6) + real(13.0 / 12.0) * s2 * s2 + real(0.25) * t2 * t2;
+  const real a0 = real(0.1) / (D0 * D0), a1 = real(0.6) / (D1 * D1), a2 = real(0.3) / (D2 * D2);
+  const real rS = real(1) / (a0 + a1 + a2);
+  const real w0 = a0 * rS, w1 = a1 * rS, w2 = a2 * rS;
+  const real W = w0 * q0 + w1 * q1 + w2 * q2;
+  // d alpha_k / d beta_k = -2 alpha_k / D_k ; d beta_k / dv = 13/6 s_k ds_k + 1/2 t_k dt_k
+  const real c0 = (q0 - W) * rS * (real(-2) * a0 / D0);
+  const real c1 = (q1 - W) * rS * (real(-2) * a1 / D1);
+  const real c2 = (q2 - W) * rS * (real(-2) * a2 / D2);
+  const real A0 = c0 * real(13.0 / 6.0) * s0, B0 = c0 * real(0.5) * t0;
+  const real A1 = c1 * real(13.0 / 6.0) * s1, B1 = c1 * real(0.5) * t1;
+  const real A2 = c2 * real(13.0 / 6.0) * s2, B2 = c2 * real(0.5) * t2;
+  const real k6 = real(1) / real(6);
+  ga += gbar * (w0 * (real(2) * k6) + A0 + B0);
+  gb += gbar * (w0 * (real(-7) * k6) + w1 * (-k6) - real(2) * A0 - real(4) * B0 + A1 + B1);
+  gc += gbar * (w0 * (real(11) * k6) + w1 * (real(5) * k6) + w2 * (real(2) * k6) + A0 + real(3) * B0 -
+                real(2) * A1 + A2 + real(3) * B2);
+  gd += gbar * (w1 * (real(2) * k6) + w2 * (real(5) * k6) + A1 - B1 - real(2) * A2 - real(4) * B2);
+  ge += gbar * (w2 * (-k6) + A2 + B2);
+}
+
+template <typename real>
+__device__ __forceinline__ real weno5_plain(real a, real b, real c, real d, real e) {
+  const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
+  const real q1 = (-b + real(5) * c + real(2) * d) / real(6);
+  const real q2 = (real(2) * c + real(5) * d - e) / real(6);
+  const real s0 = a - real(2) * b + c, t0 = a - real(4) * b + real(3) * c;
+  const real s1 = b - real(2) * c + d, t1 = b - d;
+  const real s2 = c - real(2) * d + e, t2 = real(3) * c - real(4) * d + e;
+  const real D0 = real(1e-6) + real(13.0 / 12.0) * s0 * s0 + real(0.25) * t0 * t0;
+  const real D1 = real(1e-6) + real(13.0 / 12.0) * s1 * s1 + real(0.25) * t1 * t1;
+  const real D2 = real(1e-6) + real(13.0 / 12.0) * s2 * s2 + real(0.25) * t2 * t2;
+  const real a0 = real(0.1) / (D0 * D0), a1 = real(0.6) / (D1 * D1), a2 = real(0.3) / (D2 * D2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// dF_r/dU_s of the Euler flux along x (dir 0) or y (dir 1) at one state.
+template <typename real>
+__device__ __forceinline__ void flux_jacobian(int dir, real gamma, real rho, real mx, real my, real E,
+                                              real J[4][4]) {
+  const real u = mx / rho, v = my / rho;
+  const real gm1 = gamma - real(1);
+  const real p = gm1 * (E - real(0.5) * (mx * u + my * v));
+  const real dp[4] = {gm1 * real(0.5) * (u * u + v * v), -gm1 * u, -gm1 * v, gm1};
+  const real du[4] = {-u / rho, real(1) / rho, real(0), real(0)};
+  const real dv[4] = {-v / rho, real(0), real(1) / rho, real(0)};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const real dmx = (s == 1) ? real(1) : real(0), dmy = (s == 2) ? real(1) : real(0);
+    const real dE = (s == 3) ? real(1) : real(0);
+    if (dir == 0) {
+      J[0][s] = dmx;
+      J[1][s] = dmx * u + mx * du[s] + dp[s];
+      J[2][s] = dmy * u + my * du[s];
+      J[3][s] = (dE + dp[s]) * u + (E + p) * du[s];
+    } else {
+      J[0][s] = dmy;
+      J[1][s] = dmx * v + mx * dv[s];
+      J[2][s] = dmy * v + my * dv[s] + dp[s];
+      J[3][s] = (dE + dp[s]) * v + (E + p) * dv[s];
+    }
+  }
+}
+
+template <typename real>
+struct AdjParams {
+  const real* W;     // stage input state (padded, ghosts filled)
+  const real* nu;    // dJ/dV (padded, zero outside the interior)
+  real* mu;          // J_L^T nu on the padded grid including the ghost frame
+  real* hb;          // [4] level-set Hamiltonian adjoints w.r.t. phi_x^-, phi_x^+, phi_y^-, phi_y^+ (padded)
+  real* out;         // dJ/dW = b (nu + dt mu_folded) (padded, interior written)
+  real* acc;         // dJ/dU^n accumulator (padded, interior)
+  long long fstride;
+  int nx, ny, pitch, rows;
+  int bc[4];
+  int geometry;
+  real gamma, gravity, flame_speed, ax, ay;
+  double dx, dy, x0, dt, a, b;
+  int acc_mode;      // 0: acc = a nu ; 1: acc += a nu ; 2: acc += out (final stage), write out too
+};
+
+// ---------------------------------------------------------------------------- point terms
+
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= P.nx) return;
+  const long long fs = P.fstride;
+  const long long k = static_cast<long long>(j + GY) * P.pitch + i + GX;
+  const real rho = P.W[k], mx = P.W[fs + k], my = P.W[2 * fs + k], E = P.W[3 * fs + k];
+  const real u = mx / rho, v = my / rho;
+  const real p = (P.gamma - real(1)) * (E - real(0.5) * (mx * u + my * v));
+  real nu[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) nu[f] = P.nu[f * fs + k];
+  real g[4] = {real(0), real(0), real(0), real(0)};
+  if (P.geometry == 1) {  // sources -(1/r)(m_r, m_r u, m_r v, (E + p) u)
+    const real r = static_cast<real>(P.x0 + (i + 0.5) * P.dx);
+    real J[4][4];
+    flux_jacobian<real>(0, P.gamma, rho, mx, my, E, J);
+    real JS[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      JS[0][s] = -((s == 1) ? real(1) : real(0)) / r;
+      JS[1][s] = -(((s == 1) ? u : real(0)) + mx * ((s == 0) ? -u / rho : (s == 1) ? real(1) / rho : real(0))) / r;
+      JS[2][s] = -(((s == 1) ? v : real(0)) + mx * ((s == 0) ? -v / rho : (s == 2) ? real(1) / rho : real(0))) / r;
+      JS[3][s] = -J[3][s] / r;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[s] += JS[q][s] * nu[q];
+  }
+  if (P.gravity != real(0)) {
+    g[0] += P.gravity * nu[2];
+    g[2] += P.gravity * nu[3];
+  }
+  (void)p;
+  if constexpr (NF == 5) {
+    const real* ph = P.W + 4 * fs + k;
+    const real rdx = static_cast<real>(1.0 / P.dx), rdy = static_cast<real>(1.0 / P.dy);
+    real dxs[6], dys[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      dxs[q] = (ph[q - 2] - ph[q - 3]) * rdx;                          // D_{i-3+q}
+      dys[q] = (ph[(q - 2) * P.pitch] - ph[(q - 3) * P.pitch]) * rdy;  // D_{j-3+q}
+    }
+    const real xm = weno5_plain(dxs[0], dxs[1], dxs[2], dxs[3], dxs[4]);
+    const real xq = weno5_plain(dxs[5], dxs[4], dxs[3], dxs[2], dxs[1]);
+    const real ym = weno5_plain(dys[0], dys[1], dys[2], dys[3], dys[4]);
+    const real yq = weno5_plain(dys[5], dys[4], dys[3], dys[2], dys[1]);
+    const real sf = P.flame_speed;
+    const real gx = real(0.5) * (xm + xq), gy = real(0.5) * (ym + yq);
+    const real nrm = sqrt(gx * gx + gy * gy);
+    const real Hgx = u - (nrm > real(0) ? sf * gx / nrm : real(0));
+    const real Hgy = v - (nrm > real(0) ? sf * gy / nrm : real(0));
+    const real axl = fabs(u) + sf, ayl = fabs(v) + sf;
+    const real hbar = -nu[4];  // L_phi = -H_hat
+    P.hb[0 * fs + k] = hbar * (real(0.5) * Hgx + real(0.5) * axl);
+    P.hb[1 * fs + k] = hbar * (real(0.5) * Hgx - real(0.5) * axl);
+    P.hb[2 * fs + k] = hbar * (real(0.5) * Hgy + real(0.5) * ayl);
+    P.hb[3 * fs + k] = hbar * (real(0.5) * Hgy - real(0.5) * ayl);
+    const real su = u > real(0) ? real(1) : (u < real(0) ? real(-1) : real(0));
+    const real sv = v > real(0) ? real(1) : (v < real(0) ? real(-1) : real(0));
+    const real ub = hbar * (gx - su * real(0.5) * (xq - xm));
+    const real vb = hbar * (gy - sv * real(0.5) * (yq - ym));
+    g[0] += ub * (-u / rho) + vb * (-v / rho);
+    g[1] += ub / rho;
+    g[2] += vb / rho;
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) P.mu[s * fs + k] = g[s];
+  if constexpr (NF == 5) P.mu[4 * fs + k] = real(0);
+}
+
+// ---------------------------------------------------------------------------- line adjoints
+
+constexpr int ATX = 32, ATY = 16, ARUN = 8;   // output points per tile, points per line item
+constexpr int AHX = 6;                        // box halo (hydro needs 5, level set 6)
+constexpr int ABW = ATX + 2 * AHX, ABH = ATY + 2 * AHX;
+
+template <typename real, int NF>
+struct ATile {
+  static constexpr int BOX = ABW * ABH;
+  static constexpr int OFF_W = 0;                        // [NF][ABH][ABW] state
+  static constexpr int OFF_P = OFF_W + NF * BOX;         // [4][ABH][ABW]  u, v, p, 1/rho
+  static constexpr int OFF_N = OFF_P + 4 * BOX;          // [NF][ABH][ABW] nu
+  static constexpr int OFF_H = OFF_N + NF * BOX;         // [4][ABH][ABW]  hb (level set)
+  static constexpr int OFF_PB = OFF_H + (NF == 5 ? 4 * BOX : 0);  // [4][ATY][ATX] f+bar + f-bar
+  static constexpr int OFF_MB = OFF_PB + 4 * ATY * ATX;  // [4][ATY][ATX] f+bar - f-bar
+  static constexpr int OFF_MU = OFF_MB + 4 * ATY * ATX;  // [NF][ATY][ATX] accumulated mu
+  static constexpr int ELEMS = OFF_MU + NF * ATY * ATX;
+  static constexpr size_t BYTES = ELEMS * sizeof(real);
+};
+
+// One hydro line of ARUN output points: faces f = -2 .. ARUN+2 relative to the first output point,
+// points m = -5 .. ARUN+4. Writes (f+bar + f-bar) and (f+bar - f-bar) of the outputs.
+template <typename real>
+__device__ __forceinline__ void adj_hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
+                                               const real* __restrict__ vel, const real* __restrict__ pr,
+                                               const real* __restrict__ nuc, int S, int kind, real alpha, real rd,
+                                               real* __restrict__ pb, real* __restrict__ mb, int DS) {
+  constexpr int NP = ARUN + 10;  // points, index m + 5
+  real fp[NP], fm[NP], ap[NP], am[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int m = q - 5;
+    const real uu = Uc[m * S];
+    real F;
+    if (kind == 0) F = Xc[m * S];
+    else {
+      const real vn = vel[m * S], p = pr[m * S];
+      F = kind == 1 ? uu * vn + p : kind == 2 ? uu * vn : (uu + p) * vn;
+    }
+    fp[q] = real(0.5) * (F + alpha * uu);
+    fm[q] = real(0.5) * (F - alpha * uu);
+    ap[q] = real(0);
+    am[q] = real(0);
+  }
+#pragma unroll
+  for (int f = -2; f <= ARUN + 2; ++f) {
+    // face f lies between points f-1 and f; its left-biased stencil is points f-3 .. f+1
+    const real fb = (nuc[f * S] - nuc[(f - 1) * S]) * rd;
+    if (fb != real(0)) {
+      const int q = f + 5;
+      weno5_grad_acc(fp[q - 3], fp[q - 2], fp[q - 1], fp[q], fp[q + 1], fb, ap[q - 3], ap[q - 2], ap[q - 1], ap[q],
+                     ap[q + 1]);
+      weno5_grad_acc(fm[q + 2], fm[q + 1], fm[q], fm[q - 1], fm[q - 2], fb, am[q + 2], am[q + 1], am[q], am[q - 1],
+                     am[q - 2]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ARUN; ++k) {
+    pb[k * DS] = ap[k + 5] + am[k + 5];
+    mb[k * DS] = ap[k + 5] - am[k + 5];
+  }
+}
+
+// Level-set line: output points k = 0 .. ARUN-1 receive phibar_k = (Dbar_{k-1} - Dbar_k) / h, where
+// D_n = (phi_{n+1} - phi_n) / h and Dbar collects hb^- dW/dD over phi^-_i = W(D_{i-3..i+1}) and hb^+
+// over phi^+_i = W(D_{i+2..i-2}) for the cells i = -3 .. ARUN+2 of the line.
+template <typename real>
+__device__ __forceinline__ void adj_phi_line(const real* __restrict__ ph, const real* __restrict__ hm,
+                                                   const real* __restrict__ hp, int S, real rd, real* __restrict__ dst,
+                                                   int DS) {
+  constexpr int ND = ARUN + 11;  // differences D_n, n = -6 .. ARUN+4, index n + 6
+  real D[ND], Db[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    const int n = q - 6;
+    D[q] = (ph[(n + 1) * S] - ph[n * S]) * rd;
+    Db[q] = real(0);
+  }
+#pragma unroll
+  for (int i = -3; i <= ARUN + 2; ++i) {
+    const real bm = hm[i * S], bp = hp[i * S];
+    const int q = i + 6;
+    if (bm != real(0))
+      weno5_grad_acc(D[q - 3], D[q - 2], D[q - 1], D[q], D[q + 1], bm, Db[q - 3], Db[q - 2], Db[q - 1], Db[q],
+                     Db[q + 1]);
+    if (bp != real(0))
+      weno5_grad_acc(D[q + 2], D[q + 1], D[q], D[q - 1], D[q - 2], bp, Db[q + 2], Db[q + 1], Db[q], Db[q - 1],
+                     Db[q - 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < ARUN; ++k) dst[k * DS] += (Db[k - 1 + 6] - Db[k + 6]) * rd;
+}
+
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) adj_line_kernel(AdjParams<real> P, int tiles_x) {
+  using TL = ATile<real, NF>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sm = reinterpret_cast<real*>(smem_raw);
+  real* sW = sm + TL::OFF_W;
+  real* sP = sm + TL::OFF_P;
+  real* sN = sm + TL::OFF_N;
+  real* sH = sm + TL::OFF_H;
+  real* sPB = sm + TL::OFF_PB;
+  real* sMB = sm + TL::OFF_MB;
+  real* sMU = sm + TL::OFF_MU;
+  const int tid = threadIdx.x;
+  constexpr int NT = 256;
+  const long long fs = P.fstride;
+  // output points are padded-grid points: columns 1 .. nx+6 (cells -3 .. nx+2), rows 0 .. ny+5
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int c0 = 1 + tx * ATX, r0 = ty * ATY;  // padded coordinates of the tile's first output point
+  const int bc0 = c0 - AHX, br0 = r0 - AHX;    // padded coordinates of box point (0, 0)
+  const real gamma = P.gamma;
+
+  // ---- load the boxes (zero outside the allocation), primitive variables
+  for (int idx = tid; idx < TL::BOX; idx += NT) {
+    const int r = idx / ABW, c = idx - r * ABW;
+    const int gr = br0 + r, gc = bc0 + c;
+    const bool in = gr >= 0 && gr < P.rows && gc >= 0 && gc < P.pitch;
+    const long long k = static_cast<long long>(gr) * P.pitch + gc;
+    real wv[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      wv[f] = in ? P.W[f * fs + k] : real(0);
+      sW[f * TL::BOX + idx] = wv[f];
+      sN[f * TL::BOX + idx] = in ? P.nu[f * fs + k] : real(0);
+    }
+    if constexpr (NF == 5) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sH[q * TL::BOX + idx] = in ? P.hb[q * fs + k] : real(0);
+    }
+    const real u = wv[1] / wv[0], v = wv[2] / wv[0];
+    sP[0 * TL::BOX + idx] = u;
+    sP[1 * TL::BOX + idx] = v;
+    sP[2 * TL::BOX + idx] = (gamma - real(1)) * (wv[3] - real(0.5) * (wv[1] * u + wv[2] * v));
+  }
+  for (int idx = tid; idx < NF * ATY * ATX; idx += NT) sMU[idx] = real(0);
+  __syncthreads();
+
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool xp = pass == 0;
+    const real alpha = xp ? P.ax : P.ay;
+    const real rd = static_cast<real>(1.0 / (xp ? P.dx : P.dy));
+    const int S = xp ? 1 : ABW;
+    const int DS = xp ? 1 : ATX;
+    // items: (field, line, run); x: ATY rows x 4 runs; y: ATX columns x 2 runs
+    const int per_c = xp ? ATY * (ATX / ARUN) : ATX * (ATY / ARUN);
+    for (int it = tid; it < NF * per_c; it += NT) {
+      const int c = it / per_c, rem = it - c * per_c;
+      int orow, ocol;  // first output point of the run, tile coordinates
+      if (xp) {
+        orow = rem % ATY;
+        ocol = (rem / ATY) * ARUN;
+      } else {
+        ocol = rem % ATX;
+        orow = (rem / ATX) * ARUN;
+      }
+      const int bidx = (orow + AHX) * ABW + (ocol + AHX);
+      if (c < 4) {
+        const int kind = (c == 0) ? 0 : (c == 3) ? 3 : ((c == 1) == xp) ? 1 : 2;
+        adj_hydro_line<real>(sW + c * TL::BOX + bidx, sW + (xp ? 1 : 2) * TL::BOX + bidx,
+                             sP + (xp ? 0 : 1) * TL::BOX + bidx, sP + 2 * TL::BOX + bidx, sN + c * TL::BOX + bidx, S,
+                             kind, alpha, rd, sPB + (c * ATY + orow) * ATX + ocol, sMB + (c * ATY + orow) * ATX + ocol,
+                             DS);
+      } else if constexpr (NF == 5) {
+        adj_phi_line<real>(sW + 4 * TL::BOX + bidx, sH + (xp ? 0 : 2) * TL::BOX + bidx,
+                                 sH + (xp ? 1 : 3) * TL::BOX + bidx, S, rd, sMU + (4 * ATY + orow) * ATX + ocol, DS);
+      }
+    }
+    __syncthreads();
+    // split and flux-Jacobian adjoint at every output point of the tile
+    for (int idx = tid; idx < ATY * ATX; idx += NT) {
+      const int orow = idx / ATX, ocol = idx - orow * ATX;
+      const int b = (orow + AHX) * ABW + (ocol + AHX);
+      const real rho = sW[b], mx = sW[TL::BOX + b], my = sW[2 * TL::BOX + b], E = sW[3 * TL::BOX + b];
+      real pb[4], mb[4];
+      bool any = false;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        pb[r] = sPB[(r * ATY + orow) * ATX + ocol];
+        mb[r] = sMB[(r * ATY + orow) * ATX + ocol];
+        any = any || pb[r] != real(0) || mb[r] != real(0);
+      }
+      if (!any) continue;  // also skips unfilled corner points
+      real J[4][4];
+      flux_jacobian<real>(xp ? 0 : 1, gamma, rho, mx, my, E, J);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        real acc = real(0.5) * alpha * mb[s];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc += real(0.5) * J[r][s] * pb[r];
+        sMU[(s * ATY + orow) * ATX + ocol] += acc;
+      }
+    }
+    __syncthreads();
+  }
+  // ---- write mu: interior points add to the point terms already there; frame points are set
+  for (int idx = tid; idx < ATY * ATX; idx += NT) {
+    const int orow = idx / ATX, ocol = idx - orow * ATX;
+    const int gr = r0 + orow, gc = c0 + ocol;
+    const int i = gc - GX, j = gr - GY;
+    if (gr >= P.ny + 2 * GY || gc >= P.nx + GX + 3) continue;
+    const bool ix = i >= 0 && i < P.nx, iy = j >= 0 && j < P.ny;
+    if (!ix && !iy) continue;  // corner: not part of the scheme
+    const long long k = static_cast<long long>(gr) * P.pitch + gc;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const real v = sMU[(f * ATY + orow) * ATX + ocol];
+      P.mu[f * fs + k] = (ix && iy) ? P.mu[f * fs + k] + v : v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- fold and blend
+
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) adj_blend_kernel(AdjParams<real> P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= P.nx) return;
+  const long long fs = P.fstride;
+  const int nx = P.nx, ny = P.ny;
+  const long long k = static_cast<long long>(j + GY) * P.pitch + i + GX;
+  real m[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) m[f] = P.mu[f * fs + k];
+  // adjoint of the ghost fill: every ghost point that is an image of (i, j) hands its adjoint back
+  auto take = [&](int gi, int gj, bool fx, bool fy) {
+    const long long g = static_cast<long long>(gj + GY) * P.pitch + gi + GX;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      real v = P.mu[f * fs + g];
+      if ((f == 1 && fx) || (f == 2 && fy)) v = -v;
+      m[f] += v;
+    }
+  };
+  if (i < 3 || i >= nx - 3) {
+    const int bl = P.bc[0], bh = P.bc[1];
+    if (bl == BC_PERIODIC) {
+      if (i >= nx - 3) take(i - nx, j, false, false);
+    } else if (bl == BC_TRANSMISSIVE) {
+      if (i == 0) { take(-1, j, false, false); take(-2, j, false, false); take(-3, j, false, false); }
+    } else if (i < 3) {
+      take(-1 - i, j, true, false);
+    }
+    if (bh == BC_PERIODIC) {
+      if (i < 3) take(nx + i, j, false, false);
+    } else if (bh == BC_TRANSMISSIVE) {
+      if (i == nx - 1) { take(nx, j, false, false); take(nx + 1, j, false, false); take(nx + 2, j, false, false); }
+    } else if (i >= nx - 3) {
+      take(2 * nx - 1 - i, j, true, false);
+    }
+  }
+  if (j < 3 || j >= ny - 3) {
+    const int bl = P.bc[2], bh = P.bc[3];
+    if (bl == BC_PERIODIC) {
+      if (j >= ny - 3) take(i, j - ny, false, false);
+    } else if (bl == BC_TRANSMISSIVE) {
+      if (j == 0) { take(i, -1, false, false); take(i, -2, false, false); take(i, -3, false, false); }
+    } else if (j < 3) {
+      take(i, -1 - j, false, true);
+    }
+    if (bh == BC_PERIODIC) {
+      if (j < 3) take(i, ny + j, false, false);
+    } else if (bh == BC_TRANSMISSIVE) {
+      if (j == ny - 1) { take(i, ny, false, false); take(i, ny + 1, false, false); take(i, ny + 2, false, false); }
+    } else if (j >= ny - 3) {
+      take(i, 2 * ny - 1 - j, false, true);
+    }
+  }
+  const real dt = static_cast<real>(P.dt), a = static_cast<real>(P.a), b = static_cast<real>(P.b);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const real nu = P.nu[f * fs + k];
+    const real o = b * (nu + dt * m[f]);
+    P.out[f * fs + k] = o;
+    if (P.acc_mode == 0) P.acc[f * fs + k] = a * nu;
+    else if (P.acc_mode == 1) P.acc[f * fs + k] += a * nu;
+    else P.acc[f * fs + k] += o;
+  }
+}
+
+}  // namespace hydro

@@ -14,6 +14,7 @@
 
 #include "../../include/hydro.h"
 #include "hydro_internal.cuh"
+#include "adjoint_kernel.cuh"
 
 using namespace hydro;
 
@@ -71,6 +72,16 @@ struct hydro_ctx {
   int ev_used = 0;
   cudaEvent_t done = nullptr;
   long long launches = 0;
+  // adjoint: padded work buffers (nu ping-pong, mu, hb, accumulator), checkpoints, segment states
+  void* adj_nu[2] = {nullptr, nullptr};
+  void* adj_mu = nullptr;
+  void* adj_hb = nullptr;
+  void* adj_acc = nullptr;
+  void* ckpt = nullptr;
+  size_t ckpt_cap = 0;
+  void* seg = nullptr;
+  size_t seg_cap = 0;
+  int ck_nsteps = -1, ck_every = 0;
   // batch plan (kept on the first member)
   std::vector<hydro_ctx*> plan_members;
   int plan_variant = -1;
@@ -448,6 +459,13 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->alpha_log);
   cudaFree(c->plan_params);
   cudaFree(c->plan_work);
+  cudaFree(c->adj_nu[0]);
+  cudaFree(c->adj_nu[1]);
+  cudaFree(c->adj_mu);
+  cudaFree(c->adj_hb);
+  cudaFree(c->adj_acc);
+  cudaFree(c->ckpt);
+  cudaFree(c->seg);
   if (c->host_scratch) cudaFreeHost(c->host_scratch);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->done) cudaEventDestroy(c->done);
@@ -829,28 +847,184 @@ int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nstep
   return batch_impl<float>(members, U, n, nsteps, t);
 }
 
-// ---- adjoint entry points (adjoint.cu holds the kernels and the sweep)
+// ---- discrete adjoint (frozen dt and stage alphas) and two-level checkpointing
+
+static int ensure_adjoint_buffers(hydro_ctx* c) {
+  if (c->adj_mu) return HYDRO_OK;
+  const size_t bytes = (size_t)c->nf * c->fstride * c->esize;
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&c->adj_nu[k], bytes));
+    CK(cudaMemsetAsync(c->adj_nu[k], 0, bytes, c->stream));  // zero ghost frame, never written
+  }
+  CK(cudaMalloc(&c->adj_mu, bytes));
+  CK(cudaMemsetAsync(c->adj_mu, 0, bytes, c->stream));
+  CK(cudaMalloc(&c->adj_acc, bytes));
+  CK(cudaMemsetAsync(c->adj_acc, 0, bytes, c->stream));
+  const size_t hb = (size_t)4 * c->fstride * c->esize;
+  CK(cudaMalloc(&c->adj_hb, hb));
+  CK(cudaMemsetAsync(c->adj_hb, 0, hb, c->stream));  // zero frame: only interior cells are written
+  return HYDRO_OK;
+}
+
+// caller-layout <-> padded-interior copies of a full state-shaped array
+template <typename real>
+static int copy_in(hydro_ctx* c, real* padded, const real* U) {
+  const hydro_config& g = c->cfg;
+  for (int f = 0; f < c->nf; ++f)
+    CK(cudaMemcpy2DAsync(padded + f * c->fstride + (long long)GY * c->pitch + GX, sizeof(real) * c->pitch,
+                         U + (size_t)f * g.nx * g.ny, sizeof(real) * g.nx, sizeof(real) * g.nx, g.ny,
+                         cudaMemcpyDeviceToDevice, c->stream));
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int copy_out(hydro_ctx* c, real* U, const real* padded) {
+  const hydro_config& g = c->cfg;
+  for (int f = 0; f < c->nf; ++f)
+    CK(cudaMemcpy2DAsync(U + (size_t)f * g.nx * g.ny, sizeof(real) * g.nx,
+                         padded + f * c->fstride + (long long)GY * c->pitch + GX, sizeof(real) * c->pitch,
+                         sizeof(real) * g.nx, g.ny, cudaMemcpyDeviceToDevice, c->stream));
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt, const double* alpha) {
+  int rc = ensure_adjoint_buffers(c);
+  if (rc) return rc;
+  // stage states U^n (A), U^(1) (B), U^(2) (C) with the frozen alphas and dt
+  rc = pack_state<real>(c, Un, 0.0);
+  if (rc) return rc;
+  Scratch<real>* s = scr<real>(c);
+  CK(launch_set_frozen<real>(&s->frozen_dt, dt, &s->frozen_alpha[0][0], alpha, c->stream));
+  c->launches++;
+  rc = launch_one<real>(c, 3, 0, 0, RK_A[0], RK_B[0], c->stream);
+  if (!rc) rc = launch_one<real>(c, 4, 1, 0, RK_A[1], RK_B[1], c->stream);
+  if (rc) return rc;
+  real* nu[2] = {static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1])};
+  rc = copy_in<real>(c, nu[0], lam);
+  if (rc) return rc;
+  const hydro_config& g = c->cfg;
+  AdjParams<real> P{};
+  P.mu = static_cast<real*>(c->adj_mu);
+  P.hb = static_cast<real*>(c->adj_hb);
+  P.acc = static_cast<real*>(c->adj_acc);
+  P.fstride = c->fstride;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.pitch = c->pitch;
+  P.rows = c->rows;
+  for (int k = 0; k < 4; ++k) P.bc[k] = g.bc[k];
+  P.geometry = g.geometry;
+  P.gamma = static_cast<real>(g.gamma);
+  P.gravity = static_cast<real>(g.gravity_y);
+  P.flame_speed = static_cast<real>(g.flame_speed);
+  P.dx = (g.x1 - g.x0) / g.nx;
+  P.dy = (g.y1 - g.y0) / g.ny;
+  P.x0 = g.x0;
+  P.dt = dt;
+  // reverse stages 2, 1, 0
+  const int order[3] = {2, 1, 0};
+  for (int q = 0; q < 3; ++q) {
+    const int k = order[q];
+    P.W = bufp<real>(c, k);  // stage k's input: A, B, C
+    P.nu = nu[q & 1];
+    P.out = nu[(q + 1) & 1];
+    P.ax = static_cast<real>(alpha[2 * k]);
+    P.ay = static_cast<real>(alpha[2 * k + 1]);
+    P.a = RK_A[k];
+    P.b = RK_B[k];
+    P.acc_mode = (q == 0) ? 0 : (q == 1) ? 1 : 2;
+    int nl = 0;
+    CK(launch_adjoint_stage<real>(P, c->nf, c->stream, &nl));
+    c->launches += nl;
+  }
+  rc = copy_out<real>(c, lam, static_cast<const real*>(c->adj_acc));
+  if (rc) return rc;
+  return read_status<real>(c, nullptr, nullptr);
+}
 
 int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, const double alpha[6]) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U_n || !lambda || !alpha || !(dt >= 0.0)) return fail(c, HYDRO_EINVAL, "bad adjoint arguments");
-  (void)dt;
-  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+  for (int k = 0; k < 6; ++k)
+    if (!(alpha[k] >= 0.0) || !std::isfinite(alpha[k])) return fail(c, HYDRO_EINVAL, "alphas must be finite, >= 0");
+  if (c->cfg.dtype == HYDRO_F64)
+    return adjoint_step_impl<double>(c, (const double*)U_n, (double*)lambda, dt, alpha);
+  return adjoint_step_impl<float>(c, (const float*)U_n, (float*)lambda, dt, alpha);
 }
 
 int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if (!U || nsteps < 0) return fail(c, HYDRO_EINVAL, "bad arguments");
-  (void)every;
-  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+  if (!U || nsteps < 1) return fail(c, HYDRO_EINVAL, "bad arguments");
+  if (every <= 0) every = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+  every = std::min(every, nsteps);
+  const int nseg = (nsteps + every - 1) / every;
+  const size_t state = (size_t)c->nf * c->cfg.nx * c->cfg.ny * c->esize;
+  if (c->ckpt_cap < (size_t)nseg) {
+    cudaFree(c->ckpt);
+    c->ckpt = nullptr;
+    c->ckpt_cap = 0;
+    CK(cudaMalloc(&c->ckpt, state * nseg));
+    c->ckpt_cap = nseg;
+  }
+  rc = hydro_record(c, nsteps);
+  if (rc) return rc;
+  double t = 0.0;
+  for (int sg = 0; sg < nseg; ++sg) {
+    CK(cudaMemcpyAsync(static_cast<char*>(c->ckpt) + state * sg, U, state, cudaMemcpyDeviceToDevice, c->stream));
+    const int n = std::min(every, nsteps - sg * every);
+    rc = hydro_step(c, U, n, &t, nullptr);
+    if (rc) return rc;
+  }
+  c->ck_nsteps = nsteps;
+  c->ck_every = every;
+  return HYDRO_OK;
+}
+
+template <typename real>
+static int sweep_impl(hydro_ctx* c, real* lam) {
+  const int N = c->ck_nsteps, every = c->ck_every;
+  std::vector<double> dtl(N), al(6 * (size_t)N);
+  int got = 0;
+  int rc = hydro_get_log(c, N, dtl.data(), al.data(), &got);
+  if (rc) return rc;
+  const size_t elems = (size_t)c->nf * c->cfg.nx * c->cfg.ny;
+  const size_t state = elems * sizeof(real);
+  if (c->seg_cap < (size_t)every) {
+    cudaFree(c->seg);
+    c->seg = nullptr;
+    c->seg_cap = 0;
+    CK(cudaMalloc(&c->seg, state * every));
+    c->seg_cap = every;
+  }
+  real* seg = static_cast<real*>(c->seg);
+  const int nseg = (N + every - 1) / every;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int s0 = sg * every, s1 = std::min(N, s0 + every);
+    // recompute the segment's states from its checkpoint with the recorded dt / alphas
+    CK(cudaMemcpyAsync(seg, static_cast<const char*>(c->ckpt) + state * sg, state, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    for (int st = s0; st + 1 < s1; ++st) {
+      real* nxt = seg + elems * (st - s0 + 1);
+      CK(cudaMemcpyAsync(nxt, seg + elems * (st - s0), state, cudaMemcpyDeviceToDevice, c->stream));
+      rc = step_impl<real>(c, nxt, 1, nullptr, nullptr, &dtl[st], &al[6 * (size_t)st]);
+      if (rc) return rc;
+    }
+    for (int st = s1 - 1; st >= s0; --st) {
+      rc = adjoint_step_impl<real>(c, seg + elems * (st - s0), lam, dtl[st], &al[6 * (size_t)st]);
+      if (rc) return rc;
+    }
+  }
+  return HYDRO_OK;
 }
 
 int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!lambda) return fail(c, HYDRO_EINVAL, "null lambda");
-  return fail(c, HYDRO_ESTATE, "adjoint not available in this build");
+  if (c->ck_nsteps < 1 || !c->ckpt) return fail(c, HYDRO_ESTATE, "no checkpointed forward run to reverse");
+  if (c->cfg.dtype == HYDRO_F64) return sweep_impl<double>(c, (double*)lambda);
+  return sweep_impl<float>(c, (float*)lambda);
 }
-

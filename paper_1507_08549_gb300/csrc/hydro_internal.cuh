@@ -103,6 +103,13 @@ template <typename real>
 cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geometry, double x0, double dx,
                           double dy, double* partials, int nblocks, double* out, cudaStream_t s);
 
+// Discrete adjoint of one frozen RK stage (adjoint_kernel.cuh): point terms, line adjoints over the
+// padded grid with its ghost frame, ghost fold and RK blend. Buffers are padded like the states.
+template <typename real>
+struct AdjParams;
+template <typename real>
+cudaError_t launch_adjoint_stage(const AdjParams<real>& P, int nfields, cudaStream_t s, int* launches);
+
 // ------------------------------------------------------------------------------ device helpers
 
 #ifdef __CUDACC__

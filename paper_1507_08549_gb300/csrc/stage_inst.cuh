@@ -1,6 +1,7 @@
 // stage_inst.cuh -- host launchers of the stage kernel variants and the small kernels for one
 // precision (included by stage_f32.cu / stage_f64.cu with HYDRO_REAL defined).
 #pragma once
+#include "adjoint_kernel.cuh"
 #include "aux_kernels.cuh"
 
 namespace hydro {
@@ -116,6 +117,37 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
     totals_partial_kernel<HYDRO_REAL, 4><<<nblocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, partials);
   totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, nfields, out);
   return cudaGetLastError();
+}
+
+namespace {
+template <int NF>
+cudaError_t adj_nf(const AdjParams<HYDRO_REAL>& P, cudaStream_t s, int* launches) {
+  dim3 pg((P.nx + 255) / 256, P.ny);
+  adj_point_kernel<HYDRO_REAL, NF><<<pg, 256, 0, s>>>(P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // tiles over the padded grid: columns 1 .. nx+6, rows 0 .. ny+5
+  const int tiles_x = (P.nx + 6 + ATX - 1) / ATX, tiles_y = (P.ny + 6 + ATY - 1) / ATY;
+  static const cudaError_t cfg = [] {
+    cudaError_t r = cudaFuncSetAttribute(adj_line_kernel<HYDRO_REAL, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ATile<HYDRO_REAL, NF>::BYTES);
+    if (r != cudaSuccess) (void)cudaGetLastError();
+    return r;
+  }();
+  if (cfg != cudaSuccess) return cfg;
+  adj_line_kernel<HYDRO_REAL, NF><<<tiles_x * tiles_y, 256, ATile<HYDRO_REAL, NF>::BYTES, s>>>(P, tiles_x);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_blend_kernel<HYDRO_REAL, NF><<<pg, 256, 0, s>>>(P);
+  if (launches) *launches += 3;
+  return cudaGetLastError();
+}
+}  // namespace
+
+template <>
+cudaError_t launch_adjoint_stage<HYDRO_REAL>(const AdjParams<HYDRO_REAL>& P, int nfields, cudaStream_t s,
+                                             int* launches) {
+  return nfields == 5 ? adj_nf<5>(P, s, launches) : adj_nf<4>(P, s, launches);
 }
 
 }  // namespace hydro

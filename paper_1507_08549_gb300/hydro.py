@@ -300,3 +300,40 @@ def hydro_batch_step(members: list[Hydro], states: list, nsteps: int, t=None):
         msg = lib.hydro_last_error(members[0].ctx)
         raise HydroError(rc, f"hydro_batch_step: {msg.decode() if msg else ''}")
     return tt
+
+
+def _autograd():
+    import torch
+
+    class HydroRollout(torch.autograd.Function):
+        """U_N = (nsteps SSP-RK3 steps)(U_0) with a discrete-adjoint backward: the forward run keeps
+        checkpoints every ``checkpoint_every`` steps and records dt and the stage alphas; backward
+        replays each segment from its checkpoint and runs the adjoint stages in reverse
+        (hydro_forward_checkpointed / hydro_adjoint_sweep). dt and the alphas are held at their
+        recorded values, so the gradient is that of the frozen map."""
+
+        @staticmethod
+        def forward(ctx, U0, solver, nsteps, checkpoint_every):
+            U = U0.detach().clone().contiguous()
+            solver.forward_checkpointed(U, int(nsteps), int(checkpoint_every))
+            ctx.solver = solver
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            lam = gU.detach().to(ctx.solver.torch_dtype).clone().contiguous()
+            ctx.solver.adjoint_sweep(lam)
+            return lam, None, None, None
+
+    return HydroRollout
+
+
+_ROLLOUT = None
+
+
+def rollout(solver: Hydro, U0, nsteps: int, checkpoint_every: int = 0):
+    """Differentiable multi-step rollout through the discrete adjoint (see HydroRollout)."""
+    global _ROLLOUT
+    if _ROLLOUT is None:
+        _ROLLOUT = _autograd()
+    return _ROLLOUT.apply(U0, solver, nsteps, checkpoint_every)

@@ -1,0 +1,124 @@
+"""GPU discrete adjoint (frozen dt and stage alphas) against the FP64 oracle's adjoint, central finite
+differences of the GPU's own frozen forward map, and through torch autograd (the gradient of the final
+kinetic energy with respect to the initial density at fixed u, v, p)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_08549_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _hydro():
+    from paper_1507_08549_gb300 import hydro
+    return hydro
+
+
+def _rel_linf(a, b):
+    return max(np.abs(a[f] - b[f]).max() / max(np.abs(b[f]).max(), 1e-300) for f in range(b.shape[0]))
+
+
+def _state(nx, ny, nf, seed):
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(wl.centres(nx, 0, 1), wl.centres(ny, 0, 1))
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X + 0.3) * np.cos(2 * np.pi * Y) + 0.02 * rng.random((ny, nx))
+    u = 0.3 + 0.2 * np.cos(2 * np.pi * Y) + 0.01 * rng.random((ny, nx))
+    v = -0.25 + 0.1 * np.sin(2 * np.pi * X)
+    p = 1.0 + 0.1 * rng.random((ny, nx))
+    phi = 0.3 - np.hypot(X - 0.45, Y - 0.55) + 0.1 * X
+    return wl.conserved(1.4, rho, u, v, p, phi if nf == 5 else None)
+
+
+CASES = {
+    "periodic": dict(),
+    "rz_gravity_phi": dict(geometry=1, gravity=-0.8, nfields=5, flame_speed=0.07,
+                           bc=(wl.AXIS, wl.TRANSMISSIVE, wl.REFLECT, wl.TRANSMISSIVE)),
+    "walls_phi": dict(nfields=5, flame_speed=0.03, bc=(wl.REFLECT, wl.TRANSMISSIVE, wl.PERIODIC, wl.PERIODIC)),
+}
+
+
+def _problem(case, nx=71, ny=47):
+    p = wl.Problem(name=case, nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, **CASES[case])
+    return p.with_(U0=_state(nx, ny, p.nfields, 1))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_adjoint_step_matches_oracle(case):
+    """One frozen step's adjoint, FP64 to 1e-12 relative L-inf, FP32 to 1e-4."""
+    hydro = _hydro()
+    p = _problem(case)
+    _, _, _, dtl, al = oracle.step(p, p.U0, 1, log=True)
+    lam = np.random.default_rng(4).normal(size=p.U0.shape)
+    ref = oracle.adjoint_step(p, p.U0, lam, dtl[0], al[0])
+    for dt, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        h = hydro.Hydro(p, dtype=dt)
+        L = h.state(lam)
+        h.adjoint_step(h.state(p.U0), L, dtl[0], al[0].ravel())
+        got = L.double().cpu().numpy()
+        h.close()
+        assert _rel_linf(got, ref) <= tol, (dt, _rel_linf(got, ref))
+
+
+def _kinetic(p, U):
+    return float(np.sum(0.5 * (U[1] ** 2 + U[2] ** 2) / U[0]) * p.dx * p.dy)
+
+
+def test_gradient_config_fd_fp64_and_fp32():
+    """Gradient configuration: 256^2 periodic Fourier-mode state, 200 steps, checkpoints every 20 steps,
+    d KE(U^200) / d rho_0 at fixed u, v, p through torch autograd, against central differences of the
+    frozen forward map on 32 seeded cells (FP64), and FP32 against FP64."""
+    import torch
+    hydro = _hydro()
+    p, (rho, u, v, pr) = wl.fourier_modes(256, nsteps=200)
+    grads = {}
+    for dt in ("f64", "f32"):
+        h = hydro.Hydro(p, dtype=dt)
+        td = h.torch_dtype
+        rho_t = torch.tensor(rho, dtype=torch.float64, device="cuda", requires_grad=True)
+        ut, vt, pt = (torch.tensor(a, dtype=torch.float64, device="cuda") for a in (u, v, pr))
+        U0 = torch.stack([rho_t, rho_t * ut, rho_t * vt, pt / 0.4 + 0.5 * rho_t * (ut * ut + vt * vt)]).to(td)
+        UN = hydro.rollout(h, U0, 200, 20)
+        KE = (0.5 * (UN[1].double() ** 2 + UN[2].double() ** 2) / UN[0].double()).sum() * p.dx * p.dy
+        KE.backward()
+        grads[dt] = rho_t.grad.cpu().numpy()
+        if dt == "f64":
+            dtl, al = h.get_log(200)
+            rng = np.random.default_rng(2015)
+            cells = rng.integers(0, 256, size=(32, 2))
+            eps = 1e-6
+            for (j, i) in cells:
+                vals = []
+                for sgn in (1.0, -1.0):
+                    r2 = rho.copy()
+                    r2[j, i] += sgn * eps
+                    V = h.state(wl.conserved(1.4, r2, u, v, pr))
+                    h.step_frozen(V, dtl, al)
+                    vals.append(_kinetic(p, V.cpu().numpy()))
+                fd = (vals[0] - vals[1]) / (2 * eps)
+                g = grads["f64"][j, i]
+                assert abs(fd - g) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grads["f64"]).max()), (j, i, fd, g)
+        h.close()
+    err32 = np.abs(grads["f32"] - grads["f64"]).max() / np.abs(grads["f64"]).max()
+    assert err32 <= 1e-3, err32
+
+
+def test_gradient_matches_oracle_reduced():
+    """64^2, 30 steps, every 10: the GPU FP64 gradient dJ/dU_0 against the oracle's adjoint run."""
+    hydro = _hydro()
+    p, _ = wl.fourier_modes(64, nsteps=30)
+    UN_ref = oracle.step(p, p.U0, 30)[0]
+    rho, mx, my = UN_ref[0], UN_ref[1], UN_ref[2]
+    lamN = np.zeros_like(UN_ref)
+    lamN[0] = -0.5 * (mx ** 2 + my ** 2) / rho ** 2 * p.dx * p.dy
+    lamN[1] = mx / rho * p.dx * p.dy
+    lamN[2] = my / rho * p.dx * p.dy
+    ref, _, _, _ = oracle.adjoint_run(p, p.U0, 30, lamN)
+    h = hydro.Hydro(p, dtype="f64")
+    U = h.state(p.U0)
+    h.forward_checkpointed(U, 30, 10)
+    assert np.array_equal(U.cpu().numpy(), UN_ref)
+    L = h.state(lamN)
+    h.adjoint_sweep(L)
+    assert _rel_linf(L.cpu().numpy(), ref) <= 1e-12
+    h.close()
