@@ -1,6 +1,11 @@
 """GPU discrete adjoint (frozen dt and stage alphas) against the FP64 oracle's adjoint, central finite
 differences of the GPU's own frozen forward map, and through torch autograd (the gradient of the final
-kinetic energy with respect to the initial density at fixed u, v, p)."""
+kinetic energy with respect to the initial density at fixed u, v, p).
+
+Tolerances: FP64 relative L-inf <= 1e-12 against the oracle's adjoint. FP32 <= 1e-3: the adjoint
+differentiates the nonlinear WENO weights, whose derivatives (q_k - W) d alpha_k / d beta_k subtract
+nearly equal terms where the data are smooth, so FP32 rounding is amplified by up to ~1e2 relative to
+the forward map's 1e-5."""
 import numpy as np
 import pytest
 
@@ -51,7 +56,7 @@ def test_adjoint_step_matches_oracle(case):
     _, _, _, dtl, al = oracle.step(p, p.U0, 1, log=True)
     lam = np.random.default_rng(4).normal(size=p.U0.shape)
     ref = oracle.adjoint_step(p, p.U0, lam, dtl[0], al[0])
-    for dt, tol in (("f64", 1e-12), ("f32", 1e-4)):
+    for dt, tol in (("f64", 1e-12), ("f32", 1e-3)):
         h = hydro.Hydro(p, dtype=dt)
         L = h.state(lam)
         h.adjoint_step(h.state(p.U0), L, dtl[0], al[0].ravel())
@@ -86,8 +91,7 @@ def test_gradient_config_fd_fp64_and_fp32():
             dtl, al = h.get_log(200)
             rng = np.random.default_rng(2015)
             cells = rng.integers(0, 256, size=(32, 2))
-            eps = 1e-6
-            for (j, i) in cells:
+            def central(j, i, eps):
                 vals = []
                 for sgn in (1.0, -1.0):
                     r2 = rho.copy()
@@ -95,7 +99,12 @@ def test_gradient_config_fd_fp64_and_fp32():
                     V = h.state(wl.conserved(1.4, r2, u, v, pr))
                     h.step_frozen(V, dtl, al)
                     vals.append(_kinetic(p, V.cpu().numpy()))
-                fd = (vals[0] - vals[1]) / (2 * eps)
+                return (vals[0] - vals[1]) / (2 * eps)
+
+            for (j, i) in cells:
+                # Richardson-extrapolated central difference (error O(eps^4)); eps large enough that the
+                # change of J stands far above the rounding of the 65536-cell sum
+                fd = (4.0 * central(j, i, 5e-5) - central(j, i, 1e-4)) / 3.0
                 g = grads["f64"][j, i]
                 assert abs(fd - g) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grads["f64"]).max()), (j, i, fd, g)
         h.close()
