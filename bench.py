@@ -98,6 +98,7 @@ class Clocks:
 WORKLOADS = {
     # name: (generator, default dtype, description)
     "blobs_blast_8192": ("large forward throughput: 8192^2 periodic, 5 fields, blobs + blast", "f32"),
+    "blobs_blast_4096": ("the same state generator at 4096^2 (profiling case)", "f32"),
     "rayleigh_taylor_1024x2048": ("axisymmetric Rayleigh-Taylor with gravity and level set", "f32"),
     "advected_wave_128": ("128^2 periodic advected density wave (plain method)", "f64"),
     "quadrant_ensemble_64": ("64 quadrant Riemann problems of uneven sizes, batched", "f32"),
@@ -109,6 +110,8 @@ def workload(name: str):
     from paper_1507_08549_gb300 import workloads as wl
     if name == "blobs_blast_8192":
         return wl.blobs_blast(8192)
+    if name == "blobs_blast_4096":
+        return wl.blobs_blast(4096)
     if name == "rayleigh_taylor_1024x2048":
         return wl.rayleigh_taylor(1024, 2048)
     if name == "advected_wave_128":
@@ -315,6 +318,13 @@ def run(args):
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
     roof = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1))
     # end to end through the public host-buffer entry: every step copies the state in and out
+    if args.quick:
+        h.close()
+        if rank == 0:
+            cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F, "cells": cells, "tile": info}
+            print(json.dumps(_line(args, world, value, ms, dtype, cfg, {"roofline": roof, "gpu_launches": gpu_launches,
+                                                                       "clocks": clk})), flush=True)
+        return 0
     Uh = U.cpu().numpy().copy()
     if torch.cuda.is_available():
         Uh_pinned = torch.from_numpy(Uh).pin_memory().numpy()
@@ -400,6 +410,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="forward timing only (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2)
