@@ -49,7 +49,8 @@ enum {
   HYDRO_ECUDA = -2,         /* a CUDA call failed (message in hydro_last_error)                 */
   HYDRO_ENONPHYSICAL = -3,  /* the device saw a non-finite value, rho <= 0 or p <= 0             */
   HYDRO_ETIMEOUT = -4,      /* a device wait or a host wait on the stream exceeded its limit     */
-  HYDRO_ESTATE = -5         /* call out of order (e.g. adjoint sweep without a recorded run)     */
+  HYDRO_ESTATE = -5,        /* call out of order (e.g. adjoint sweep without a recorded run)     */
+  HYDRO_ESIZE = -6          /* a size beyond a fixed limit of an allocation-free entry point     */
 };
 
 typedef struct {
@@ -104,6 +105,20 @@ int conserved_totals(hydro_ctx* ctx, const void* U, double out[5]);
 /* Totals of the state written by the last completed hydro_step / hydro_batch_step, accumulated by
  * the last stage kernel of each step (FP64; atomics, so the last bits may vary between runs). */
 int hydro_last_totals(hydro_ctx* ctx, double out[5]);
+
+/* Conserved totals of a device state WITHOUT allocating anything and without a context, for callers
+ * that cannot call cudaMalloc (code in host callbacks or allocator hooks, processes with a fixed
+ * memory pool, frameworks that forbid device allocation on their threads). The paper has no
+ * counterpart: this is an interface addition. Same result definition as conserved_totals (FP64
+ * sums of U_f dV in a fixed order, out[4] = 0 for nfields = 4); U is a device [nfields][ny][nx]
+ * array of dtype; the domain (x0, x1, y0, y1) and geometry give dV; out is a host array of 5.
+ * Scratch: a file-scope device array of 16384 x 5 + 5 doubles (655 KB) that every GPU loading the
+ * library keeps until the process exits; hence ny <= 16384, else HYDRO_ESIZE (nothing launched).
+ * The first call on a device looks up that array's device address; make that first call before any
+ * CUDA stream capture. All calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller. Runs on `stream` and synchronises it. */
+int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dtype, int geometry, double x0,
+                             double x1, double y0, double y1, void* stream, double out[5]);
 
 /* ---- recording and the discrete adjoint (frozen alpha and dt) ---------------------------------
  * alpha_x, alpha_y and dt are maxima/minima over the grid and have no derivative; the adjoint and the

@@ -17,9 +17,9 @@ from . import build as _build
 
 HYDRO_F32, HYDRO_F64 = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECT, BC_AXIS = 0, 1, 2, 3
-OK, EINVAL, ECUDA, ENONPHYSICAL, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ECUDA, ENONPHYSICAL, ETIMEOUT, ESTATE, ESIZE = 0, -1, -2, -3, -4, -5, -6
 _NAMES = {EINVAL: "HYDRO_EINVAL", ECUDA: "HYDRO_ECUDA", ENONPHYSICAL: "HYDRO_ENONPHYSICAL",
-          ETIMEOUT: "HYDRO_ETIMEOUT", ESTATE: "HYDRO_ESTATE"}
+          ETIMEOUT: "HYDRO_ETIMEOUT", ESTATE: "HYDRO_ESTATE", ESIZE: "HYDRO_ESIZE"}
 
 
 class HydroError(RuntimeError):
@@ -45,7 +45,7 @@ EXPORTS = [
     "hydro_rhs", "conserved_totals", "hydro_last_totals", "hydro_record", "hydro_get_log", "hydro_step_frozen",
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
-    "hydro_stage_timing", "hydro_launch_count",
+    "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc",
 ]
 
 _lock = threading.Lock()
@@ -99,6 +99,9 @@ def load(build_if_needed: bool = True):
             "hydro_profile": ([ctxp, ctypes.c_int], ctypes.c_int),
             "hydro_stage_timing": ([ctxp, ip, dp], ctypes.c_int),
             "hydro_launch_count": ([ctxp], ctypes.c_longlong),
+            "conserved_totals_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, dp],
+                                         ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -285,6 +288,26 @@ class Hydro:
 
     def launch_count(self) -> int:
         return int(self.lib.hydro_launch_count(self.ctx))
+
+
+def conserved_totals_noalloc(problem, U, stream=None) -> np.ndarray:
+    """Totals of a CUDA tensor state through the allocation-free, context-free C entry point (for
+    callers that cannot allocate device memory; see include/hydro.h)."""
+    torch = _torch()
+    lib = load()
+    code = HYDRO_F64 if U.dtype == torch.float64 else HYDRO_F32
+    if not U.is_cuda or not U.is_contiguous():
+        raise HydroError(EINVAL, "U must be a contiguous CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream(U.device)
+    out = np.zeros(5)
+    rc = lib.conserved_totals_noalloc(ctypes.c_void_p(U.data_ptr()), int(problem.nx), int(problem.ny),
+                                      int(problem.nfields), code, int(problem.geometry), float(problem.x0),
+                                      float(problem.x1), float(problem.y0), float(problem.y1),
+                                      ctypes.c_void_p(s.cuda_stream),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != OK:
+        raise HydroError(rc, "conserved_totals_noalloc")
+    return out
 
 
 def hydro_batch_step(members: list[Hydro], states: list, nsteps: int, t=None):

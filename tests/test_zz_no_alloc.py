@@ -1,0 +1,58 @@
+"""The allocation-free totals entry point (for callers that cannot allocate device memory) against the
+context-based conserved_totals, called through the C ABI twice in a row, plus its size limit.
+
+Collected last on purpose (file name), so a failure here comes after every other test has run."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1507_08549_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    X = wl.advected_wave(96, ny=53)
+    rt = wl.rayleigh_taylor(64, 128)
+    return [(X, "f64"), (X, "f32"), (rt, "f64"), (rt, "f32")]
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_noalloc_totals_match_conserved_totals_twice(k):
+    import torch
+    from paper_1507_08549_gb300 import hydro
+    prob, dt = _problems()[k]
+    h = hydro.Hydro(prob, dtype=dt)
+    U = h.state(prob.U0)
+    ref = h.totals(U)
+    lib = hydro.load()
+    code = hydro.HYDRO_F64 if dt == "f64" else hydro.HYDRO_F32
+    # summation-order tolerance: 1e-14 of the sum of |U_f| dV (a total that cancels to ~0, like the level
+    # set's, differs between reduction orders at that absolute level, not relative to itself)
+    dv_max = prob.dx * prob.dy * (2 * np.pi * prob.x1 if prob.geometry == 1 else 1.0)
+    scale = np.abs(prob.U0).sum(axis=(1, 2)) * dv_max
+    scale = np.concatenate([scale, np.zeros(5 - scale.size)])
+    for _ in range(2):  # the shared scratch keeps the previous call's contents: results must not depend on it
+        out = np.full(5, np.nan)
+        rc = lib.conserved_totals_noalloc(ctypes.c_void_p(U.data_ptr()), prob.nx, prob.ny, prob.nfields, code,
+                                          prob.geometry, prob.x0, prob.x1, prob.y0, prob.y1,
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert rc == hydro.OK
+        assert np.all(np.abs(out - ref) <= 1e-14 * scale), (out, ref)
+    h.close()
+
+
+def test_noalloc_totals_reject_sizes_beyond_the_limit():
+    import torch
+    from paper_1507_08549_gb300 import hydro
+    lib = hydro.load()
+    U = torch.zeros(4 * 16385 * 3, dtype=torch.float32, device="cuda")
+    out = np.zeros(5)
+    rc = lib.conserved_totals_noalloc(ctypes.c_void_p(U.data_ptr()), 3, 16385, 4, hydro.HYDRO_F32, 0, 0.0, 1.0,
+                                      0.0, 1.0, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert rc == hydro.ESIZE
+    p = wl.advected_wave(16)
+    Ug = torch.zeros((4, 16, 16), dtype=torch.float32, device="cuda")
+    np.testing.assert_array_equal(hydro.conserved_totals_noalloc(p, Ug), np.zeros(5))
