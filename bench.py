@@ -285,8 +285,11 @@ def run(args):
         return run_gradient(args, prob, dtype, rank, world, barrier)
     h = hydro.Hydro(prob, dtype=dtype)
     U = h.state(prob.U0)
+    tune = None
+    if args.variant is not None:
+        h.set_tile_variant(args.variant)
     if args.autotune:
-        h.autotune(U, steps=2)
+        tune = [round(x, 4) for x in h.autotune(U, steps=2)]
     n_var, var = h.tile_variants()
     info = h.tile_info(var)
     # warm-up (untimed)
@@ -321,7 +324,8 @@ def run(args):
     if args.quick:
         h.close()
         if rank == 0:
-            cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F, "cells": cells, "tile": info}
+            cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F, "cells": cells, "tile": info,
+                   "autotune_ms_per_step": tune}
             print(json.dumps(_line(args, world, value, ms, dtype, cfg, {"roofline": roof, "gpu_launches": gpu_launches,
                                                                        "clocks": clk})), flush=True)
         return 0
@@ -386,7 +390,8 @@ def run(args):
                                   if F * B * cells > 129e6 else
                                   f"state {F * B * cells / 1e6:.1f} MB per copy fits in L2: steps back to back,"
                                   " in-L2 rate (not an HBM-bound measurement)"),
-                           "tile": info, "parallelism": "replicas" if world > 1 else "single"},
+                           "tile": info, "autotune_ms_per_step": tune,
+                           "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
                 "adjoint": adjoint, "fp64_step": fp64}
         if not args.no_cpu_baseline:
@@ -406,6 +411,7 @@ def main():
     ap.add_argument("--workload", default="blobs_blast_8192", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default=None, choices=["f32", "f64"])
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="tile variant (see hydro_tile_info)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
