@@ -17,6 +17,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -54,7 +55,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hydro_bench_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:
@@ -175,15 +176,42 @@ def run_reference(args):
     return 0
 
 
-def roofline(F, B, cells, avg_launch_ms):
-    """HBM roofline of the stage kernel: algorithmic bytes per launch = 8 F B per cell per step (stage 1
-    reads U^n and writes U^(1); stages 2 and 3 read U^n and the stage state and write) over 3 launches."""
+# Measured DRAM traffic of one stage launch, from an ncu capture of the 4096^2 blobs + blast case
+# (dram__bytes_read.sum + dram__bytes_write.sum of stage 1: 640.2 MB for 16.78 M cells), scaled to a
+# launch by cells processed; None for other states (set to None whenever the stage kernel changes).
+TRAFFIC_BYTES_PER_CELL_STAGE1_F32_NF5 = 640.2e6 / (4096 * 4096)
+
+# FP32 arithmetic operations the stage performs per cell (one per rounded operation of the method, a
+# fused multiply-add counted once), from the kernel's arithmetic with its sharing in place: a WENO5
+# reconstruction 23, a point's split flux and smoothness data 22.9, per 15-cell line 1271 ops for a
+# hydro component (84.7 per cell, 8 lines per cell) and 928 for the level set (61.9 per cell, 2 lines);
+# primitives 12.3 per cell (halo included); the cell phase 61 with the level-set Hamiltonian, 40 without.
+def alg_ops_per_cell_stage(F):
+    return 8 * 84.7 + 12.3 + (2 * 61.9 + 61.0 if F == 5 else 40.0)
+
+
+def roofline(F, B, cells, avg_launch_ms, sm_mhz=None, alu=False, traffic=None):
+    """Roofline of the stage kernel. HBM: algorithmic bytes per launch = 8 F B per cell per step (stage 1
+    reads U^n and writes U^(1); stages 2 and 3 read U^n and the stage input and write) over 3 launches.
+    ALU (FP32): algorithmic operations per launch against 152 SMs x 128 FP32 lanes x SM clock."""
     alg_bytes_per_launch = 8 * F * B * cells / 3.0
     achieved = alg_bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind, "kernel": "stage_kernel", "avg_launch_ms": avg_launch_ms,
-            "alg_bytes_per_launch": alg_bytes_per_launch}
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "kernel": "stage_kernel", "avg_launch_ms": avg_launch_ms,
+           "alg_bytes_per_launch": alg_bytes_per_launch}
+    if not alu:
+        return hbm, None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    ops = alg_ops_per_cell_stage(F) * cells
+    a = ops / (avg_launch_ms * 1e-3) / 1e12
+    pk = sms * 128 * mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": a, "peak": pk, "unit": "T FP32 ops/s (FMA = 1)", "frac": a / pk,
+            "traffic": traffic, "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
+            "kernel": "stage_kernel", "avg_launch_ms": avg_launch_ms, "alg_ops_per_launch": ops}
+    return roof, hbm
 
 
 def _line(args, world, value, ms_total, dtype, config, extra):
@@ -219,7 +247,7 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
     ms = e0.elapsed_time(e1)
     launches = sum(h.launch_count() for h in hs) - l0
     F, B = members[0].nfields, (8 if dtype == "f64" else 4)
-    roof = roofline(F, B, cells, ms / (3 * args.steps))
+    roof, roof_hbm = roofline(F, B, cells, ms / (3 * args.steps), (clk or {}).get("sm_mhz"), alu=(dtype == "f32"))
     roof["note"] = "launch time from the whole timed region / (3 x steps): includes packing and graph launch"
     for h in hs:
         h.close()
@@ -228,7 +256,8 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
         cfg = {"workload": args.workload, "members": len(members), "cells": cells, "sizes": len(sizes),
                "seed": members[0].seed, "graph": "3 persistent launches per step, replayed from a CUDA graph"}
         print(json.dumps(_line(args, world, world * cells * args.steps / (ms * 1e-3), ms, dtype, cfg,
-                               {"roofline": roof, "gpu_launches": launches, "clocks": clk})), flush=True)
+                               {"roofline": roof, "roofline_hbm": roof_hbm, "gpu_launches": launches,
+                                "clocks": clk})), flush=True)
     return 0
 
 
@@ -319,14 +348,21 @@ def run(args):
     cells = prob.nx * prob.ny
     value = world * cells * args.steps / (ms * 1e-3)
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
-    roof = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1))
+    traffic = None
+    if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast"):
+        # measured stage-1 traffic per cell times cells, as the per-launch figure (stage 1 moves 2FB of the
+        # average launch's 8FB/3 algorithmic bytes; stages 2 and 3 were not captured)
+        traffic = TRAFFIC_BYTES_PER_CELL_STAGE1_F32_NF5 * cells
+    roof, roof_hbm = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1), (clk or {}).get("sm_mhz"),
+                              alu=(dtype == "f32"), traffic=traffic)
     # end to end through the public host-buffer entry: every step copies the state in and out
     if args.quick:
         h.close()
         if rank == 0:
             cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F, "cells": cells, "tile": info,
                    "autotune_ms_per_step": tune}
-            print(json.dumps(_line(args, world, value, ms, dtype, cfg, {"roofline": roof, "gpu_launches": gpu_launches,
+            print(json.dumps(_line(args, world, value, ms, dtype, cfg, {"roofline": roof, "roofline_hbm": roof_hbm,
+                                                                       "gpu_launches": gpu_launches,
                                                                        "clocks": clk})), flush=True)
         return 0
     Uh = U.cpu().numpy().copy()
@@ -362,6 +398,18 @@ def run(args):
         adj_ms = a0.elapsed_time(a1) / ka
         adjoint = {"ms_per_step": adj_ms, "dtype": dtype, "steps": ka,
                    "adjoint_over_forward": adj_ms / (ms / args.steps)}
+    # level-set reinitialisation of the state's phi, timed once after a warm-up call
+    reinit = None
+    if args.workload == "blobs_blast_8192":
+        h.reinit(U)
+        torch.cuda.synchronize()
+        r0_, r1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0_.record()
+        npts = h.reinit(U)
+        r1_.record()
+        torch.cuda.synchronize()
+        reinit = {"ms": r0_.elapsed_time(r1_), "front_points": npts,
+                  "pair_distances_per_s": npts * cells / (r0_.elapsed_time(r1_) * 1e-3)}
     h.close()
     fp64 = None
     if not args.no_fp64 and dtype == "f32" and args.workload == "blobs_blast_8192":
@@ -392,8 +440,8 @@ def run(args):
                                   " in-L2 rate (not an HBM-bound measurement)"),
                            "tile": info, "autotune_ms_per_step": tune,
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roof, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
-                "adjoint": adjoint, "fp64_step": fp64}
+                "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
+                "adjoint": adjoint, "fp64_step": fp64, "reinit": reinit}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)

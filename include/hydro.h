@@ -120,6 +120,16 @@ int hydro_last_totals(hydro_ctx* ctx, double out[5]);
 int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dtype, int geometry, double x0,
                              double x1, double y0, double y1, void* stream, double out[5]);
 
+/* Level-set reinitialisation of phi (field 4 of a device state with nfields = 5), in place (Sec. 2.2):
+ * the front points are the linear-interpolation zeros of phi along every pair of neighbouring cells (in
+ * x and in y, inside the grid) whose values lie on opposite sides of zero (> 0 ash, <= 0 fuel); every
+ * cell's distance d to the front is its smallest distance to those points (Euclidean, no periodic
+ * images); phi_new = H(d) phi_old + (1 - H(d)) sign(phi_old) d with H(d) = [1 - tanh((d - d0)/(Delta/3))]
+ * / [1 - tanh(-d0/(Delta/3))], d0 = 3 Delta, Delta = min(dx, dy). phi is unchanged when there is no
+ * front. Cost O(cells x front points). *npoints (may be NULL) receives the number of front points.
+ * Allocates its point buffer (2 points per cell) on first use. Synchronises the stream. */
+int hydro_reinit(hydro_ctx* ctx, void* U, int* npoints);
+
 /* ---- recording and the discrete adjoint (frozen alpha and dt) ---------------------------------
  * alpha_x, alpha_y and dt are maxima/minima over the grid and have no derivative; the adjoint and the
  * finite-difference checks freeze them at the values the forward run used. */

@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libhydro_oracle.so")
-_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc"]
+_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc", "hydro_oracle_reinit.inc"]
 _lock = threading.Lock()
 _lib = None
 
@@ -82,6 +82,9 @@ def _load():
         lib.orc_totals.argtypes = [cp, dp, dp]
         lib.orc_adjoint_step.argtypes = [cp, dp, dp, ctypes.c_double, dp]
         lib.orc_rhs_adjoint.argtypes = [cp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_reinit.argtypes = [cp, dp, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_reinit_blend.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.orc_reinit_blend.restype = ctypes.c_double
         _lib = lib
         return lib
 
@@ -204,6 +207,18 @@ def totals(p, U) -> np.ndarray:
     out = np.zeros(5)
     _check(_load().orc_totals(ctypes.byref(_cfg(p)), _ptr(U), _ptr(out)), "totals")
     return out
+
+
+def reinit(p, U):
+    """Level-set reinitialisation (Sec. 2.2) of phi; returns (U, number of front points)."""
+    U = _state(p, U).copy()
+    npts = ctypes.c_int(0)
+    _check(_load().orc_reinit(ctypes.byref(_cfg(p)), _ptr(U), ctypes.byref(npts)), "reinit")
+    return U, npts.value
+
+
+def reinit_blend(d: float, delta: float) -> float:
+    return float(_load().orc_reinit_blend(float(d), float(delta)))
 
 
 def rhs_adjoint(p, U, ax: float, ay: float, mu) -> np.ndarray:

@@ -68,6 +68,11 @@ int orc_totals(const orc_config* c, const double* U, double out[5]);
  * alpha holds (alpha_x, alpha_y) for the three stages. */
 int orc_adjoint_step(const orc_config* c, const double* Un, double* lambda, double dt,
                      const double alpha[6]);
+/* Level-set reinitialisation of phi (field 4) in place (Sec. 2.2); *npoints receives the number of
+ * front points. orc_reinit_blend is the blending weight H(d) for grid size delta. */
+int orc_reinit(const orc_config* c, double* U, int* npoints);
+double orc_reinit_blend(double d, double delta);
+
 /* Adjoint of the spatial operator: out = (dL/dU)^T mu (alpha frozen). */
 int orc_rhs_adjoint(const orc_config* c, const double* U, double ax, double ay, const double* mu,
                     double* out);

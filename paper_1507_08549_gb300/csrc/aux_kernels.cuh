@@ -7,17 +7,18 @@
 
 namespace hydro {
 
+// Grid-stride over the cells (a few blocks per SM); one block-level reduction and one atomic per slot
+// and block at the end, so the global maxima see a few thousand atomics, not one per warp.
 template <typename real, int NF>
 __global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, GridParams<real> g,
                                                    real* alpha_slot, real* smax_slot, double* t_acc, double t0) {
-  using T = RT<real>;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && t_acc) *t_acc = t0;
+  __shared__ real sred[8][3];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && t_acc) *t_acc = t0;
   real amx = real(0), amy = real(0), smx = real(0);
-  if (i < g.nx) {
-    const long long n = static_cast<long long>(g.nx) * g.ny;
-    const long long k = static_cast<long long>(j) * g.nx + i;
+  const long long n = static_cast<long long>(g.nx) * g.ny;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const int j = static_cast<int>(k / g.nx), i = static_cast<int>(k - static_cast<long long>(j) * g.nx);
     real val[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) val[f] = U[f * n + k];
@@ -26,12 +27,15 @@ __global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, G
     for (int f = 0; f < NF; ++f) g.out[f * g.fstride + off] = val[f];
     if (i < 3 || i >= g.nx - 3 || j < 3 || j >= g.ny - 3)
       write_ghost_images<real, NF>(g.out, g.fstride, g.pitch, g.nx, g.ny, g.bc, i, j, val);
-    const real rho = val[0], mx = val[1], my = val[2], E = val[3];
-    real p;
-    Ar<real>::speeds(rho, mx, my, E, g.gamma, g.gm1, p, amx, amy, smx);
-    bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) && T::finite(smx);
-    if (NF == 5) ok = ok && T::finite(val[NF - 1]);
+    real p, sx, sy, sm;
+    Ar<real>::speeds(val[0], val[1], val[2], val[3], g.gamma, g.gm1, p, sx, sy, sm);
+    bool ok = val[0] > real(0) && p > real(0) && RT<real>::finite(val[3]) && RT<real>::finite(val[1]) &&
+              RT<real>::finite(val[2]) && RT<real>::finite(sm);
+    if (NF == 5) ok = ok && RT<real>::finite(val[NF - 1]);
     if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
+    amx = fmax(amx, sx);
+    amy = fmax(amy, sy);
+    smx = fmax(smx, sm);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -39,12 +43,19 @@ __global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, G
     amy = fmax(amy, __shfl_xor_sync(0xffffffffu, amy, o));
     smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
   }
+  const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    if (alpha_slot) {
-      T::atomic_max(&alpha_slot[0], amx);
-      T::atomic_max(&alpha_slot[1], amy);
-    }
-    if (smax_slot) T::atomic_max(smax_slot, smx);
+    sred[warp][0] = amx;
+    sred[warp][1] = amy;
+    sred[warp][2] = smx;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    real m = real(0);
+    for (int w = 0; w < 8; ++w) m = fmax(m, sred[w][threadIdx.x]);
+    if (threadIdx.x == 0 && alpha_slot) RT<real>::atomic_max(&alpha_slot[0], m);
+    if (threadIdx.x == 1 && alpha_slot) RT<real>::atomic_max(&alpha_slot[1], m);
+    if (threadIdx.x == 2 && smax_slot) RT<real>::atomic_max(smax_slot, m);
   }
 }
 

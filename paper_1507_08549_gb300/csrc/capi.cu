@@ -82,6 +82,10 @@ struct hydro_ctx {
   void* seg = nullptr;
   size_t seg_cap = 0;
   int ck_nsteps = -1, ck_every = 0;
+  // level-set reinitialisation: front points (x, y pairs) and their count
+  void* front = nullptr;
+  int* front_count = nullptr;
+  int front_cap = 0;
   // batch plan (kept on the first member)
   std::vector<hydro_ctx*> plan_members;
   int plan_variant = -1;
@@ -466,6 +470,8 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->adj_acc);
   cudaFree(c->ckpt);
   cudaFree(c->seg);
+  cudaFree(c->front);
+  cudaFree(c->front_count);
   if (c->host_scratch) cudaFreeHost(c->host_scratch);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->done) cudaEventDestroy(c->done);
@@ -1027,4 +1033,41 @@ int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
   if (c->ck_nsteps < 1 || !c->ckpt) return fail(c, HYDRO_ESTATE, "no checkpointed forward run to reverse");
   if (c->cfg.dtype == HYDRO_F64) return sweep_impl<double>(c, (double*)lambda);
   return sweep_impl<float>(c, (float*)lambda);
+}
+
+// ---- level-set reinitialisation (Sec. 2.2)
+
+template <typename real>
+static int reinit_impl(hydro_ctx* c, real* U) {
+  const hydro_config& g = c->cfg;
+  const long long n = (long long)g.nx * g.ny;
+  if (!c->front) {
+    // every cell pair can hold one front point: at most 2 n points
+    const long long cap = 2 * n;
+    if (cap > 0x7fffffffLL) return fail(c, HYDRO_EINVAL, "grid too large for the front point buffer");
+    CK(cudaMalloc(&c->front, sizeof(real) * 2 * cap));
+    CK(cudaMalloc(&c->front_count, sizeof(int)));
+    c->front_cap = (int)cap;
+  }
+  Scratch<real>* s = scr<real>(c);
+  CK(cudaMemsetAsync(&s->err, 0, sizeof(int), c->stream));
+  const double dx = (g.x1 - g.x0) / g.nx, dy = (g.y1 - g.y0) / g.ny;
+  int nl = 0;
+  CK(launch_reinit<real>(U + 4 * n, g.nx, g.ny, g.nx, g.x0, g.y0, dx, dy, static_cast<real*>(c->front), c->front_cap,
+                         c->front_count, &s->err, c->stream, &nl));
+  c->launches += nl;
+  return read_status<real>(c, nullptr, nullptr);
+}
+
+int hydro_reinit(hydro_ctx* c, void* U, int* npoints) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U) return fail(c, HYDRO_EINVAL, "null state");
+  if (c->nf != 5) return fail(c, HYDRO_EINVAL, "reinitialisation needs the level-set field (nfields = 5)");
+  rc = c->cfg.dtype == HYDRO_F64 ? reinit_impl<double>(c, (double*)U) : reinit_impl<float>(c, (float*)U);
+  if (rc == HYDRO_OK && npoints) {
+    cudaError_t e = cudaMemcpy(npoints, c->front_count, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "front count");
+  }
+  return rc;
 }

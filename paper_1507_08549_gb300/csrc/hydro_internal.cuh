@@ -103,6 +103,12 @@ template <typename real>
 cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geometry, double x0, double dx,
                           double dy, double* partials, int nblocks, double* out, cudaStream_t s);
 
+// Level-set reinitialisation (reinit_kernel.cuh): front points where phi changes sign between
+// neighbouring cells (linear interpolation), minimum distance of every cell to them, tanh blend.
+template <typename real>
+cudaError_t launch_reinit(real* phi, int nx, int ny, int pitch, double x0, double y0, double dx, double dy,
+                          real* front, int capacity, int* count, int* err, cudaStream_t s, int* launches);
+
 // Discrete adjoint of one frozen RK stage (adjoint_kernel.cuh): point terms, line adjoints over the
 // padded grid with its ghost frame, ghost fold and RK blend. Buffers are padded like the states.
 template <typename real>

@@ -2,6 +2,7 @@
 // precision (included by stage_f32.cu / stage_f64.cu with HYDRO_REAL defined).
 #pragma once
 #include "adjoint_kernel.cuh"
+#include "reinit_kernel.cuh"
 #include "aux_kernels.cuh"
 
 namespace hydro {
@@ -92,7 +93,11 @@ template <>
 cudaError_t launch_pack<HYDRO_REAL>(const HYDRO_REAL* U, const GridParams<HYDRO_REAL>& g, int nfields,
                                     HYDRO_REAL* alpha_slot, HYDRO_REAL* smax_slot, double* t_acc, double t0,
                                     cudaStream_t s) {
-  dim3 grid((g.nx + 255) / 256, g.ny);
+  int dev = 0, sms = 132;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long n = static_cast<long long>(g.nx) * g.ny;
+  const long long want = (n + 255) / 256;
+  const int grid = static_cast<int>(want < 8LL * sms ? want : 8LL * sms);
   if (nfields == 5)
     pack_kernel<HYDRO_REAL, 5><<<grid, 256, 0, s>>>(U, g, alpha_slot, smax_slot, t_acc, t0);
   else
@@ -116,6 +121,23 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
   else
     totals_partial_kernel<HYDRO_REAL, 4><<<nblocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, partials);
   totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, nfields, out);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_reinit<HYDRO_REAL>(HYDRO_REAL* phi, int nx, int ny, int pitch, double x0, double y0, double dx,
+                                      double dy, HYDRO_REAL* front, int capacity, int* count, int* err,
+                                      cudaStream_t s, int* launches) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  front_kernel<HYDRO_REAL><<<dim3((nx + 255) / 256, ny), 256, 0, s>>>(phi, nx, ny, pitch, x0, y0, dx, dy, front,
+                                                                       capacity, count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = static_cast<long long>(nx) * ny;
+  distance_kernel<HYDRO_REAL><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      phi, nx, ny, pitch, x0, y0, dx, dy, dx < dy ? dx : dy, front, capacity, count, err);
+  if (launches) *launches += 2;
   return cudaGetLastError();
 }
 

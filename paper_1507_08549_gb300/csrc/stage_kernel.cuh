@@ -111,8 +111,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 //   m: eps + 13/12 s^2 + 1/4 (2s - t)^2  (the triplet as the leftmost stencil of a face),
 //   t: eps + 13/12 s^2 + 1/4 t^2          (as the central stencil),
 //   p: eps + 13/12 s^2 + 1/4 (2s + t)^2  (as the rightmost stencil),
-// with s = (L + R) - 2C and t = L - R. Mirroring the triplet keeps s and negates t, so the same data
-// serve the reconstruction from the right.
+// with s = (L + R) - 2C and t = L - R, evaluated as (s -+ t/2)^2 and (t/2)^2 (t/2 is exact). Mirroring
+// the triplet keeps s and negates t, so the same data serve the reconstruction from the right.
 template <typename real>
 struct B3 {
   real m, t, p;
@@ -122,14 +122,14 @@ template <typename real>
 __device__ __forceinline__ B3<real> betas(real L, real C, real R) {
   using T = RT<real>;
   const real s = T::fma_(real(-2), C, L + R);
-  const real t = L - R;
+  const real th = real(0.5) * (L - R);
   const real bs = T::fma_(real(13.0 / 12.0) * s, s, real(1e-6));
-  const real mm = T::fma_(real(2), s, -t);
-  const real pp = T::fma_(real(2), s, t);
+  const real mm = s - th;
+  const real pp = s + th;
   B3<real> b;
-  b.m = T::fma_(real(0.25) * mm, mm, bs);
-  b.t = T::fma_(real(0.25) * t, t, bs);
-  b.p = T::fma_(real(0.25) * pp, pp, bs);
+  b.m = T::fma_(mm, mm, bs);
+  b.t = T::fma_(th, th, bs);
+  b.p = T::fma_(pp, pp, bs);
   return b;
 }
 

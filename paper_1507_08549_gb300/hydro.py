@@ -45,7 +45,7 @@ EXPORTS = [
     "hydro_rhs", "conserved_totals", "hydro_last_totals", "hydro_record", "hydro_get_log", "hydro_step_frozen",
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
-    "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc",
+    "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
 ]
 
 _lock = threading.Lock()
@@ -99,6 +99,7 @@ def load(build_if_needed: bool = True):
             "hydro_profile": ([ctxp, ctypes.c_int], ctypes.c_int),
             "hydro_stage_timing": ([ctxp, ip, dp], ctypes.c_int),
             "hydro_launch_count": ([ctxp], ctypes.c_longlong),
+            "hydro_reinit": ([ctxp, vp, ip], ctypes.c_int),
             "conserved_totals_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, dp],
                                          ctypes.c_int),
@@ -257,6 +258,12 @@ class Hydro:
 
     def adjoint_sweep(self, lam):
         self._check(self.lib.hydro_adjoint_sweep(self.ctx, self._ptr(lam, "lambda")), "hydro_adjoint_sweep")
+
+    def reinit(self, U) -> int:
+        """Level-set reinitialisation of phi in place (hydro_reinit); returns the front point count."""
+        n = ctypes.c_int(0)
+        self._check(self.lib.hydro_reinit(self.ctx, self._ptr(U), ctypes.byref(n)), "hydro_reinit")
+        return n.value
 
     def tile_variants(self):
         n, cur = ctypes.c_int(), ctypes.c_int()
