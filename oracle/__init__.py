@@ -11,6 +11,7 @@ ctypes. ``riemann_exact`` holds the exact Riemann solver used to pin the oracle.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -20,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libhydro_oracle.so")
-_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc", "hydro_oracle_reinit.inc"]
+_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc", "hydro_oracle_reinit.inc", "hydro_oracle_poisson.inc"]
 _lock = threading.Lock()
 _lib = None
 
@@ -85,6 +86,8 @@ def _load():
         lib.orc_reinit.argtypes = [cp, dp, ctypes.POINTER(ctypes.c_int)]
         lib.orc_reinit_blend.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.orc_reinit_blend.restype = ctypes.c_double
+        lib.orc_poisson.argtypes = [cp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
         _lib = lib
         return lib
 
@@ -215,6 +218,31 @@ def reinit(p, U):
     npts = ctypes.c_int(0)
     _check(_load().orc_reinit(ctypes.byref(_cfg(p)), _ptr(U), ctypes.byref(npts)), "reinit")
     return U, npts.value
+
+
+def mass(p, rho) -> float:
+    """Mass of an (r,z) grid, sum over cells of rho 2 pi r dr dz (Sec. 2.1), each term rounded in that
+    order and the sum correctly rounded (math.fsum)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    if rho.shape != (int(p.ny), int(p.nx)):
+        raise OracleError("rho shape mismatch")
+    dr = (float(p.x1) - float(p.x0)) / int(p.nx)
+    dz = (float(p.y1) - float(p.y0)) / int(p.ny)
+    r = float(p.x0) + (np.arange(int(p.nx), dtype=np.float64) + 0.5) * dr
+    terms = rho * (2.0 * np.pi) * r[None, :] * dr * dz
+    return math.fsum(terms.ravel().tolist())
+
+
+def poisson(p, rho, G=1.0, omega=1.9, tol=1e-8, max_iters=100000, phi0=None):
+    """Self-gravity potential by red-black SOR (Sec. 2.1). Returns (phi, sweeps)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    if rho.shape != (int(p.ny), int(p.nx)):
+        raise OracleError("rho shape mismatch")
+    phi = np.zeros_like(rho) if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64).copy()
+    it = ctypes.c_int(0)
+    _check(_load().orc_poisson(ctypes.byref(_cfg(p)), _ptr(rho), float(G), mass(p, rho), float(omega), float(tol),
+                               int(max_iters), _ptr(phi), ctypes.byref(it)), "poisson")
+    return phi, it.value
 
 
 def reinit_blend(d: float, delta: float) -> float:

@@ -474,3 +474,4 @@ int orc_totals(const orc_config* c, const double* U, double out[5]) {
 
 #include "hydro_oracle_adjoint.inc"
 #include "hydro_oracle_reinit.inc"
+#include "hydro_oracle_poisson.inc"

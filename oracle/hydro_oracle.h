@@ -73,6 +73,12 @@ int orc_adjoint_step(const orc_config* c, const double* Un, double* lambda, doub
 int orc_reinit(const orc_config* c, double* U, int* npoints);
 double orc_reinit_blend(double d, double delta);
 
+/* Self-gravity potential of rho [ny][nx] on an (r,z) grid by red-black SOR (Sec. 2.1); mass is the
+ * grid's mass (sum of rho 2 pi r dr dz); phi holds the initial guess on entry and the result on exit;
+ * *iters receives the sweeps done. */
+int orc_poisson(const orc_config* c, const double* rho, double grav_const, double mass, double omega, double tol,
+                int max_iters, double* phi, int* iters);
+
 /* Adjoint of the spatial operator: out = (dL/dU)^T mu (alpha frozen). */
 int orc_rhs_adjoint(const orc_config* c, const double* U, double ax, double ay, const double* mu,
                     double* out);
