@@ -176,10 +176,11 @@ def run_reference(args):
     return 0
 
 
-# Measured DRAM traffic of one stage launch, from an ncu capture of the 4096^2 blobs + blast case
-# (dram__bytes_read.sum + dram__bytes_write.sum of stage 1: 640.2 MB for 16.78 M cells), scaled to a
-# launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_STAGE1_F32_NF5 = 640.2e6 / (4096 * 4096)
+# Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
+# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 640.0, 994.2 and 973.5 MB
+# for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
+# a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
+TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (640.0e6 + 994.2e6 + 973.5e6) / 3.0 / (4096 * 4096)
 
 # FP32 arithmetic operations the stage performs per cell (one per rounded operation of the method, a
 # fused multiply-add counted once), from the kernel's arithmetic with its sharing in place: a WENO5
@@ -350,9 +351,8 @@ def run(args):
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
     traffic = None
     if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast"):
-        # measured stage-1 traffic per cell times cells, as the per-launch figure (stage 1 moves 2FB of the
-        # average launch's 8FB/3 algorithmic bytes; stages 2 and 3 were not captured)
-        traffic = TRAFFIC_BYTES_PER_CELL_STAGE1_F32_NF5 * cells
+        # measured average traffic of a stage launch per cell, times cells
+        traffic = TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 * cells
     roof, roof_hbm = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1), (clk or {}).get("sm_mhz"),
                               alu=(dtype == "f32"), traffic=traffic)
     # end to end through the public host-buffer entry: every step copies the state in and out
