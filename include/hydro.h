@@ -130,6 +130,37 @@ int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dty
  * Allocates its point buffer (2 points per cell) on first use. Synchronises the stream. */
 int hydro_reinit(hydro_ctx* ctx, void* U, int* npoints);
 
+/* Self-gravity potential Phi of the density rho = U[0] on an (r,z) grid (geometry 1), Sec. 2.1:
+ * (1/r) d/dr (r dPhi/dr) + d2Phi/dz2 = 4 pi G rho, solved by successive over-relaxation of red-black
+ * Gauss-Seidel sweeps (red: i + j even, then black) with
+ *   Phi_GS = (aE Phi_E + aW Phi_W + aN Phi_N + aS Phi_S - 4 pi G rho) / (aE + aW + aN + aS),
+ *   aE = r_{i+1/2} / (r_i dr^2), aW = r_{i-1/2} / (r_i dr^2), aN = aS = 1 / dz^2,
+ *   Phi <- (1 - omega) Phi + omega Phi_GS,
+ * every operation rounded once in that order (FP64 whatever the state's dtype). Inner boundaries
+ * reflect: the x-lo face (the axis, where aW = 0 at r = 0, or a wall) and the y-lo face when its bc is
+ * HYDRO_BC_REFLECT (the missing neighbour is the cell's own value). The other faces hold the Roche value
+ * -G M / sqrt(r^2 + z^2) at the ghost cell centre, M the mass, doubled when y-lo reflects (a z = 0
+ * symmetry plane). The mass of the grid, sum of rho 2 pi r dr dz with each term rounded in that order,
+ * is summed exactly and rounded once (correctly rounded, independent of summation order).
+ * The sweeps stop after the first sweep in which every cell's relative change |new - old| / |new| is
+ * below tol (cells with 0/0 are ignored), or after max_iters sweeps; tol <= 0 runs exactly max_iters.
+ *   U        device state [nfields][ny][nx] (only the rho plane is read)
+ *   phi      device double [ny][nx]: the initial guess on entry, the potential on exit (caller-owned)
+ *   omega    relaxation factor, 0 < omega < 2
+ *   iters    (may be NULL) receives the sweeps done; mass (may be NULL) the grid mass (not doubled)
+ * Errors: HYDRO_EINVAL for a Cartesian grid, null pointers, omega outside (0, 2), max_iters < 0, ny >
+ * 131070; HYDRO_ESIZE beyond 2^31 - 1 cells; HYDRO_ENONPHYSICAL when rho holds inf or NaN (phi is then
+ * NaN). Allocates its work arrays (5 nx + ny doubles and a few KB) on first use. Synchronises the stream. */
+int hydro_poisson(hydro_ctx* ctx, const void* U, double G, double omega, double tol, int max_iters, double* phi,
+                  int* iters, double* mass);
+
+/* Correctly rounded sum of n device doubles x (round to nearest, ties to even, once): the terms are added
+ * exactly into a fixed-point long accumulator, so the result does not depend on the order of summation.
+ * It is the summation the Poisson solve uses for its mass. *out is a host double. Errors: HYDRO_ESIZE
+ * for n > 2^31 - 1; HYDRO_ENONPHYSICAL (and *out = NaN) when a term is inf or NaN. Allocates on first
+ * use like hydro_poisson. Synchronises the stream. */
+int hydro_exact_sum(hydro_ctx* ctx, const double* x, long long n, double* out);
+
 /* ---- recording and the discrete adjoint (frozen alpha and dt) ---------------------------------
  * alpha_x, alpha_y and dt are maxima/minima over the grid and have no derivative; the adjoint and the
  * finite-difference checks freeze them at the values the forward run used. */

@@ -86,6 +86,12 @@ struct hydro_ctx {
   void* front = nullptr;
   int* front_count = nullptr;
   int front_cap = 0;
+  // self-gravity Poisson solve and exact sums: device PoissonDev block + coefficient arrays, pinned
+  // host mirror of the control words, the captured graph of one chunk of sweeps
+  void* pois = nullptr;
+  void* pois_host = nullptr;
+  cudaGraphExec_t sor_graph = nullptr;
+  cudaEvent_t sor_ev[2] = {nullptr, nullptr};
   // batch plan (kept on the first member)
   std::vector<hydro_ctx*> plan_members;
   int plan_variant = -1;
@@ -453,6 +459,11 @@ void hydro_destroy(hydro_ctx* c) {
   if (c->stream || true) cudaStreamSynchronize(c->stream);
   if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
   if (c->plan_graph) cudaGraphExecDestroy(c->plan_graph);
+  if (c->sor_graph) cudaGraphExecDestroy(c->sor_graph);
+  for (cudaEvent_t e : c->sor_ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(c->pois);
+  if (c->pois_host) cudaFreeHost(c->pois_host);
   for (int k = 0; k < 3; ++k) cudaFree(c->buf[k]);
   cudaFree(c->scratch);
   cudaFree(c->params);
@@ -1070,4 +1081,170 @@ int hydro_reinit(hydro_ctx* c, void* U, int* npoints) {
     if (e != cudaSuccess) return cuda_fail(c, e, "front count");
   }
   return rc;
+}
+
+// ---- self-gravity potential (Sec. 2.1) and exact sums
+
+namespace {
+struct PoissonDev {
+  PoissonParams P;
+  SorCtl ctl;
+  ExactAcc acc;
+  double sum_out;
+};
+struct PoissonHost {
+  SorCtl ctl;
+  int nonfinite;
+  double mass, sum_out;
+  int done[2];
+};
+}  // namespace
+
+static int ensure_poisson(hydro_ctx* c) {
+  if (c->pois) return HYDRO_OK;
+  const size_t head = (sizeof(PoissonDev) + 255) / 256 * 256;
+  const size_t arrays = sizeof(double) * (5 * (size_t)c->cfg.nx + (size_t)c->cfg.ny);
+  CK(cudaMalloc(&c->pois, head + arrays));
+  CK(cudaMallocHost(&c->pois_host, sizeof(PoissonHost)));
+  for (cudaEvent_t& e : c->sor_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return HYDRO_OK;
+}
+
+static PoissonDev* pdev(hydro_ctx* c) { return static_cast<PoissonDev*>(c->pois); }
+static PoissonHost* phost(hydro_ctx* c) { return static_cast<PoissonHost*>(c->pois_host); }
+
+static int wait_event(hydro_ctx* c, cudaEvent_t ev) {
+  const double limit = host_timeout_s();
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return HYDRO_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(c, e, "event wait");
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return fail(c, HYDRO_ETIMEOUT, "stream did not finish within HYDRO_TIMEOUT_S");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+  }
+}
+
+template <typename T>
+static int ensure_sor_graph(hydro_ctx* c) {
+  if (c->sor_graph) return HYDRO_OK;
+  cudaGraph_t gr = nullptr;
+  CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+  long long before = c->launches;
+  int nl = 0;
+  cudaError_t e1 = launch_sor_chunk<T>(&pdev(c)->P, &pdev(c)->ctl, c->cfg.nx, c->cfg.ny, c->capture, &nl);
+  cudaError_t e = cudaStreamEndCapture(c->capture, &gr);
+  c->launches = before;  // captured, not launched
+  if (e1 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return cuda_fail(c, e1, "capture of the SOR sweeps");
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->sor_graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return HYDRO_OK;
+}
+
+template <typename T>
+static int poisson_impl(hydro_ctx* c, const T* U, double G, double omega, double tol, int max_iters, double* phi,
+                        int* iters, double* mass) {
+  int rc = ensure_poisson(c);
+  if (rc) return rc;
+  const hydro_config& g = c->cfg;
+  PoissonDev* d = pdev(c);
+  double* arr = reinterpret_cast<double*>(static_cast<char*>(c->pois) + (sizeof(PoissonDev) + 255) / 256 * 256);
+  PoissonParams hp{};
+  hp.phi = phi;
+  hp.rho = U;  // field 0 of the caller's state
+  hp.nx = g.nx;
+  hp.ny = g.ny;
+  hp.zsym = g.bc[2] == HYDRO_BC_REFLECT ? 1 : 0;
+  hp.max_iters = max_iters;
+  hp.x0 = g.x0;
+  hp.y0 = g.y0;
+  hp.dr = (g.x1 - g.x0) / g.nx;
+  hp.dz = (g.y1 - g.y0) / g.ny;
+  hp.G = G;
+  hp.omega = omega;
+  hp.one_minus_omega = 1.0 - omega;
+  hp.tol = tol;
+  hp.cE = arr;
+  hp.cW = arr + g.nx;
+  hp.cD = arr + 2 * g.nx;
+  hp.gN = arr + 3 * g.nx;
+  hp.gS = arr + 4 * g.nx;
+  hp.gE = arr + 5 * g.nx;
+  CK(cudaMemcpyAsync(&d->P, &hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(&d->ctl, 0, sizeof(SorCtl), c->stream));
+  int nl = 0;
+  CK(launch_poisson_setup<T>(&d->P, &d->acc, (long long)g.nx * g.ny, g.nx, g.ny, c->stream, &nl));
+  c->launches += nl;
+  PoissonHost* h = phost(c);
+  if (max_iters > 0) {
+    rc = ensure_sor_graph<T>(c);
+    if (rc) return rc;
+    const int nchunks = (int)(((long long)max_iters + SOR_CHUNK - 1) / SOR_CHUNK);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      CK(cudaGraphLaunch(c->sor_graph, c->stream));
+      c->launches += 2 * SOR_CHUNK + 1;
+      if (tol > 0.0) {
+        // read the done flag one chunk behind, so the GPU always has the next chunk queued
+        CK(cudaMemcpyAsync(&h->done[ch & 1], &d->ctl.done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaEventRecord(c->sor_ev[ch & 1], c->stream));
+        if (ch >= 1) {
+          rc = wait_event(c, c->sor_ev[(ch - 1) & 1]);
+          if (rc) return rc;
+          if (h->done[(ch - 1) & 1]) break;
+        }
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(&h->ctl, &d->ctl, sizeof(SorCtl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&h->nonfinite, &d->acc.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&h->mass, &d->P.mass, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  rc = wait_stream(c);
+  if (rc) return rc;
+  if (iters) *iters = h->ctl.done ? h->ctl.iters : max_iters;
+  if (mass) *mass = h->mass;
+  if (h->nonfinite) return fail(c, HYDRO_ENONPHYSICAL, "non-finite density in the mass sum");
+  return HYDRO_OK;
+}
+
+int hydro_poisson(hydro_ctx* c, const void* U, double G, double omega, double tol, int max_iters, double* phi,
+                  int* iters, double* mass) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !phi) return fail(c, HYDRO_EINVAL, "null state or potential");
+  if (c->cfg.geometry != 1) return fail(c, HYDRO_EINVAL, "the Poisson solve is defined on an (r,z) grid (geometry 1)");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(c, HYDRO_EINVAL, "omega must lie in (0, 2)");
+  if (max_iters < 0 || !std::isfinite(G) || std::isnan(tol)) return fail(c, HYDRO_EINVAL, "bad G, tol or max_iters");
+  if ((c->cfg.nx + 1) / 2 > 0x7fffffff / 2 || (c->cfg.ny + SOR_BY - 1) / SOR_BY > 65535)
+    return fail(c, HYDRO_EINVAL, "grid too tall for the SOR launch (ny <= 131070)");
+  if ((long long)c->cfg.nx * c->cfg.ny > XS_MAX_TERMS) return fail(c, HYDRO_ESIZE, "more than 2^31 - 1 cells");
+  if (c->cfg.dtype == HYDRO_F64)
+    return poisson_impl<double>(c, static_cast<const double*>(U), G, omega, tol, max_iters, phi, iters, mass);
+  return poisson_impl<float>(c, static_cast<const float*>(U), G, omega, tol, max_iters, phi, iters, mass);
+}
+
+int hydro_exact_sum(hydro_ctx* c, const double* x, long long n, double* out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out || (n > 0 && !x) || n < 0) return fail(c, HYDRO_EINVAL, "null pointer or negative count");
+  if (n > XS_MAX_TERMS) return fail(c, HYDRO_ESIZE, "more than 2^31 - 1 terms");
+  rc = ensure_poisson(c);
+  if (rc) return rc;
+  PoissonDev* d = pdev(c);
+  PoissonHost* h = phost(c);
+  int nl = 0;
+  CK(launch_exact_sum(x, n, &d->acc, &d->sum_out, c->stream, &nl));
+  c->launches += nl;
+  CK(cudaMemcpyAsync(&h->sum_out, &d->sum_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&h->nonfinite, &d->acc.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  rc = wait_stream(c);
+  if (rc) return rc;
+  *out = h->sum_out;
+  if (h->nonfinite) return fail(c, HYDRO_ENONPHYSICAL, "a term is inf or NaN");
+  return HYDRO_OK;
 }

@@ -131,4 +131,51 @@ __host__ __device__ inline int ghost_src(int bc, bool hi, int k, int n, bool* fl
 
 #endif
 
+// ---- exact (correctly rounded) summation and the self-gravity Poisson solve (Sec. 2.1)
+
+// limb k holds digits of weight 2^(32 k - XS_BIAS); a finite double's bits lie in [2^-1074, 2^1024),
+// i.e. bit positions 14 .. 2111 above 2^-1088, limbs 0 .. 65; two more limbs absorb carries.
+constexpr int XS_LIMBS = 68;
+constexpr int XS_BIAS = 1088;
+// every add puts less than 2^32 into a limb: at most 2^31 - 1 terms keep each 64-bit limb from overflowing
+constexpr long long XS_MAX_TERMS = 0x7fffffffLL;
+
+struct ExactAcc {
+  unsigned long long limb[XS_LIMBS];  // two's complement digit sums
+  int nonfinite;                      // a term was inf or NaN
+};
+
+struct PoissonParams {
+  double* phi;        // [ny][nx], in/out
+  const void* rho;    // density plane of the caller's state, [ny][nx] of the state dtype
+  int nx, ny, zsym, max_iters;
+  double x0, y0, dr, dz, G;
+  double omega, one_minus_omega, tol;
+  double four_pi_G, aN;  // set by poisson_setup_kernel
+  double mass;           // grid mass (not doubled), set by poisson_setup_kernel
+  double* cE;            // [nx] aE
+  double* cW;            // [nx] aW
+  double* cD;            // [nx] aE + aW + aN + aS
+  double* gE;            // [ny] Roche value of the ghost east of column nx - 1
+  double* gN;            // [nx] Roche value of the ghost north of row ny - 1
+  double* gS;            // [nx] Roche value of the ghost south of row 0 (unused with zsym)
+};
+
+struct SorCtl {
+  int base;     // sweeps of the chunks already launched
+  int done;     // convergence seen
+  int iters;    // sweeps done when `done` was set
+  int flag[3];  // flag[s % 3]: some cell of sweep s changed by tol or more
+};
+
+constexpr int SOR_CHUNK = 64;  // sweeps per captured graph
+constexpr int SOR_BX = 128, SOR_BY = 2;
+
+cudaError_t launch_exact_sum(const double* x, long long n, ExactAcc* acc, double* out, cudaStream_t s, int* launches);
+template <typename T>
+cudaError_t launch_poisson_setup(PoissonParams* P_dev, ExactAcc* acc, long long n, int nx, int ny, cudaStream_t s,
+                                 int* launches);
+template <typename T>
+cudaError_t launch_sor_chunk(const PoissonParams* P_dev, SorCtl* ctl, int nx, int ny, cudaStream_t s, int* launches);
+
 }  // namespace hydro

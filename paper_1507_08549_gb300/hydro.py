@@ -46,6 +46,7 @@ EXPORTS = [
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
+    "hydro_poisson", "hydro_exact_sum",
 ]
 
 _lock = threading.Lock()
@@ -100,6 +101,9 @@ def load(build_if_needed: bool = True):
             "hydro_stage_timing": ([ctxp, ip, dp], ctypes.c_int),
             "hydro_launch_count": ([ctxp], ctypes.c_longlong),
             "hydro_reinit": ([ctxp, vp, ip], ctypes.c_int),
+            "hydro_poisson": ([ctxp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, ip, dp],
+                              ctypes.c_int),
+            "hydro_exact_sum": ([ctxp, vp, ctypes.c_longlong, dp], ctypes.c_int),
             "conserved_totals_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, dp],
                                          ctypes.c_int),
@@ -264,6 +268,32 @@ class Hydro:
         n = ctypes.c_int(0)
         self._check(self.lib.hydro_reinit(self.ctx, self._ptr(U), ctypes.byref(n)), "hydro_reinit")
         return n.value
+
+    def poisson(self, U, G: float = 1.0, omega: float = 1.9, tol: float = 1e-8, max_iters: int = 100000, phi=None):
+        """Self-gravity potential of rho = U[0] (hydro_poisson). ``phi`` (a CUDA float64 [ny, nx] tensor,
+        updated in place) is the initial guess, zeros when None. Returns (phi, sweeps, grid mass)."""
+        torch = _torch()
+        shape = self.shape[1:]
+        if phi is None:
+            phi = torch.zeros(shape, dtype=torch.float64, device=self.device)
+        if not isinstance(phi, torch.Tensor) or not phi.is_cuda or phi.dtype != torch.float64 \
+                or tuple(phi.shape) != shape or not phi.is_contiguous():
+            raise HydroError(EINVAL, f"phi must be a contiguous CUDA float64 tensor of shape {shape}")
+        it, m = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.lib.hydro_poisson(self.ctx, self._ptr(U), float(G), float(omega), float(tol), int(max_iters),
+                                           ctypes.c_void_p(phi.data_ptr()), ctypes.byref(it), ctypes.byref(m)),
+                    "hydro_poisson")
+        return phi, it.value, m.value
+
+    def exact_sum(self, x) -> float:
+        """Correctly rounded sum of a CUDA float64 tensor (hydro_exact_sum)."""
+        torch = _torch()
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise HydroError(EINVAL, "x must be a contiguous CUDA float64 tensor")
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.hydro_exact_sum(self.ctx, ctypes.c_void_p(x.data_ptr()), int(x.numel()),
+                                             ctypes.byref(out)), "hydro_exact_sum")
+        return out.value
 
     def tile_variants(self):
         n, cur = ctypes.c_int(), ctypes.c_int()
