@@ -1103,7 +1103,8 @@ struct PoissonHost {
 static int ensure_poisson(hydro_ctx* c) {
   if (c->pois) return HYDRO_OK;
   const size_t head = (sizeof(PoissonDev) + 255) / 256 * 256;
-  const size_t arrays = sizeof(double) * (5 * (size_t)c->cfg.nx + (size_t)c->cfg.ny);
+  const size_t arrays =
+      sizeof(double) * (6 * (size_t)c->cfg.nx + (size_t)c->cfg.ny + (size_t)c->cfg.nx * (size_t)c->cfg.ny);
   CK(cudaMalloc(&c->pois, head + arrays));
   CK(cudaMallocHost(&c->pois_host, sizeof(PoissonHost)));
   for (cudaEvent_t& e : c->sor_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1126,14 +1127,13 @@ static int wait_event(hydro_ctx* c, cudaEvent_t ev) {
   }
 }
 
-template <typename T>
 static int ensure_sor_graph(hydro_ctx* c) {
   if (c->sor_graph) return HYDRO_OK;
   cudaGraph_t gr = nullptr;
   CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
   long long before = c->launches;
   int nl = 0;
-  cudaError_t e1 = launch_sor_chunk<T>(&pdev(c)->P, &pdev(c)->ctl, c->cfg.nx, c->cfg.ny, c->capture, &nl);
+  cudaError_t e1 = launch_sor_chunk(&pdev(c)->P, &pdev(c)->ctl, c->cfg.nx, c->cfg.ny, c->capture, &nl);
   cudaError_t e = cudaStreamEndCapture(c->capture, &gr);
   c->launches = before;  // captured, not launched
   if (e1 != cudaSuccess) {
@@ -1170,12 +1170,22 @@ static int poisson_impl(hydro_ctx* c, const T* U, double G, double omega, double
   hp.omega = omega;
   hp.one_minus_omega = 1.0 - omega;
   hp.tol = tol;
+  {
+    int e2 = 0;
+    const double m = std::frexp(tol, &e2);  // tol = m 2^e2, m in [1/2, 1)
+    hp.tol_screen = std::isnormal(tol) && tol > 0.0 ? 1 : 0;
+    hp.tol_exp = e2 - 1;
+    hp.tol_mant = (float)(2.0 * m);
+  }
+  hp.four_pi_G = (4.0 * 3.14159265358979323846264338328) * G;
   hp.cE = arr;
   hp.cW = arr + g.nx;
   hp.cD = arr + 2 * g.nx;
   hp.gN = arr + 3 * g.nx;
   hp.gS = arr + 4 * g.nx;
   hp.gE = arr + 5 * g.nx;
+  hp.cY = arr + 5 * g.nx + g.ny;
+  hp.src = arr + 6 * g.nx + g.ny;
   CK(cudaMemcpyAsync(&d->P, &hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(&d->ctl, 0, sizeof(SorCtl), c->stream));
   int nl = 0;
@@ -1183,7 +1193,7 @@ static int poisson_impl(hydro_ctx* c, const T* U, double G, double omega, double
   c->launches += nl;
   PoissonHost* h = phost(c);
   if (max_iters > 0) {
-    rc = ensure_sor_graph<T>(c);
+    rc = ensure_sor_graph(c);
     if (rc) return rc;
     const int nchunks = (int)(((long long)max_iters + SOR_CHUNK - 1) / SOR_CHUNK);
     for (int ch = 0; ch < nchunks; ++ch) {

@@ -151,11 +151,16 @@ struct PoissonParams {
   int nx, ny, zsym, max_iters;
   double x0, y0, dr, dz, G;
   double omega, one_minus_omega, tol;
-  double four_pi_G, aN;  // set by poisson_setup_kernel
+  int tol_screen, tol_exp;  // tol normal and finite: its unbiased exponent Et (tol in [2^Et, 2^(Et+1)))
+  float tol_mant;           // tol / 2^Et in [1, 2), rounded to FP32
+  double four_pi_G;      // RN(RN(4 pi) G)
+  double aN;             // set by poisson_setup_kernel
   double mass;           // grid mass (not doubled), set by poisson_setup_kernel
   double* cE;            // [nx] aE
   double* cW;            // [nx] aW
-  double* cD;            // [nx] aE + aW + aN + aS
+  double* cD;            // [nx] D = aE + aW + aN + aS
+  double* cY;            // [nx] RN(1 / D)
+  double* src;           // [ny][nx] RN(4 pi G rho), set by poisson_mass_kernel
   double* gE;            // [ny] Roche value of the ghost east of column nx - 1
   double* gN;            // [nx] Roche value of the ghost north of row ny - 1
   double* gS;            // [nx] Roche value of the ghost south of row 0 (unused with zsym)
@@ -175,7 +180,6 @@ cudaError_t launch_exact_sum(const double* x, long long n, ExactAcc* acc, double
 template <typename T>
 cudaError_t launch_poisson_setup(PoissonParams* P_dev, ExactAcc* acc, long long n, int nx, int ny, cudaStream_t s,
                                  int* launches);
-template <typename T>
 cudaError_t launch_sor_chunk(const PoissonParams* P_dev, SorCtl* ctl, int nx, int ny, cudaStream_t s, int* launches);
 
 }  // namespace hydro

@@ -52,13 +52,12 @@ cudaError_t launch_poisson_setup(PoissonParams* P_dev, ExactAcc* acc, long long 
   return cudaGetLastError();
 }
 
-template <typename T>
 cudaError_t launch_sor_chunk(const PoissonParams* P_dev, SorCtl* ctl, int nx, int ny, cudaStream_t s, int* launches) {
   const int hx = (nx + 1) / 2;
   const dim3 grid((hx + SOR_BX - 1) / SOR_BX, (ny + SOR_BY - 1) / SOR_BY), block(SOR_BX, SOR_BY);
   for (int r = 0; r < SOR_CHUNK; ++r)
     for (int color = 0; color < 2; ++color) {
-      sor_color_kernel<T><<<grid, block, 0, s>>>(P_dev, ctl, color, r);
+      sor_color_kernel<<<grid, block, 0, s>>>(P_dev, ctl, color, r);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -69,7 +68,5 @@ cudaError_t launch_sor_chunk(const PoissonParams* P_dev, SorCtl* ctl, int nx, in
 
 template cudaError_t launch_poisson_setup<float>(PoissonParams*, ExactAcc*, long long, int, int, cudaStream_t, int*);
 template cudaError_t launch_poisson_setup<double>(PoissonParams*, ExactAcc*, long long, int, int, cudaStream_t, int*);
-template cudaError_t launch_sor_chunk<float>(const PoissonParams*, SorCtl*, int, int, cudaStream_t, int*);
-template cudaError_t launch_sor_chunk<double>(const PoissonParams*, SorCtl*, int, int, cudaStream_t, int*);
 
 }  // namespace hydro

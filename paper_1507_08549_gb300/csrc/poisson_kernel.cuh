@@ -12,9 +12,15 @@
 // the Roche value -G M / sqrt(r^2 + z^2), M the mass (doubled for a z = 0 symmetry plane).
 //
 // Every operation is rounded once in the order written above (explicit _rn intrinsics, no contraction),
-// so a sweep is bitwise reproducible against any IEEE FP64 evaluation in that order. The stopping test
-// (every cell's relative change |Phi_new - Phi_old| / |Phi_new| below tol after a sweep) is evaluated
-// per cell with the same rounding: a screen by multiplication decides the clear cases, the rest divide.
+// so a sweep is bitwise reproducible against any IEEE FP64 evaluation in that order. The GPU's FP64 pipe
+// (2 operations per SM per clock) bounds the sweep, so the kernel spends as few FP64 operations as
+// that allows: 4 pi G rho is formed once per solve (one rounding, as in the definition); the division
+// by the diagonal D is Markstein's correctly rounded quotient from the column's reciprocal y = RN(1/D)
+// (q0 = RN(a y), r0 = RN(a - D q0), q1 = RN(q0 + r0 y) faithful, r1 = a - D q1 exact, q = RN(q1 + r1 y)
+// = RN(a / D); P. Markstein, IBM J. Res. Dev. 34 (1990)), five fused operations in place of a full
+// division; and the stopping test (every cell's relative change |Phi_new - Phi_old| / |Phi_new| below
+// tol) compares exponents with integer operations, dividing only where the ratio is within a factor of
+// four of tol, which takes the same decision as the rounded quotient.
 //
 // Convergence runs on the device: a sweep's kernels set flag[s % 3] when any cell did not converge; the
 // red kernel of sweep s + 1 reads flag[s % 3] and, when it is clear, marks the solve done and every later
@@ -155,8 +161,10 @@ __global__ void __launch_bounds__(256) poisson_mass_kernel(const PoissonParams* 
        k += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(k % P.nx);
     const double r = cell_r(P, i + 0.5);
-    const double term = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(static_cast<double>(rho[k]), two_pi), r), P.dr), P.dz);
+    const double rk = static_cast<double>(rho[k]);
+    const double term = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(rk, two_pi), r), P.dr), P.dz);
     xs_add(s, &acc->nonfinite, term);
+    P.src[k] = __dmul_rn(P.four_pi_G, rk);
   }
   xs_block_end(s, acc);
 }
@@ -169,7 +177,6 @@ __global__ void __launch_bounds__(256) poisson_setup_kernel(PoissonParams* Pp, c
     Ms = m;
     if (blockIdx.x == 0) {
       Pp->mass = m;
-      Pp->four_pi_G = __dmul_rn(4.0 * 3.14159265358979323846264338328, Pp->G);
       Pp->aN = __ddiv_rn(1.0, __dmul_rn(Pp->dz, Pp->dz));
     }
   }
@@ -183,7 +190,9 @@ __global__ void __launch_bounds__(256) poisson_setup_kernel(PoissonParams* Pp, c
     const double aE = __ddiv_rn(rp, den), aW = __ddiv_rn(rm, den);
     P.cE[i] = aE;
     P.cW[i] = aW;
-    P.cD[i] = __dadd_rn(__dadd_rn(__dadd_rn(aE, aW), aN), aN);
+    const double D = __dadd_rn(__dadd_rn(__dadd_rn(aE, aW), aN), aN);
+    P.cD[i] = D;
+    P.cY[i] = __drcp_rn(D);
     const double ztop = __dadd_rn(P.y0, __dmul_rn(P.ny - 1 + 0.5, P.dz));
     const double zbot = __dadd_rn(P.y0, __dmul_rn(0.5, P.dz));
     P.gN[i] = roche(P.G, M, r, __dadd_rn(ztop, P.dz));
@@ -195,7 +204,6 @@ __global__ void __launch_bounds__(256) poisson_setup_kernel(PoissonParams* Pp, c
 }
 
 // One colour of one sweep. s_rel is the sweep's index within the chunk; the sweep is base + s_rel.
-template <typename T>
 __global__ void __launch_bounds__(SOR_BX* SOR_BY) sor_color_kernel(const PoissonParams* __restrict__ Pp,
                                                                    SorCtl* ctl, int color, int s_rel) {
   const int s = ctl->base + s_rel;
@@ -218,7 +226,6 @@ __global__ void __launch_bounds__(SOR_BX* SOR_BY) sor_color_kernel(const Poisson
   bool unconv = false;
   if (j < ny && i < nx) {
     double* __restrict__ phi = Pp->phi;
-    const T* __restrict__ rho = static_cast<const T*>(Pp->rho);
     const long long g = static_cast<long long>(j) * nx + i;
     const double aN = Pp->aN;
     const double old = phi[g];
@@ -226,19 +233,45 @@ __global__ void __launch_bounds__(SOR_BX* SOR_BY) sor_color_kernel(const Poisson
     const double pW = i > 0 ? phi[g - 1] : old;  // aW = 0 on the axis; a reflecting inner face elsewhere
     const double pN = j + 1 < ny ? phi[g + nx] : Pp->gN[i];
     const double pS = j > 0 ? phi[g - nx] : (Pp->zsym ? old : Pp->gS[i]);
-    double acc = __dadd_rn(__dmul_rn(Pp->cE[i], pE), __dmul_rn(Pp->cW[i], pW));
-    acc = __dadd_rn(acc, __dmul_rn(aN, pN));
-    acc = __dadd_rn(acc, __dmul_rn(aN, pS));
-    acc = __dsub_rn(acc, __dmul_rn(Pp->four_pi_G, static_cast<double>(rho[g])));
-    const double gs = __ddiv_rn(acc, Pp->cD[i]);
+    double a = __dadd_rn(__dmul_rn(Pp->cE[i], pE), __dmul_rn(Pp->cW[i], pW));
+    a = __dadd_rn(a, __dmul_rn(aN, pN));
+    a = __dadd_rn(a, __dmul_rn(aN, pS));
+    a = __dsub_rn(a, Pp->src[g]);
+    // Markstein's correctly rounded a / D from y = RN(1/D)
+    const double D = Pp->cD[i], y = Pp->cY[i];
+    const double q0 = __dmul_rn(a, y);
+    const double q1 = __fma_rn(__fma_rn(-q0, D, a), y, q0);
+    const double gs = __fma_rn(__fma_rn(-q1, D, a), y, q1);
     const double nw = __dadd_rn(__dmul_rn(Pp->one_minus_omega, old), __dmul_rn(Pp->omega, gs));
     phi[g] = nw;
     if (tol > 0.0) {
-      // fl(|d| / |nw|) >= tol, NaN excluded: |d| <= tol |nw| / 2 is surely below, |d| >= 2 tol |nw| surely
-      // at or above (the products are within an ulp); the band between divides
-      const double ad = fabs(__dsub_rn(nw, old)), an = fabs(nw);
-      if (!(ad <= __dmul_rn(0.5 * tol, an)))
-        unconv = ad >= __dmul_rn(2.0 * tol, an) || __ddiv_rn(ad, an) >= tol;
+      // decision fl(|d| / |nw|) >= tol (NaN: no). For normal d and nw with biased exponents ed, en and
+      // mantissas Md, Mn in [1, 2), |d| / |nw| = (Md / Mn) 2^(ed - en) and tol = Mt 2^Et: with k = ed - en - Et
+      // the ratio over tol is (Md / (Mn Mt)) 2^k. k <= -2 puts it below 1/2, k >= 2 at or above 2. Otherwise
+      // an estimate from the leading 20 mantissa bits of d and nw (FP32 arithmetic, relative error below
+      // 2^-18) decides unless it lies within 2^-14 of 1; only those cells divide. A ratio that clears 1 by
+      // more than half an ulp rounds to the same side of tol, so every branch takes fl's decision.
+      const double d = __dsub_rn(nw, old);
+      const int hd = __double2hiint(d), hn = __double2hiint(nw);
+      const int ed = (hd >> 20) & 0x7ff, en = (hn >> 20) & 0x7ff;
+      if (d == 0.0) {
+        unconv = false;  // 0 / |nw| = 0 < tol, or 0 / 0
+      } else if (Pp->tol_screen && ed != 0 && ed != 0x7ff && en != 0 && en != 0x7ff) {
+        const int k = ed - en - Pp->tol_exp;
+        if (k >= 2) {
+          unconv = true;
+        } else if (k > -2) {
+          const float fd = __int_as_float(0x3f800000 | ((hd & 0xfffff) << 3));
+          const float fn = __int_as_float(0x3f800000 | ((hn & 0xfffff) << 3));
+          const float est = __fdividef(fd, fn * Pp->tol_mant) * (k == 0 ? 1.0f : (k > 0 ? 2.0f : 0.5f));
+          if (est >= 1.0f + 0x1p-14f)
+            unconv = true;
+          else if (est > 1.0f - 0x1p-14f)
+            unconv = __ddiv_rn(fabs(d), fabs(nw)) >= tol;
+        }
+      } else {
+        unconv = __ddiv_rn(fabs(d), fabs(nw)) >= tol;
+      }
     }
   }
   if (__syncthreads_or(unconv) && threadIdx.x == 0 && threadIdx.y == 0) {

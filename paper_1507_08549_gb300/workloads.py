@@ -214,6 +214,27 @@ def rayleigh_taylor(nr: int = 1024, nz: int = 2048, seed: int = DEFAULT_SEED, ns
                    nsteps=nsteps, seed=seed, U0=conserved(gamma, rho, 0.0, vz, p, phi))
 
 
+def self_gravity_star(nr: int = 1024, nz: int = 2048, radius: float = 0.3, rho_c: float = 1.0,
+                      seed: int = DEFAULT_SEED) -> Problem:
+    """Density of a centrally condensed star for the self-gravity potential: r in [0, 0.5], z in [0, 1]
+    (square cells on the 1024 x 2048 axisymmetric grid), z = 0 the equatorial symmetry plane (reflecting),
+    the axis at r = 0; rho = rho_c (1 - (s/R)^2)^(3/2) inside s = sqrt(r^2 + z^2) < R, a floor of 1e-4 rho_c
+    outside, times 1 + 1e-3 xi with xi the SplitMix64 uniform of the cell (seed ^ cell index); p = rho^(5/3)
+    (only rho matters for the potential)."""
+    gamma = 5.0 / 3.0
+    r = centres(nr, 0.0, 0.5)
+    z = centres(nz, 0.0, 1.0)
+    R, Z = np.meshgrid(r, z)
+    s = np.hypot(R, Z)
+    core = np.clip(1.0 - (s / radius) ** 2, 0.0, None) ** 1.5
+    xi = uniform_cells(seed, nr * nz).reshape(nz, nr)
+    rho = rho_c * np.maximum(core, 1e-4) * (1.0 + 1e-3 * xi)
+    p = rho ** gamma
+    return Problem(name=f"self_gravity_star_{nr}x{nz}", nx=nr, ny=nz, x0=0.0, x1=0.5, y0=0.0, y1=1.0,
+                   gamma=gamma, geometry=1, bc=(AXIS, TRANSMISSIVE, REFLECT, TRANSMISSIVE), nfields=4,
+                   seed=seed, U0=conserved(gamma, rho, 0.0, 0.0, p))
+
+
 ENSEMBLE_SIZES = (128, 256, 512, 1024)
 
 

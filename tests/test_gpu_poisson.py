@@ -76,6 +76,17 @@ def test_converged_solve_bitwise_same_sweeps(dt):
         assert np.array_equal(got_c, ref_c)
 
 
+@pytest.mark.parametrize("tol", [2.0 ** -30, 3.7e-9, 1e-6])
+def test_stopping_test_takes_the_oracle_decision(tol):
+    # a power-of-two tolerance and two others: the per-cell decision fl(|d| / |new|) >= tol is taken with
+    # exponent and mantissa screens plus exact division near tol; the sweep count must be the oracle's
+    p, U, rho = _rz(50, 70, z1=1.4)
+    ref, n_ref = oracle.poisson(p, rho, omega=1.9, tol=tol)
+    got, n, _ = _gpu_solve(p, U, "f64", omega=1.9, tol=tol)
+    assert n == n_ref
+    assert np.array_equal(got, ref)
+
+
 def test_warm_start_and_uniform_sphere():
     # the analytic uniform sphere, and a converged guess stopping after one sweep
     n = 64
