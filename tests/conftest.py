@@ -28,3 +28,17 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print the errors against the oracle that tests record with record_property("err:<name>", value)."""
+    rows = []
+    for key in ("passed", "failed"):
+        for rep in terminalreporter.stats.get(key, []):
+            for k, v in getattr(rep, "user_properties", []):
+                if isinstance(k, str) and k.startswith("err:"):
+                    rows.append((rep.nodeid.split("::")[-1], k[4:], v))
+    if rows:
+        terminalreporter.write_sep("-", "measured errors against the FP64 oracle")
+        for test, name, v in rows:
+            terminalreporter.write_line(f"{test:60s} {name:28s} {v:.3e}")

@@ -49,7 +49,7 @@ def _problem(case, nx=71, ny=47):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_adjoint_step_matches_oracle(case):
+def test_adjoint_step_matches_oracle(case, record_property):
     """One frozen step's adjoint, FP64 to 1e-12 relative L-inf, FP32 to 1e-4."""
     hydro = _hydro()
     p = _problem(case)
@@ -62,6 +62,7 @@ def test_adjoint_step_matches_oracle(case):
         h.adjoint_step(h.state(p.U0), L, dtl[0], al[0].ravel())
         got = L.double().cpu().numpy()
         h.close()
+        record_property(f"err:{dt}_adjoint_rel_linf", _rel_linf(got, ref))
         assert _rel_linf(got, ref) <= tol, (dt, _rel_linf(got, ref))
 
 
@@ -69,7 +70,7 @@ def _kinetic(p, U):
     return float(np.sum(0.5 * (U[1] ** 2 + U[2] ** 2) / U[0]) * p.dx * p.dy)
 
 
-def test_gradient_config_fd_fp64_and_fp32():
+def test_gradient_config_fd_fp64_and_fp32(record_property):
     """Gradient configuration: 256^2 periodic Fourier-mode state, 200 steps, checkpoints every 20 steps,
     d KE(U^200) / d rho_0 at fixed u, v, p through torch autograd, against central differences of the
     frozen forward map on 32 seeded cells (FP64), and FP32 against FP64."""
@@ -101,6 +102,7 @@ def test_gradient_config_fd_fp64_and_fp32():
                     vals.append(_kinetic(p, V.cpu().numpy()))
                 return (vals[0] - vals[1]) / (2 * eps)
 
+            fd_err = 0.0
             for (j, i) in cells:
                 # Richardson-extrapolated central difference (error O(eps^4)); eps large enough that the
                 # change of J stands far above the rounding of the 65536-cell sum
@@ -109,8 +111,11 @@ def test_gradient_config_fd_fp64_and_fp32():
                 # relative to the gradient's scale (its largest entry): cells where the gradient is small
                 # compare at the finite differences' absolute accuracy
                 assert abs(fd - g) <= 1e-6 * np.abs(grads["f64"]).max(), (j, i, fd, g)
+                fd_err = max(fd_err, abs(fd - g) / np.abs(grads["f64"]).max())
+            record_property("err:f64_grad_vs_fd", fd_err)
         h.close()
     err32 = np.abs(grads["f32"] - grads["f64"]).max() / np.abs(grads["f64"]).max()
+    record_property("err:f32_grad_vs_f64", err32)
     assert err32 <= 1e-3, err32
 
 

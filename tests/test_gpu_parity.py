@@ -68,10 +68,11 @@ def test_config1_advected_wave_fp64_matches_oracle():
     assert np.array_equal(got, ref) and t == t_ref and dtl == dt_ref  # same IEEE operations, same order
 
 
-def test_config1_advected_wave_fp32_l1():
+def test_config1_advected_wave_fp32_l1(record_property):
     prob = wl.advected_wave(128)
     got, t, _ = run_gpu(prob, 100, "f32")
     ref, t_ref, _ = oracle.step(prob, prob.U0, 100)
+    record_property("err:fp32_rel_l1", rel_l1(got, ref))
     assert rel_l1(got, ref) <= F32_SMOOTH
     assert abs(t - t_ref) <= 1e-5 * t_ref
 
@@ -118,7 +119,7 @@ def test_ragged_grid_all_boundaries_all_variants(variant):
     assert ran >= 1
 
 
-def test_config2_rayleigh_taylor_reduced_fp64_and_fp32():
+def test_config2_rayleigh_taylor_reduced_fp64_and_fp32(record_property):
     """(r,z) axisymmetric Rayleigh-Taylor with gravity and the level set, at 128x256 for 40 steps."""
     prob = wl.rayleigh_taylor(128, 256, nsteps=40)
     got, t, _ = run_gpu(prob, 40, "f64")
@@ -126,6 +127,7 @@ def test_config2_rayleigh_taylor_reduced_fp64_and_fp32():
     assert rel_linf(got, ref) <= F64_TOL
     assert np.array_equal(got, ref)
     got32, _, _ = run_gpu(prob, 40, "f32")
+    record_property("err:fp32_rel_l1", rel_l1(got32, ref, prob.gamma))
     assert rel_l1(got32, ref, prob.gamma) <= F32_SHOCK
 
 
@@ -139,7 +141,7 @@ def test_config2_rayleigh_taylor_full_size_first_steps():
     assert abs(t - t_ref) <= 1e-13 * t_ref
 
 
-def test_shock_tubes_fp64_and_fp32():
+def test_shock_tubes_fp64_and_fp32(record_property):
     for test in (1, 3, 4):
         prob = wl.shock_tube(test, nx=400, ny=3)
         got, _, _ = run_gpu(prob, 60, "f64")
@@ -147,10 +149,11 @@ def test_shock_tubes_fp64_and_fp32():
         assert rel_linf(got, ref) <= F64_TOL, test
         assert np.array_equal(got, ref), test
         got32, _, _ = run_gpu(prob, 60, "f32")
+        record_property(f"err:fp32_rel_l1_test{test}", rel_l1(got32, ref))
         assert rel_l1(got32, ref) <= F32_SHOCK, test
 
 
-def test_config5_full_size_windows_against_oracle():
+def test_config5_full_size_windows_against_oracle(record_property):
     """8192^2, 5 fields, FP32: the global alpha and dt of step 1 against the oracle on the whole grid,
     and the state after one step on sampled windows: the oracle steps each window with a 9-cell margin
     (the domain of dependence of one RK3 step) using the global alpha / dt, and the window interior is
@@ -180,6 +183,7 @@ def test_config5_full_size_windows_against_oracle():
         ref = oracle.step_frozen(win, sub, [dt_ref], a6.reshape(1, 3, 2))
         cut = ref[:, m:-m, m:-m]
         g = got[:, j0:j0 + w, i0:i0 + w]
+        record_property(f"err:fp32_rel_l1_window_{j0}_{i0}", rel_l1(g, cut))
         assert rel_l1(g, cut) <= F32_SHOCK
 
 
@@ -313,7 +317,7 @@ def test_nonphysical_state_is_reported():
 
 # ------------------------------------------------------------------------------ batched ensemble
 
-def test_batched_ensemble_matches_member_runs():
+def test_batched_ensemble_matches_member_runs(record_property):
     hydro = _hydro()
     members = wl.quadrant_ensemble(6, sizes=(64, 96, 131))
     nsteps = 15
@@ -324,6 +328,8 @@ def test_batched_ensemble_matches_member_runs():
         for p, U, tm in zip(members, Us, t):
             ref, t_ref, _ = oracle.step(p, p.U0, nsteps)
             got = U.double().cpu().numpy()
+            if dt == "f32":
+                record_property(f"err:fp32_rel_l1_{p.name}", fn(got, ref))
             assert fn(got, ref) <= tol, (dt, p.name)
             if dt == "f64":
                 assert np.array_equal(got, ref), p.name

@@ -26,7 +26,7 @@ def _cases():
 
 
 @pytest.mark.parametrize("k", [0, 1])
-def test_reinit_matches_oracle(k):
+def test_reinit_matches_oracle(k, record_property):
     from paper_1507_08549_gb300 import hydro
     p = _cases()[k]
     ref, npts = oracle.reinit(p, p.U0)
@@ -38,6 +38,7 @@ def test_reinit_matches_oracle(k):
         h.close()
         assert n == npts
         err = np.abs(got[4] - ref[4]).max() / np.abs(ref[4]).max()
+        record_property(f"err:{dt}_reinit_rel_linf", err)
         assert err <= tol, (dt, err)
         assert np.array_equal(got[:4], p.U0[:4].astype(np.float32 if dt == "f32" else np.float64))
 
