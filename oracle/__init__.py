@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libhydro_oracle.so")
-_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc", "hydro_oracle_reinit.inc", "hydro_oracle_poisson.inc"]
+_SOURCES = ["hydro_oracle.c", "hydro_oracle.h", "hydro_oracle_adjoint.inc", "hydro_oracle_reinit.inc", "hydro_oracle_poisson.inc", "hydro_oracle_char.inc"]
 _lock = threading.Lock()
 _lib = None
 
@@ -41,7 +41,7 @@ class _Config(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("geometry", ctypes.c_int), ("gravity", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("nfields", ctypes.c_int),
-        ("flame_speed", ctypes.c_double),
+        ("flame_speed", ctypes.c_double), ("scheme", ctypes.c_int),
     ]
 
 
@@ -86,6 +86,7 @@ def _load():
         lib.orc_reinit.argtypes = [cp, dp, ctypes.POINTER(ctypes.c_int)]
         lib.orc_reinit_blend.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.orc_reinit_blend.restype = ctypes.c_double
+        lib.orc_roe_eigen.argtypes = [ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp]
         lib.orc_poisson.argtypes = [cp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
         _lib = lib
@@ -106,6 +107,7 @@ def _cfg(p) -> _Config:
     for k in range(4):
         c.bc[k] = int(p.bc[k])
     c.nfields, c.flame_speed = int(p.nfields), float(p.flame_speed)
+    c.scheme = int(getattr(p, "scheme", 0))
     return c
 
 
@@ -218,6 +220,20 @@ def reinit(p, U):
     npts = ctypes.c_int(0)
     _check(_load().orc_reinit(ctypes.byref(_cfg(p)), _ptr(U), ctypes.byref(npts)), "reinit")
     return U, npts.value
+
+
+def roe_eigen(gamma: float, direction: int, a, b):
+    """Roe average of the conserved states a, b and the eigen-system of the flux Jacobian along
+    `direction` there (rotated frame rho, m_n, m_t, tau). Returns (R, L, lam): R[:, k] is right
+    eigenvector k, L[k, :] left eigenvector k."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    R = np.zeros(16)
+    L = np.zeros(16)
+    lam = np.zeros(4)
+    _check(_load().orc_roe_eigen(float(gamma), int(direction), _ptr(a), _ptr(b), _ptr(R), _ptr(L), _ptr(lam)),
+           "roe_eigen")
+    return R.reshape(4, 4), L.reshape(4, 4), lam
 
 
 def mass(p, rho) -> float:

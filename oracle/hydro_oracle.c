@@ -64,6 +64,7 @@ int orc_validate(const orc_config* c) {
   if (c->bc[1] == ORC_AXIS || c->bc[2] == ORC_AXIS || c->bc[3] == ORC_AXIS) return ORC_EINVAL;
   if (c->bc[0] == ORC_AXIS && (c->geometry != 1 || c->x0 != 0.0)) return ORC_EINVAL;
   if (c->geometry == 1 && c->x0 < 0.0) return ORC_EINVAL;
+  if (c->scheme != 0 && c->scheme != 1) return ORC_EINVAL;
   return ORC_OK;
 }
 
@@ -224,11 +225,24 @@ static void euler_flux(int dir, double gamma, const double Uc[4], double F[4]) {
   }
 }
 
+#include "hydro_oracle_char.inc"
+
 /* Flux difference (fhat_{m+1/2} - fhat_{m-1/2}) / h along one line of n cells for the 4 hydro
  * components. line[c][k] holds component c at line index k - G (k = 0 .. n + 2G - 1). */
 static void line_divergence(int dir, double gamma, double alpha, double h, int n, double* const line[4],
-                            double* const out[4], double* work) {
+                            double* const out[4], double* work, int scheme) {
   const int m = n + 2 * G;
+  if (scheme == 1) { /* characteristic-wise: face fluxes from the Roe-averaged eigen-system */
+    double* fh = work + 8 * m;
+    for (int f = 0; f <= n; ++f) {
+      double o[4];
+      char_face_flux(dir, gamma, alpha, line, f - 1 + G, o);
+      for (int cc = 0; cc < 4; ++cc) fh[cc * (n + 1) + f] = o[cc];
+    }
+    for (int cc = 0; cc < 4; ++cc)
+      for (int i = 0; i < n; ++i) out[cc][i] = (fh[cc * (n + 1) + i + 1] - fh[cc * (n + 1) + i]) / h;
+    return;
+  }
   double* fp = work;          /* [4][m] positive split flux */
   double* fm = work + 4 * m;  /* [4][m] negative split flux */
   double* fh = work + 8 * m;  /* [4][n+1] numerical flux at faces -1/2 .. n-1/2 */
@@ -297,7 +311,7 @@ int orc_rhs(const orc_config* c, const double* U, double ax, double ay, double* 
         op[cc] = out + cc * nx;
         memcpy(lp[cc], P + cc * pn + (size_t)(j + G) * px, sizeof(double) * m);
       }
-      line_divergence(0, c->gamma, ax, dx, nx, lp, op, work);
+      line_divergence(0, c->gamma, ax, dx, nx, lp, op, work, c->scheme);
       for (int cc = 0; cc < 4; ++cc) memcpy(dF + cc * n + (size_t)j * nx, op[cc], sizeof(double) * nx);
       if (nf == 5) {
         double* ph = line + 4 * m;
@@ -326,7 +340,7 @@ int orc_rhs(const orc_config* c, const double* U, double ax, double ay, double* 
         op[cc] = out + cc * ny;
         for (int k = 0; k < m; ++k) lp[cc][k] = P[cc * pn + (size_t)k * px + (i + G)];
       }
-      line_divergence(1, c->gamma, ay, dy, ny, lp, op, work);
+      line_divergence(1, c->gamma, ay, dy, ny, lp, op, work, c->scheme);
       for (int cc = 0; cc < 4; ++cc)
         for (int j = 0; j < ny; ++j) dG[cc * n + (size_t)j * nx + i] = op[cc][j];
       if (nf == 5) {

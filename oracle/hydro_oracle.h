@@ -32,6 +32,8 @@ typedef struct {
   int bc[4];           /* x-lo, x-hi, y-lo, y-hi, values ORC_*                                */
   int nfields;         /* 4 (hydro) or 5 (hydro + level set phi)                              */
   double flame_speed;  /* burning speed s_f of the level-set front                            */
+  int scheme;          /* 0 component-wise WENO5; 1 characteristic-wise with Roe-averaged       *
+                        * eigenvectors (the adjoint covers scheme 0 only)                       */
 } orc_config;
 
 int orc_validate(const orc_config* c);
@@ -60,6 +62,13 @@ int orc_step(const orc_config* c, double* U, int nsteps, double* t, double* dt_l
 /* Same map with dt and the per-stage alphas frozen at the given logged values. */
 int orc_step_frozen(const orc_config* c, double* U, int nsteps, const double* dt_log,
                     const double* alpha_log);
+
+/* Roe average of the conserved states a, b (rho, m_x, m_y, tau) and the eigen-system of the flux
+ * Jacobian along dir (0 x, 1 y) there, in the rotated frame (rho, m_n, m_t, tau): R[4*c + k] is component c
+ * of right eigenvector k, Lm[4*k + c] the left eigenvectors (rows), lam the wave speeds v_n - c, v_n, v_n,
+ * v_n + c. ORC_ENONPHYSICAL if the averaged sound speed is not real. */
+int orc_roe_eigen(double gamma, int dir, const double a[4], const double b[4], double R[16], double Lm[16],
+                  double lam[4]);
 
 /* Conserved totals sum U_f dV, f = 0..4 (phi total is 0 when nfields == 4). */
 int orc_totals(const orc_config* c, const double* U, double out[5]);

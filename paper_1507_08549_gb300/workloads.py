@@ -40,6 +40,7 @@ class Problem:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC, PERIODIC)  # x-lo, x-hi, y-lo, y-hi
     nfields: int = 4
     flame_speed: float = 0.0
+    scheme: int = 0            # 0 component-wise WENO5, 1 characteristic-wise (Roe-averaged eigenvectors)
     nsteps: int = 0            # step count of the workload definition
     seed: int = DEFAULT_SEED
     U0: np.ndarray = field(default=None, repr=False)  # float64 [nfields, ny, nx]
