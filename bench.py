@@ -310,6 +310,11 @@ def run(args):
 
     prob = workload(args.workload)
     dtype = args.dtype or WORKLOADS[args.workload][1]
+    char = args.scheme == "characteristic"
+    if char:
+        if args.workload in ("quadrant_ensemble_64", "fourier_256_adjoint"):
+            raise SystemExit("the characteristic scheme runs single-grid forward workloads")
+        prob = prob.with_(scheme=1)
     if args.workload == "quadrant_ensemble_64":
         return run_ensemble(args, prob, dtype, rank, world, barrier)
     if args.workload == "fourier_256_adjoint":
@@ -355,13 +360,15 @@ def run(args):
         # measured average traffic of a stage launch per cell, times cells
         traffic = TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 * cells
     roof, roof_hbm = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1), (clk or {}).get("sm_mhz"),
-                              alu=(dtype == "f32"), traffic=traffic)
+                              alu=(dtype == "f32" and not char), traffic=None if char else traffic)
+    if char:  # two kernels per stage (char_div_kernel, stage_kernel), timed together
+        roof["kernel"] = "char_div_kernel + stage_kernel"
     # end to end through the public host-buffer entry: every step copies the state in and out
     if args.quick:
         h.close()
         if rank == 0:
-            cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F, "cells": cells, "tile": info,
-                   "autotune_ms_per_step": tune}
+            cfg = {"workload": args.workload, "scheme": args.scheme, "nx": prob.nx, "ny": prob.ny, "nfields": F,
+                   "cells": cells, "tile": info, "autotune_ms_per_step": tune}
             print(json.dumps(_line(args, world, value, ms, dtype, cfg, {"roofline": roof, "roofline_hbm": roof_hbm,
                                                                        "gpu_launches": gpu_launches,
                                                                        "clocks": clk})), flush=True)
@@ -381,7 +388,7 @@ def run(args):
            "d2h_bytes_per_step": state_bytes, "steps": ke}
     # FP32 discrete adjoint of one step (frozen dt / alphas of the step it reverses) and the FP64 plain step
     adjoint = None
-    if not args.no_adjoint and args.workload == "blobs_blast_8192":
+    if not args.no_adjoint and args.workload == "blobs_blast_8192" and not char:
         h.record(2)
         h.step(U, 1)
         dtl, al = h.get_log(1)
@@ -412,6 +419,24 @@ def run(args):
         reinit = {"ms": r0_.elapsed_time(r1_), "front_points": npts,
                   "pair_distances_per_s": npts * cells / (r0_.elapsed_time(r1_) * 1e-3)}
     h.close()
+    characteristic = None
+    if args.workload == "blobs_blast_8192" and not char and not args.no_char:
+        # the characteristic-wise scheme (Roe-averaged eigenvectors) on the same state, FP32
+        hc = hydro.Hydro(prob.with_(scheme=1), dtype=dtype)
+        Uc = hc.state(prob.U0)
+        hc.step(Uc, 1)
+        torch.cuda.synchronize()
+        kc = max(1, args.char_steps)
+        c0_, c1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0_.record()
+        hc.step(Uc, kc)
+        c1_.record()
+        torch.cuda.synchronize()
+        msc = c0_.elapsed_time(c1_) / kc
+        characteristic = {"ms_per_step": msc, "value": cells / (msc * 1e-3), "unit": UNIT, "steps": kc,
+                          "dtype": dtype, "over_component": msc / (ms / args.steps)}
+        hc.close()
+        del Uc
     poisson = poisson_timing(args) if args.workload == "blobs_blast_8192" and not args.no_poisson else None
     fp64 = None
     if not args.no_fp64 and dtype == "f32" and args.workload == "blobs_blast_8192":
@@ -434,7 +459,7 @@ def run(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "nfields": F,
+                "config": {"workload": args.workload, "scheme": args.scheme, "nx": prob.nx, "ny": prob.ny, "nfields": F,
                            "cells": cells, "steps_simulated": args.steps, "t_end": t_sim,
                            "l2": (f"state {F * B * cells / 1e9:.2f} GB per copy > 129 MB L2: no flush needed"
                                   if F * B * cells > 129e6 else
@@ -444,7 +469,7 @@ def run(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
                 "adjoint": adjoint, "fp64_step": fp64, "reinit": reinit,
-                "poisson": poisson}
+                "characteristic": characteristic, "poisson": poisson}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -491,6 +516,10 @@ def poisson_timing(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = h.launch_count() - launches0
+    if getattr(args, "quick", False):  # profiling runs: the fixed sweeps only
+        clocks.stop()
+        h.close()
+        return {"workload": prob.name, "cells": cells, "sweeps": n_fixed, "ms": ms, "gpu_launches": launches}
     phi.zero_()
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c0.record()
@@ -543,12 +572,21 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-poisson", action="store_true")
+    ap.add_argument("--scheme", default="component", choices=["component", "characteristic"],
+                    help="flux reconstruction of the timed run")
+    ap.add_argument("--no-char", action="store_true", help="skip the characteristic-scheme timing")
+    ap.add_argument("--char-steps", type=int, default=5)
     ap.add_argument("--poisson-sweeps", type=int, default=2048)
+    ap.add_argument("--only-poisson", action="store_true",
+                    help="time the self-gravity Poisson solve alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_poisson:
+        print(json.dumps(poisson_timing(args)), flush=True)
+        return 0
     return run(args)
 
 

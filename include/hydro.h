@@ -53,6 +53,14 @@ enum {
   HYDRO_ESIZE = -6          /* a size beyond a fixed limit of an allocation-free entry point     */
 };
 
+/* Flux reconstruction (Sec. 2.1). COMPONENT: WENO5 of each conserved component's Lax-Friedrichs split
+ * flux. CHARACTERISTIC: the "WENO-Roe" construction the paper names (Jiang & Shu 1996): at every face
+ * the split fluxes of the six stencil cells are projected on the left eigenvectors of the flux Jacobian
+ * at the Roe average of the face's two cells, reconstructed per characteristic field with WENO5, and
+ * projected back; the same global alpha serves every field. The adjoint entry points and batched steps
+ * take COMPONENT contexts only (HYDRO_EINVAL otherwise). */
+typedef enum { HYDRO_SCHEME_COMPONENT = 0, HYDRO_SCHEME_CHARACTERISTIC = 1 } hydro_scheme;
+
 typedef struct {
   int nx, ny;               /* interior cells, >= 3 each                                         */
   double x0, x1, y0, y1;    /* domain; with geometry 1, x is r and x0 >= 0                        */
@@ -64,6 +72,7 @@ typedef struct {
   int nfields;              /* 4 (hydro) or 5 (hydro + level set phi)                             */
   double flame_speed;       /* burning speed s_f of the level-set front (phi > 0 ash)             */
   int dtype;                /* hydro_dtype                                                       */
+  int scheme;               /* hydro_scheme: how the hydro fluxes are reconstructed               */
 } hydro_config;
 
 /* Create a context for one grid: validates cfg (HYDRO_EINVAL on a bad field, an unpaired periodic

@@ -66,6 +66,7 @@ struct hydro_ctx {
   bool track_totals = true;
   // graph of one step
   cudaGraphExec_t step_graph = nullptr;
+  long long step_graph_launches = 0;
   // per-launch profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
@@ -82,6 +83,8 @@ struct hydro_ctx {
   void* seg = nullptr;
   size_t seg_cap = 0;
   int ck_nsteps = -1, ck_every = 0;
+  // characteristic scheme: padded D = dF/dx + dG/dy of the 4 hydro fields, written per stage
+  void* char_div = nullptr;
   // level-set reinitialisation: front points (x, y pairs) and their count
   void* front = nullptr;
   int* front_count = nullptr;
@@ -140,6 +143,10 @@ static int validate_config(const hydro_config* g, std::string* why) {
     return HYDRO_EINVAL;
   }
   if (g->geometry == 1 && g->x0 < 0.0) { *why = "(r,z) grids need r >= 0"; return HYDRO_EINVAL; }
+  if (g->scheme != HYDRO_SCHEME_COMPONENT && g->scheme != HYDRO_SCHEME_CHARACTERISTIC) {
+    *why = "scheme must be HYDRO_SCHEME_COMPONENT or HYDRO_SCHEME_CHARACTERISTIC";
+    return HYDRO_EINVAL;
+  }
   if (!std::isfinite(g->gravity_y) || !std::isfinite(g->flame_speed) || g->flame_speed < 0.0) {
     *why = "gravity and flame speed must be finite, flame speed >= 0";
     return HYDRO_EINVAL;
@@ -187,6 +194,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   base.dt_cur = &s->dt_cur;
   base.t_acc = &s->t_acc;
   base.err = &s->err;
+  base.ext_div = static_cast<const real*>(c->char_div);
   real* A = bufp<real>(c, 0);
   real* B = bufp<real>(c, 1);
   real* C = bufp<real>(c, 2);
@@ -280,6 +288,10 @@ static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double
     }
     CK(cudaEventRecord(c->ev[c->ev_used], s));
   }
+  if (c->char_div) {  // characteristic scheme: the hydro divergence of this stage's input first
+    CK(launch_char_div<real>(p, c->cfg.nx, c->cfg.ny, s));
+    c->launches++;
+  }
   CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), s));
   if (prof) {
     CK(cudaEventRecord(c->ev[c->ev_used + 1], s));
@@ -306,8 +318,11 @@ static int ensure_graph(hydro_ctx* c) {
   if (c->step_graph) return HYDRO_OK;
   cudaGraph_t gr = nullptr;
   CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+  const long long before = c->launches;
   int rc = launch_step<real>(c, false, c->capture);
   cudaError_t e = cudaStreamEndCapture(c->capture, &gr);
+  c->step_graph_launches = c->launches - before;
+  c->launches = before;  // captured, not launched
   if (rc) {
     if (gr) cudaGraphDestroy(gr);
     return rc;
@@ -316,7 +331,6 @@ static int ensure_graph(hydro_ctx* c) {
   e = cudaGraphInstantiate(&c->step_graph, gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-  c->launches -= 3;  // captured, not launched
   return HYDRO_OK;
 }
 
@@ -379,7 +393,7 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
       rc = launch_step<real>(c, true, c->stream);
     } else if (use_graph) {
       CK(cudaGraphLaunch(c->step_graph, c->stream));
-      c->launches += 3;
+      c->launches += c->step_graph_launches;
     } else {
       rc = launch_step<real>(c, false, c->stream);
     }
@@ -436,6 +450,11 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
     if (cudaMalloc(&c->buf[k], bytes) != cudaSuccess) return bail(HYDRO_ECUDA);
     if (cudaMemsetAsync(c->buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   }
+  if (cfg->scheme == HYDRO_SCHEME_CHARACTERISTIC) {
+    const size_t db = (size_t)4 * c->fstride * c->esize;
+    if (cudaMalloc(&c->char_div, db) != cudaSuccess) return bail(HYDRO_ECUDA);
+    if (cudaMemsetAsync(c->char_div, 0, db, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
+  }
   const size_t sb = c->esize == 8 ? sizeof(Scratch<double>) : sizeof(Scratch<float>);
   if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
@@ -483,6 +502,7 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->seg);
   cudaFree(c->front);
   cudaFree(c->front_count);
+  cudaFree(c->char_div);
   if (c->host_scratch) cudaFreeHost(c->host_scratch);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->done) cudaEventDestroy(c->done);
@@ -859,6 +879,8 @@ int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nstep
     if (!members[k] || !U[k]) return fail(c, HYDRO_EINVAL, "null member or state");
     if (members[k]->cfg.dtype != c->cfg.dtype || members[k]->nf != c->nf || members[k]->device != c->device)
       return fail(c, HYDRO_EINVAL, "members must share dtype, nfields and device");
+    if (members[k]->cfg.scheme != HYDRO_SCHEME_COMPONENT)
+      return fail(c, HYDRO_EINVAL, "batched steps take component-wise contexts (step characteristic ones one by one)");
   }
   if (c->cfg.dtype == HYDRO_F64) return batch_impl<double>(members, U, n, nsteps, t);
   return batch_impl<float>(members, U, n, nsteps, t);
@@ -964,6 +986,8 @@ int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, c
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U_n || !lambda || !alpha || !(dt >= 0.0)) return fail(c, HYDRO_EINVAL, "bad adjoint arguments");
+  if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
+    return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");
   for (int k = 0; k < 6; ++k)
     if (!(alpha[k] >= 0.0) || !std::isfinite(alpha[k])) return fail(c, HYDRO_EINVAL, "alphas must be finite, >= 0");
   if (c->cfg.dtype == HYDRO_F64)
@@ -975,6 +999,8 @@ int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U || nsteps < 1) return fail(c, HYDRO_EINVAL, "bad arguments");
+  if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
+    return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");
   if (every <= 0) every = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
   every = std::min(every, nsteps);
   const int nseg = (nsteps + every - 1) / every;

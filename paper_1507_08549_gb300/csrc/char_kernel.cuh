@@ -1,0 +1,212 @@
+// char_kernel.cuh -- characteristic-wise WENO5 flux divergence (Leung, Chu & Lin 2015, Sec. 2.1: the
+// "WENO-Roe" construction of Jiang & Shu 1996).
+//
+// At every face the Lax-Friedrichs split fluxes f+- = (F +- alpha U) / 2 of the six stencil cells are
+// projected on the left eigenvectors of the flux Jacobian at the Roe average of the face's two cells,
+// each characteristic field is reconstructed with WENO5 (f+ left-biased, f- right-biased), and the sum
+// is projected back with the right eigenvectors. The eigen-system is written in the rotated frame
+// (rho, m_n, m_t, tau) so that x and y faces run the same instructions:
+//   R = [1, 1, 0, 1; u_n - c, u_n, 0, u_n + c; u_t, u_t, 1, u_t; H - u_n c, q^2/2, u_t, H + u_n c]
+//   L = R^-1 = [(b2 + u_n/c)/2, -(b1 u_n + 1/c)/2, -b1 u_t/2, b1/2;  1 - b2, b1 u_n, b1 u_t, -b1;
+//               -u_t, 0, 1, 0;  (b2 - u_n/c)/2, -(b1 u_n - 1/c)/2, -b1 u_t/2, b1/2],
+//   b1 = (gamma - 1)/c^2, b2 = b1 q^2/2, from s = sqrt(rho): v~ = (s_l v_l + s_r v_r)/(s_l + s_r) for u_n,
+//   u_t and H = (tau + p)/rho, c^2 = (gamma - 1)(H - q^2/2).
+//
+// char_div_kernel writes D = dF/dx + dG/dy of the four hydro components for one stage input into a
+// padded buffer laid out like the states; the stage kernel then takes D from there instead of its own
+// component-wise passes (the level set, sources, RK blend and reductions are unchanged). One CTA holds a
+// 32 x 8 tile with a 3-cell halo in shared memory; one thread per face computes the face flux (x faces,
+// then y faces), then one thread per cell differences them.
+//
+// FP64: every operation the plain definition writes, in its order, rounded once (products by the 0 and 1
+// entries of R and L included), so D is reproducible bit for bit by a sequential implementation.
+// FP32: the same arithmetic with fused operations and the shared-smoothness WENO of the stage kernel.
+#pragma once
+#include "stage_kernel.cuh"
+
+namespace hydro {
+
+constexpr int CX = 32, CY = 8;                // cells per tile
+constexpr int CBW = CX + 6, CBH = CY + 6;     // halo box
+constexpr int CHAR_THREADS = CX * CY;         // 256
+
+template <typename real>
+struct CharSmem {
+  real U[4][CBH][CBW];
+  real u[CBH][CBW], v[CBH][CBW], p[CBH][CBW];
+  real FX[4][CY][CX + 1];   // x-face fluxes, face f left of tile column f
+  real FY[4][CY + 1][CX];   // y-face fluxes, face f below tile row f
+};
+
+// operation policy: FP64 rounds each written operation once; FP32 lets the compiler fuse
+template <typename real>
+struct CO;
+
+template <>
+struct CO<double> {
+  static __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sq(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double rc(double a) { return __ddiv_rn(1.0, a); }
+  static __device__ __forceinline__ double weno(double a, double b, double c, double d, double e) {
+    return Ar<double>::weno5(a, b, c, d, e);
+  }
+};
+
+template <>
+struct CO<float> {
+  static __device__ __forceinline__ float ad(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float sb(float a, float b) { return a - b; }
+  static __device__ __forceinline__ float ml(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float dv(float a, float b) { return a * RT<float>::rcp(b); }
+  static __device__ __forceinline__ float sq(float a) { return RT<float>::sqrt_(a); }
+  static __device__ __forceinline__ float rc(float a) { return RT<float>::rcp(a); }
+  static __device__ __forceinline__ float weno(float a, float b, float c, float d, float e) {
+    return weno_side(a, b, c, d, e, betas(a, b, c).m, betas(b, c, d).t, betas(c, d, e).p);
+  }
+};
+
+// Face flux between box cells (r, c) and its right (dir 0) or upper (dir 1) neighbour. out[] in the frame
+// (rho, m_x, m_y, tau). Returns false when the averaged sound speed is not real.
+template <typename real>
+__device__ __forceinline__ bool char_face(const CharSmem<real>& S, int dir, int r, int c, real alpha, real gm1,
+                                          real out[4]) {
+  using O = CO<real>;
+  const int n = dir == 0 ? 1 : 2, t = dir == 0 ? 2 : 1;
+  const int dr = dir == 0 ? 0 : 1, dc = dir == 0 ? 1 : 0;
+  // Roe average of the cells l = (r, c) and l + 1
+  real s[2], vn[2], vt[2], H[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int rr = r + k * dr, cc = c + k * dc;
+    const real rho = S.U[0][rr][cc];
+    s[k] = O::sq(rho);
+    vn[k] = dir == 0 ? S.u[rr][cc] : S.v[rr][cc];
+    vt[k] = dir == 0 ? S.v[rr][cc] : S.u[rr][cc];
+    H[k] = O::dv(O::ad(S.U[3][rr][cc], S.p[rr][cc]), rho);
+  }
+  const real den = O::ad(s[0], s[1]);
+  const real un = O::dv(O::ad(O::ml(s[0], vn[0]), O::ml(s[1], vn[1])), den);
+  const real ut = O::dv(O::ad(O::ml(s[0], vt[0]), O::ml(s[1], vt[1])), den);
+  const real h = O::dv(O::ad(O::ml(s[0], H[0]), O::ml(s[1], H[1])), den);
+  const real q2 = O::ad(O::ml(un, un), O::ml(ut, ut));
+  const real c2 = O::ml(gm1, O::sb(h, O::ml(real(0.5), q2)));
+  if (!(c2 > real(0)) || !isfinite(c2)) return false;
+  const real cs = O::sq(c2), rcs = O::rc(cs);
+  const real b1 = O::dv(gm1, c2), b2 = O::ml(real(0.5), O::ml(b1, q2));
+  const real Lm[4][4] = {
+      {O::ml(real(0.5), O::ad(b2, O::ml(un, rcs))), O::ml(real(-0.5), O::ad(O::ml(b1, un), rcs)),
+       O::ml(real(-0.5), O::ml(b1, ut)), O::ml(real(0.5), b1)},
+      {O::sb(real(1), b2), O::ml(b1, un), O::ml(b1, ut), -b1},
+      {-ut, real(0), real(1), real(0)},
+      {O::ml(real(0.5), O::sb(b2, O::ml(un, rcs))), O::ml(real(-0.5), O::sb(O::ml(b1, un), rcs)),
+       O::ml(real(-0.5), O::ml(b1, ut)), O::ml(real(0.5), b1)}};
+  // projected split fluxes of the six stencil cells l-2 .. l+3
+  real wp[4][6], wm[4][6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int rr = r + (k - 2) * dr, cc = c + (k - 2) * dc;
+    const real Ur[4] = {S.U[0][rr][cc], S.U[n][rr][cc], S.U[t][rr][cc], S.U[3][rr][cc]};
+    const real vnk = dir == 0 ? S.u[rr][cc] : S.v[rr][cc];
+    const real pk = S.p[rr][cc];
+    // rotated flux (m_n, m_n v_n + p, m_t v_n, (tau + p) v_n), as the frame flux's components
+    const real Fr[4] = {Ur[1], O::ad(O::ml(Ur[1], vnk), pk), O::ml(Ur[2], vnk), O::ml(O::ad(Ur[3], pk), vnk)};
+    real fp[4], fm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Ar<real>::split(Fr[q], Ur[q], alpha, fp[q], fm[q]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      wp[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fp[0]), O::ml(Lm[w][1], fp[1])), O::ml(Lm[w][2], fp[2])),
+                       O::ml(Lm[w][3], fp[3]));
+      wm[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fm[0]), O::ml(Lm[w][1], fm[1])), O::ml(Lm[w][2], fm[2])),
+                       O::ml(Lm[w][3], fm[3]));
+    }
+  }
+  real wh[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+    wh[w] = O::ad(O::weno(wp[w][0], wp[w][1], wp[w][2], wp[w][3], wp[w][4]),
+                  O::weno(wm[w][5], wm[w][4], wm[w][3], wm[w][2], wm[w][1]));
+  const real Rm[4][4] = {{real(1), real(1), real(0), real(1)},
+                         {O::sb(un, cs), un, real(0), O::ad(un, cs)},
+                         {ut, ut, real(1), ut},
+                         {O::sb(h, O::ml(un, cs)), O::ml(real(0.5), q2), ut, O::ad(h, O::ml(un, cs))}};
+  real fr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    fr[q] = O::ad(O::ad(O::ad(O::ml(Rm[q][0], wh[0]), O::ml(Rm[q][1], wh[1])), O::ml(Rm[q][2], wh[2])),
+                  O::ml(Rm[q][3], wh[3]));
+  out[0] = fr[0];
+  out[n] = fr[1];
+  out[t] = fr[2];
+  out[3] = fr[3];
+  return true;
+}
+
+// D = dF/dx + dG/dy of the hydro components of the stage input p->win into p->ext_div (padded layout).
+template <typename real>
+__global__ void __launch_bounds__(CHAR_THREADS) char_div_kernel(const GridParams<real>* __restrict__ pp) {
+  __shared__ CharSmem<real> S;
+  const GridParams<real>& g = *pp;
+  const int nx = g.nx, ny = g.ny, pitch = g.pitch;
+  const long long fs = g.fstride;
+  const long long rows_alloc = fs / pitch;
+  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * CY;
+  const int tid = threadIdx.x;
+  const real gm1 = g.gm1;
+  // box cell (r, c) is grid cell (x0 - 3 + c, y0 - 3 + r): padded element (y0 + r) * pitch + (x0 + 1 + c)
+  for (int idx = tid; idx < CBH * CBW; idx += CHAR_THREADS) {
+    const int r = idx / CBW, c = idx - r * CBW;
+    const long long row = y0 + r, col = x0 + 1 + c;
+    const bool in = row < rows_alloc && col < pitch;
+    const long long e = row * pitch + col;
+    real U[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      U[f] = in ? g.win[f * fs + e] : real(0);
+      S.U[f][r][c] = U[f];
+    }
+    real u = real(0), v = real(0), p = real(0);
+    if (in && U[0] != real(0)) Ar<real>::prims(U[0], U[1], U[2], U[3], gm1, u, v, p);
+    S.u[r][c] = u;
+    S.v[r][c] = v;
+    S.p[r][c] = p;
+  }
+  __syncthreads();
+  const real ax = g.alpha_in[0], ay = g.alpha_in[1];
+  bool bad = false;
+  // x faces: tile row fr, face fc (left of tile column fc); needed for rows < ny and faces <= nx - x0
+  for (int it = tid; it < CY * (CX + 1); it += CHAR_THREADS) {
+    const int fr = it / (CX + 1), fc = it - fr * (CX + 1);
+    real o[4] = {real(0), real(0), real(0), real(0)};
+    if (y0 + fr < ny && x0 + fc <= nx) bad |= !char_face(S, 0, fr + 3, fc + 2, ax, gm1, o);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) S.FX[f][fr][fc] = o[f];
+  }
+  // y faces: face fr below tile row fr, tile column fc
+  for (int it = tid; it < (CY + 1) * CX; it += CHAR_THREADS) {
+    const int fr = it / CX, fc = it - fr * CX;
+    real o[4] = {real(0), real(0), real(0), real(0)};
+    if (x0 + fc < nx && y0 + fr <= ny) bad |= !char_face(S, 1, fr + 2, fc + 3, ay, gm1, o);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) S.FY[f][fr][fc] = o[f];
+  }
+  if (bad) atomicOr(g.err, ERR_NONPHYSICAL);
+  __syncthreads();
+  const int tr = tid / CX, tc = tid - tr * CX;
+  const int i = x0 + tc, j = y0 + tr;
+  if (i < nx && j < ny) {
+    const long long e = static_cast<long long>(j + GY) * pitch + i + GX;
+    real* D = const_cast<real*>(g.ext_div);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const real dxf = Ar<real>::divided(S.FX[f][tr][tc + 1], S.FX[f][tr][tc], g.rdx, g.dx);
+      const real dyf = Ar<real>::divided(S.FY[f][tr + 1][tc], S.FY[f][tr][tc], g.rdy, g.dy);
+      D[f * fs + e] = Ar<real>::sum(dxf, dyf);
+    }
+  }
+}
+
+}  // namespace hydro

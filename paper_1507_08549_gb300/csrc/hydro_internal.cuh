@@ -63,6 +63,7 @@ struct GridParams {
   double* totals;         // 5 FP64 totals of the output (last stage), may be null
   double* totals_reset;   // totals array to clear (stage 1), may be null
   int* err;               // error bits
+  const real* ext_div;    // characteristic scheme: D = dF/dx + dG/dy of the hydro fields (padded), else null
 };
 
 // Launch-wide stage control.
@@ -105,6 +106,10 @@ cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geomet
 
 // Level-set reinitialisation (reinit_kernel.cuh): front points where phi changes sign between
 // neighbouring cells (linear interpolation), minimum distance of every cell to them, tanh blend.
+// Characteristic-wise flux divergence of p_dev->win into p_dev->ext_div (one launch per stage).
+template <typename real>
+cudaError_t launch_char_div(const GridParams<real>* p_dev, int nx, int ny, cudaStream_t s);
+
 template <typename real>
 cudaError_t launch_reinit(real* phi, int nx, int ny, int pitch, double x0, double y0, double dx, double dy,
                           real* front, int capacity, int* count, int* err, cudaStream_t s, int* launches);

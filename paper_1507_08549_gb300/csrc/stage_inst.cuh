@@ -3,6 +3,7 @@
 #pragma once
 #include "adjoint_kernel.cuh"
 #include "reinit_kernel.cuh"
+#include "char_kernel.cuh"
 #include "aux_kernels.cuh"
 
 namespace hydro {
@@ -121,6 +122,13 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
   else
     totals_partial_kernel<HYDRO_REAL, 4><<<nblocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, partials);
   totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, nfields, out);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_char_div<HYDRO_REAL>(const GridParams<HYDRO_REAL>* p_dev, int nx, int ny, cudaStream_t s) {
+  const dim3 grid((nx + CX - 1) / CX, (ny + CY - 1) / CY);
+  char_div_kernel<HYDRO_REAL><<<grid, CHAR_THREADS, 0, s>>>(p_dev);
   return cudaGetLastError();
 }
 

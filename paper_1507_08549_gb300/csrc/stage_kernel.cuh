@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         const int S = xp ? 1 : W;
         const int DS = xp ? 1 : TX;
         if (c < 4) {
+          if (g.ext_div) continue;  // characteristic scheme: the divergence comes from char_div_kernel
           const int kind = (c == 0) ? 0 : (c == 3) ? 3 : ((c == 1) == xp) ? 1 : 2;
           const real* Uc = sU + (c * H + brow) * W + bcol;
           const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
@@ -700,7 +701,11 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             real Uv[4], Dv[4], un[4];
             load4(sU + (f * H + srow) * W + scol, Uv);
             if (f < 4) {
-              load4(sD + (f * TY + row) * TX + tcol, Dv);
+              if (g.ext_div) {
+                load4(g.ext_div + f * fs + gbase, Dv);
+              } else {
+                load4(sD + (f * TY + row) * TX + tcol, Dv);
+              }
             } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
               real xm[4], xq[4], ym[4], yq[4];
               load4(sX + (0 * TY + row) * TX + tcol, xm);

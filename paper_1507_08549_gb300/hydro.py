@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 HYDRO_F32, HYDRO_F64 = 0, 1
+SCHEME_COMPONENT, SCHEME_CHARACTERISTIC = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECT, BC_AXIS = 0, 1, 2, 3
 OK, EINVAL, ECUDA, ENONPHYSICAL, ETIMEOUT, ESTATE, ESIZE = 0, -1, -2, -3, -4, -5, -6
 _NAMES = {EINVAL: "HYDRO_EINVAL", ECUDA: "HYDRO_ECUDA", ENONPHYSICAL: "HYDRO_ENONPHYSICAL",
@@ -36,7 +37,7 @@ class hydro_config(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("geometry", ctypes.c_int), ("gravity_y", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("nfields", ctypes.c_int),
-        ("flame_speed", ctypes.c_double), ("dtype", ctypes.c_int),
+        ("flame_speed", ctypes.c_double), ("dtype", ctypes.c_int), ("scheme", ctypes.c_int),
     ]
 
 
@@ -127,6 +128,7 @@ def make_config(p, dtype: int) -> hydro_config:
     for k in range(4):
         c.bc[k] = int(p.bc[k])
     c.nfields, c.flame_speed, c.dtype = int(p.nfields), float(p.flame_speed), int(dtype)
+    c.scheme = int(getattr(p, "scheme", 0))
     return c
 
 
