@@ -189,6 +189,8 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   base.rdx = static_cast<real>(1.0 / base.dx);
   base.rdy = static_cast<real>(1.0 / base.dy);
   base.x0 = g.x0;
+  base.dx_r = static_cast<real>(base.dx);
+  base.x0_r = static_cast<real>(g.x0);
   base.cfl_delta = g.cfl * std::min(base.dx, base.dy);
   base.smax = &s->smax;
   base.dt_cur = &s->dt_cur;

@@ -47,6 +47,7 @@ struct GridParams {
   real gamma, gm1, gravity, flame_speed;
   real rdx, rdy;       // 1/dx, 1/dy
   double dx, dy, x0;   // FP64 copies for geometry and totals
+  real dx_r, x0_r;     // dx and x0 in the state precision (FP32 radii)
   double cfl_delta;    // c_cfl * min(dx, dy)
   // reduction slots (device)
   const real* alpha_in;   // (alpha_x, alpha_y) used by this stage

@@ -189,11 +189,16 @@ struct Ar<float> {
     const float inner = rb * T::fma_(dt, L, w);
     return use_un ? T::fma_(ra, un, inner) : inner;
   }
+  // cell-centre radius r_i = x0 + (i + 1/2) dx, in FP32
+  template <typename G>
+  static __device__ __forceinline__ float radius(const G& g, int i) {
+    return T::fma_(static_cast<float>(i) + 0.5f, g.dx_r, g.x0_r);
+  }
   static __device__ __forceinline__ float source(int f, bool rz, float grav, float rho, float mr, float mz, float E,
-                                                float u, float v, float p, double x0, int i, double dx) {
+                                                float u, float v, float p, float r) {
     float S = 0.0f;
     if (rz) {  // -(1/r)(rho v_r, rho v_r^2, rho v_r v_z, (tau + p) v_r)
-      const float rinv = T::rcp(static_cast<float>(x0 + (i + 0.5) * dx));
+      const float rinv = T::rcp(r);
       S = (f == 0) ? -mr * rinv : (f == 1) ? -(mr * u) * rinv : (f == 2) ? -(mr * v) * rinv : -((E + p) * u) * rinv;
     }
     if (f == 2) S = T::fma_(rho, grav, S);  // -rho dPhi/dz with dPhi/dz = -g
@@ -250,12 +255,15 @@ struct Ar<double> {
     const double inner = ml(rb, ad(w, ml(dt, L)));
     return use_un ? ad(ml(ra, un), inner) : inner;
   }
+  // cell-centre radius r_i = x0 + (i + 1/2) dx, each operation rounded once
+  template <typename G>
+  static __device__ __forceinline__ double radius(const G& g, int i) {
+    return ad(g.x0, ml(i + 0.5, g.dx));
+  }
   static __device__ __forceinline__ double source(int f, bool rz, double grav, double rho, double mr, double mz,
-                                                 double E, double u, double v, double p, double x0, int i,
-                                                 double dx) {
+                                                 double E, double u, double v, double p, double r) {
     double S = 0.0;
     if (rz) {
-      const double r = ad(x0, ml(i + 0.5, dx));
       S = (f == 0) ? dv(-mr, r) : (f == 1) ? dv(-ml(mr, u), r) : (f == 2) ? dv(-ml(mr, v), r) : dv(-ml(ad(E, p), u), r);
     }
     if (grav != 0.0) {
@@ -522,6 +530,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_DOUBLES);  // two barriers, one per box buffer
   __shared__ GridParams<real> g;
   __shared__ int s_abort;
+  // stage scalars, formed once per CTA and member (dt needs an FP64 division at stage 0; the FP64 pipe
+  // is 1/64 of the FP32 rate, so no per-thread FP64 work stays in the tile loop of the FP32 kernel)
+  __shared__ double s_dtd;
+  __shared__ real s_dt, s_ra, s_rb;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -552,7 +564,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int tile = work ? work[w].tile : w;
     if (member != cur_member) {
       __syncthreads();
-      if (tid == 0) g = members[member];
+      if (tid == 0) {
+        g = members[member];
+        const double d = ctl.stage == 0 ? (g.dt_src ? *g.dt_src : g.cfl_delta / static_cast<double>(*g.smax))
+                                        : *g.dt_cur;
+        s_dtd = d;
+        s_dt = static_cast<real>(d);
+        s_ra = static_cast<real>(ctl.rk_a);
+        s_rb = static_cast<real>(ctl.rk_b);
+      }
       __syncthreads();
       cur_member = member;
     }
@@ -570,13 +590,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
     // stage scalars (overlap with the copies)
     const real ax = g.alpha_in[0], ay = g.alpha_in[1];
-    double dtd;
-    if (ctl.stage == 0) {
-      dtd = g.dt_src ? *g.dt_src : g.cfl_delta / static_cast<double>(*g.smax);
-    } else {
-      dtd = *g.dt_cur;
-    }
-    if (tile == 0 && tid == 0 && ctl.mode == 0) {  // once per grid and stage
+    if (tile == 0 && tid == 0 && ctl.mode == 0) {
+      const double dtd = s_dtd;  // once per grid and stage
       if (ctl.stage == 0) {
         *g.dt_cur = dtd;
         *g.t_acc += dtd;
@@ -671,14 +686,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
     // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
     real amx = real(0), amy = real(0), smx = real(0);
+    // totals: FP64 per cell in the FP64 kernel; the FP32 kernel sums U_f (times r in (r,z)) over a thread's
+    // cells and then over its warp in FP32, and the warp partials across the CTA, tiles and grid in FP64,
+    // with dV = dx dy (or 2 pi dr dz) applied once at the end
     double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    real totr[5] = {real(0), real(0), real(0), real(0), real(0)};
     {
       const int nx = g.nx, ny = g.ny;
       const real gamma = g.gamma, grav = g.gravity, sf = g.flame_speed;
       const bool rz = g.geometry == 1;
-      const real dt = static_cast<real>(dtd);
-      const real ra = static_cast<real>(ctl.rk_a), rb = static_cast<real>(ctl.rk_b);
-      const bool use_un = ctl.rk_a != 0.0 && ctl.mode == 0;
+      const real dt = s_dt;
+      const real ra = s_ra, rb = s_rb;
+      const bool use_un = ra != real(0) && ctl.mode == 0;
       constexpr int NG = TX / 4;
       for (int it2 = tid; it2 < TY * NG; it2 += NT) {
         const int row = it2 / NG, g4 = it2 - row * NG;
@@ -689,7 +708,11 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         const int srow = row + 3, scol = 4 + 4 * g4, tcol = 4 * g4;
         real o[NF][4];
         {
-          real u4[4], v4[4], p4[4];
+          real u4[4], v4[4], p4[4], rr[4];
+          if (rz) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) rr[e] = Ar<real>::radius(g, ib + e);
+          }
           const bool need_prims = rz || grav != real(0) || NF == 5;
           if (need_prims) {
             load4(su + row * W + scol, u4);
@@ -729,7 +752,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               if (f < 4 && (rz || grav != real(0))) {
                 const real rho = sU[(0 * H + srow) * W + scol + e], mr = sU[(1 * H + srow) * W + scol + e];
                 const real mz = sU[(2 * H + srow) * W + scol + e], E = sU[(3 * H + srow) * W + scol + e];
-                S = Ar<real>::source(f, rz, grav, rho, mr, mz, E, u4[e], v4[e], p4[e], g.x0, ib + e, g.dx);
+                S = Ar<real>::source(f, rz, grav, rho, mr, mz, E, u4[e], v4[e], p4[e], rr[e]);
               }
               const real L = (f < 4) ? Ar<real>::lval(Dv[e], S) : -Dv[e];
               o[f][e] = (ctl.mode == 1) ? L : Ar<real>::blend(use_un, ra, rb, un[e], Uv[e], dt, L);
@@ -772,9 +795,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           amy = fmax(amy, sy);
           smx = fmax(smx, sm);
           if (g.totals) {
-            const double dV = rz ? 6.283185307179586 * (g.x0 + (i + 0.5) * g.dx) * g.dx * g.dy : g.dx * g.dy;
+            if constexpr (sizeof(real) == 4) {
+              const real wr = rz ? T::fma_(static_cast<real>(i) + real(0.5), g.dx_r, g.x0_r) : real(1);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) tot[f] = fma(static_cast<double>(o[f][e]), dV, tot[f]);
+              for (int f = 0; f < NF; ++f) totr[f] = T::fma_(o[f][e], wr, totr[f]);
+            } else {
+              const double dV = rz ? 6.283185307179586 * (g.x0 + (i + 0.5) * g.dx) * g.dx * g.dy : g.dx * g.dy;
+#pragma unroll
+              for (int f = 0; f < NF; ++f) tot[f] = fma(static_cast<double>(o[f][e]), dV, tot[f]);
+            }
           }
         }
       }
@@ -790,10 +819,19 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       }
       const bool want_tot = g.totals != nullptr;
       if (want_tot) {
+        if constexpr (sizeof(real) == 4) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f)
+          for (int f = 0; f < NF; ++f) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) tot[f] += __shfl_xor_sync(0xffffffffu, tot[f], o);
+            for (int o = 16; o > 0; o >>= 1) totr[f] += __shfl_xor_sync(0xffffffffu, totr[f], o);
+            tot[f] = static_cast<double>(totr[f]);
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot[f] += __shfl_xor_sync(0xffffffffu, tot[f], o);
+        }
       }
       if (lane == 0) {
         red[warp * 8 + 0] = static_cast<double>(amx);
@@ -812,7 +850,11 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         if (tid == 0 && g.alpha_out) T::atomic_max(&g.alpha_out[0], static_cast<real>(acc));
         if (tid == 1 && g.alpha_out) T::atomic_max(&g.alpha_out[1], static_cast<real>(acc));
         if (tid == 2 && ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(acc));
-        if (tid >= 3 && tid < 3 + NF && want_tot) atomicAdd(&g.totals[tid - 3], acc);
+        if (tid >= 3 && tid < 3 + NF && want_tot) {
+          if constexpr (sizeof(real) == 4)  // the cell volume, applied once
+            acc *= g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
+          atomicAdd(&g.totals[tid - 3], acc);
+        }
       }
     }
     // the next copy overwrites the box: everyone is done reading it (generic proxy) before TMA writes

@@ -220,6 +220,24 @@ def test_rhs_operator_fp64(case):
 
 # ------------------------------------------------------------------------------ properties
 
+@pytest.mark.parametrize("case", ["cartesian_blobs", "rz_rayleigh_taylor"])
+def test_fused_totals_fp32(case, record_property):
+    """FP32 contexts sum each warp's cells in FP32 and the partials in FP64: the fused totals agree with
+    the FP64 sum of the same FP32 state to 1e-6 of sum |U_f dV|."""
+    hydro = _hydro()
+    prob = wl.blobs_blast(512) if case == "cartesian_blobs" else wl.rayleigh_taylor(256, 512, nsteps=3)
+    h = hydro.Hydro(prob, dtype="f32")
+    U = h.state(prob.U0)
+    h.step(U, 3)
+    fused = h.last_totals()
+    ref = h.totals(U)
+    absU = h.totals(U.abs())
+    h.close()
+    err = max(abs(fused[f] - ref[f]) / absU[f] for f in range(prob.nfields))
+    record_property("err:fp32_fused_totals_rel", err)
+    assert err <= 1e-6
+
+
 def test_periodic_conservation_on_gpu_fp64():
     prob = wl.advected_wave(96)
     hydro = _hydro()
