@@ -21,26 +21,51 @@
 namespace hydro {
 
 // gbar * dW/dv of the WENO5-JS value W(a, b, c, d, e) (Jiang & Shu weights), added to g[0..4].
+// With D_k = eps + beta_k, alpha_k = d_k / D_k^2, w_k = alpha_k / sum alpha:
+//   dW/dv = sum_k w_k dq_k/dv + sum_k (q_k - W) / sum alpha * dalpha_k/dbeta_k * dbeta_k/dv,
+//   dalpha_k/dbeta_k = -2 alpha_k / D_k,  dbeta_k/dv = 13/6 s_k ds_k/dv + 1/2 t_k dt_k/dv.
+// FP32 forms the four reciprocals 1/D_k and 1/sum alpha with approximate reciprocals and folds the 1/6 of
+// the candidate values into their coefficients; FP64 keeps true divisions.
 template <typename real>
 __device__ __forceinline__ void weno5_grad_acc(real a, real b, real c, real d, real e, real gbar, real& ga,
                                                real& gb, real& gc, real& gd, real& ge) {
-  const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
-  const real q1 = (-b + real(5) * c + real(2) * d) / real(6);
-  const real q2 = (real(2) * c + real(5) * d - e) / real(6);
   const real s0 = a - real(2) * b + c, t0 = a - real(4) * b + real(3) * c;
   const real s1 = b - real(2) * c + d, t1 = b - d;
   const real s2 = c - real(2) * d + e, t2 = real(3) * c - real(4) * d + e;
   const real D0 = real(1e-6) + real(13.0 / 12.0) * s0 * s0 + real(0.25) * t0 * t0;
   const real D1 = real(1e-6) + real(13.0 / 12.0) * s1 * s1 + real(0.25) * t1 * t1;
   const real D2 = real(1e-6) + real(13.0 / 12.0) * s2 * s2 + real(0.25) * t2 * t2;
-  const real a0 = real(0.1) / (D0 * D0), a1 = real(0.6) / (D1 * D1), a2 = real(0.3) / (D2 * D2);
-  const real rS = real(1) / (a0 + a1 + a2);
+  real q0, q1, q2, a0, a1, a2, rS, n0, n1, n2;  // n_k = -2 alpha_k / D_k
+  if constexpr (sizeof(real) == 4) {
+    using T = RT<float>;
+    q0 = T::fma_(real(1.0 / 3.0), a, T::fma_(real(-7.0 / 6.0), b, real(11.0 / 6.0) * c));
+    q1 = T::fma_(real(-1.0 / 6.0), b, T::fma_(real(5.0 / 6.0), c, real(1.0 / 3.0) * d));
+    q2 = T::fma_(real(1.0 / 3.0), c, T::fma_(real(5.0 / 6.0), d, real(-1.0 / 6.0) * e));
+    const real r0 = T::rcp(D0), r1 = T::rcp(D1), r2 = T::rcp(D2);
+    a0 = real(0.1) * r0 * r0;
+    a1 = real(0.6) * r1 * r1;
+    a2 = real(0.3) * r2 * r2;
+    rS = T::rcp(a0 + a1 + a2);
+    n0 = real(-2) * a0 * r0;
+    n1 = real(-2) * a1 * r1;
+    n2 = real(-2) * a2 * r2;
+  } else {
+    q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
+    q1 = (-b + real(5) * c + real(2) * d) / real(6);
+    q2 = (real(2) * c + real(5) * d - e) / real(6);
+    a0 = real(0.1) / (D0 * D0);
+    a1 = real(0.6) / (D1 * D1);
+    a2 = real(0.3) / (D2 * D2);
+    rS = real(1) / (a0 + a1 + a2);
+    n0 = real(-2) * a0 / D0;
+    n1 = real(-2) * a1 / D1;
+    n2 = real(-2) * a2 / D2;
+  }
   const real w0 = a0 * rS, w1 = a1 * rS, w2 = a2 * rS;
   const real W = w0 * q0 + w1 * q1 + w2 * q2;
-  // d alpha_k / d beta_k = -2 alpha_k / D_k ; d beta_k / dv = 13/6 s_k ds_k + 1/2 t_k dt_k
-  const real c0 = (q0 - W) * rS * (real(-2) * a0 / D0);
-  const real c1 = (q1 - W) * rS * (real(-2) * a1 / D1);
-  const real c2 = (q2 - W) * rS * (real(-2) * a2 / D2);
+  const real c0 = (q0 - W) * rS * n0;
+  const real c1 = (q1 - W) * rS * n1;
+  const real c2 = (q2 - W) * rS * n2;
   const real A0 = c0 * real(13.0 / 6.0) * s0, B0 = c0 * real(0.5) * t0;
   const real A1 = c1 * real(13.0 / 6.0) * s1, B1 = c1 * real(0.5) * t1;
   const real A2 = c2 * real(13.0 / 6.0) * s2, B2 = c2 * real(0.5) * t2;
@@ -72,12 +97,17 @@ __device__ __forceinline__ real weno5_plain(real a, real b, real c, real d, real
 template <typename real>
 __device__ __forceinline__ void flux_jacobian(int dir, real gamma, real rho, real mx, real my, real E,
                                               real J[4][4]) {
-  const real u = mx / rho, v = my / rho;
+  real rr;  // 1 / rho
+  if constexpr (sizeof(real) == 4)
+    rr = RT<float>::rcp(rho);
+  else
+    rr = real(1) / rho;
+  const real u = sizeof(real) == 4 ? mx * rr : mx / rho, v = sizeof(real) == 4 ? my * rr : my / rho;
   const real gm1 = gamma - real(1);
   const real p = gm1 * (E - real(0.5) * (mx * u + my * v));
   const real dp[4] = {gm1 * real(0.5) * (u * u + v * v), -gm1 * u, -gm1 * v, gm1};
-  const real du[4] = {-u / rho, real(1) / rho, real(0), real(0)};
-  const real dv[4] = {-v / rho, real(0), real(1) / rho, real(0)};
+  const real du[4] = {sizeof(real) == 4 ? -u * rr : -u / rho, rr, real(0), real(0)};
+  const real dv[4] = {sizeof(real) == 4 ? -v * rr : -v / rho, real(0), rr, real(0)};
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const real dmx = (s == 1) ? real(1) : real(0), dmy = (s == 2) ? real(1) : real(0);
