@@ -221,6 +221,9 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
 // ---------------------------------------------------------------------------- line adjoints
 
 constexpr int ATX = 32, ATY = 16, ARUN = 8;   // output points per tile, points per line item
+// threads per CTA: one line item each in both passes (NF x 64 items) for FP32, two CTAs per SM
+template <typename real, int NF>
+__host__ __device__ constexpr int adj_threads() { return sizeof(real) == 4 ? NF * 64 : 256; }
 constexpr int AHX = 6;                        // box halo (hydro needs 5, level set 6)
 constexpr int ABW = ATX + 2 * AHX, ABH = ATY + 2 * AHX;
 
@@ -228,8 +231,8 @@ template <typename real, int NF>
 struct ATile {
   static constexpr int BOX = ABW * ABH;
   static constexpr int OFF_W = 0;                        // [NF][ABH][ABW] state
-  static constexpr int OFF_P = OFF_W + NF * BOX;         // [4][ABH][ABW]  u, v, p, 1/rho
-  static constexpr int OFF_N = OFF_P + 4 * BOX;          // [NF][ABH][ABW] nu
+  static constexpr int OFF_P = OFF_W + NF * BOX;         // [3][ABH][ABW]  u, v, p
+  static constexpr int OFF_N = OFF_P + 3 * BOX;          // [NF][ABH][ABW] nu
   static constexpr int OFF_H = OFF_N + NF * BOX;         // [4][ABH][ABW]  hb (level set)
   static constexpr int OFF_PB = OFF_H + (NF == 5 ? 4 * BOX : 0);  // [4][ATY][ATX] f+bar + f-bar
   static constexpr int OFF_MB = OFF_PB + 4 * ATY * ATX;  // [4][ATY][ATX] f+bar - f-bar
@@ -239,7 +242,10 @@ struct ATile {
 };
 
 // One hydro line of ARUN output points: faces f = -2 .. ARUN+2 relative to the first output point,
-// points m = -5 .. ARUN+4. Writes (f+bar + f-bar) and (f+bar - f-bar) of the outputs.
+// points m = -5 .. ARUN+4. Writes (f+bar + f-bar) and (f+bar - f-bar) of the outputs. The faces advance
+// left to right; a point's split fluxes are formed just before the first face that reads them (face m-1)
+// and its output is written after the last face that adds to it (face m+3), so only a six-point window
+// of values is live at a time.
 template <typename real>
 __device__ __forceinline__ void adj_hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
                                                const real* __restrict__ vel, const real* __restrict__ pr,
@@ -247,8 +253,7 @@ __device__ __forceinline__ void adj_hydro_line(const real* __restrict__ Uc, cons
                                                real* __restrict__ pb, real* __restrict__ mb, int DS) {
   constexpr int NP = ARUN + 10;  // points, index m + 5
   real fp[NP], fm[NP], ap[NP], am[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
+  auto point = [&](int q) {
     const int m = q - 5;
     const real uu = Uc[m * S];
     real F;
@@ -261,23 +266,27 @@ __device__ __forceinline__ void adj_hydro_line(const real* __restrict__ Uc, cons
     fm[q] = real(0.5) * (F - alpha * uu);
     ap[q] = real(0);
     am[q] = real(0);
-  }
+  };
+#pragma unroll
+  for (int q = 0; q < 5; ++q) point(q);  // points -5 .. -1
 #pragma unroll
   for (int f = -2; f <= ARUN + 2; ++f) {
-    // face f lies between points f-1 and f; its left-biased stencil is points f-3 .. f+1
+    // face f lies between points f-1 and f; its left-biased stencil is points f-3 .. f+1 and its
+    // right-biased one f+2 .. f-2: point f+2 is new
+    const int q = f + 5;
+    if (q + 2 < NP) point(q + 2);
     const real fb = (nuc[f * S] - nuc[(f - 1) * S]) * rd;
     if (fb != real(0)) {
-      const int q = f + 5;
       weno5_grad_acc(fp[q - 3], fp[q - 2], fp[q - 1], fp[q], fp[q + 1], fb, ap[q - 3], ap[q - 2], ap[q - 1], ap[q],
                      ap[q + 1]);
       weno5_grad_acc(fm[q + 2], fm[q + 1], fm[q], fm[q - 1], fm[q - 2], fb, am[q + 2], am[q + 1], am[q], am[q - 1],
                      am[q - 2]);
     }
-  }
-#pragma unroll
-  for (int k = 0; k < ARUN; ++k) {
-    pb[k * DS] = ap[k + 5] + am[k + 5];
-    mb[k * DS] = ap[k + 5] - am[k + 5];
+    const int k = f - 3;  // output point completed by this face
+    if (k >= 0 && k < ARUN) {
+      pb[k * DS] = ap[k + 5] + am[k + 5];
+      mb[k * DS] = ap[k + 5] - am[k + 5];
+    }
   }
 }
 
@@ -290,29 +299,34 @@ __device__ __forceinline__ void adj_phi_line(const real* __restrict__ ph, const 
                                                    int DS) {
   constexpr int ND = ARUN + 11;  // differences D_n, n = -6 .. ARUN+4, index n + 6
   real D[ND], Db[ND];
-#pragma unroll
-  for (int q = 0; q < ND; ++q) {
+  // D_n formed just before the first cell that reads it, outputs written after the last cell that adds
+  // to the differences they need (a six-value window is live at a time)
+  auto diff = [&](int q) {
     const int n = q - 6;
     D[q] = (ph[(n + 1) * S] - ph[n * S]) * rd;
     Db[q] = real(0);
-  }
+  };
+#pragma unroll
+  for (int q = 0; q < 5; ++q) diff(q);
 #pragma unroll
   for (int i = -3; i <= ARUN + 2; ++i) {
-    const real bm = hm[i * S], bp = hp[i * S];
     const int q = i + 6;
+    if (q + 2 < ND) diff(q + 2);
+    const real bm = hm[i * S], bp = hp[i * S];
     if (bm != real(0))
       weno5_grad_acc(D[q - 3], D[q - 2], D[q - 1], D[q], D[q + 1], bm, Db[q - 3], Db[q - 2], Db[q - 1], Db[q],
                      Db[q + 1]);
     if (bp != real(0))
       weno5_grad_acc(D[q + 2], D[q + 1], D[q], D[q - 1], D[q - 2], bp, Db[q + 2], Db[q + 1], Db[q], Db[q - 1],
                      Db[q - 2]);
+    const int k = i - 3;  // output whose two differences are complete
+    if (k >= 0 && k < ARUN) dst[k * DS] += (Db[k - 1 + 6] - Db[k + 6]) * rd;
   }
-#pragma unroll
-  for (int k = 0; k < ARUN; ++k) dst[k * DS] += (Db[k - 1 + 6] - Db[k + 6]) * rd;
 }
 
 template <typename real, int NF>
-__global__ void __launch_bounds__(256) adj_line_kernel(AdjParams<real> P, int tiles_x) {
+__global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2 : 1)
+    adj_line_kernel(AdjParams<real> P, int tiles_x) {
   using TL = ATile<real, NF>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(256) adj_line_kernel(AdjParams<real> P, int ti
   real* sMB = sm + TL::OFF_MB;
   real* sMU = sm + TL::OFF_MU;
   const int tid = threadIdx.x;
-  constexpr int NT = 256;
+  constexpr int NT = adj_threads<real, NF>();
   const long long fs = P.fstride;
   // output points are padded-grid points: columns 1 .. nx+6 (cells -3 .. nx+2), rows 0 .. ny+5
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;

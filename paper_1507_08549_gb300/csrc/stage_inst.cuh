@@ -165,7 +165,8 @@ cudaError_t adj_nf(const AdjParams<HYDRO_REAL>& P, cudaStream_t s, int* launches
     return r;
   }();
   if (cfg != cudaSuccess) return cfg;
-  adj_line_kernel<HYDRO_REAL, NF><<<tiles_x * tiles_y, 256, ATile<HYDRO_REAL, NF>::BYTES, s>>>(P, tiles_x);
+  adj_line_kernel<HYDRO_REAL, NF><<<tiles_x * tiles_y, adj_threads<HYDRO_REAL, NF>(), ATile<HYDRO_REAL, NF>::BYTES, s>>>(
+      P, tiles_x);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj_blend_kernel<HYDRO_REAL, NF><<<pg, 256, 0, s>>>(P);
