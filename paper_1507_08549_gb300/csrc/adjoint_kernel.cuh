@@ -80,17 +80,21 @@ __device__ __forceinline__ void weno5_grad_acc(real a, real b, real c, real d, r
 
 template <typename real>
 __device__ __forceinline__ real weno5_plain(real a, real b, real c, real d, real e) {
-  const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
-  const real q1 = (-b + real(5) * c + real(2) * d) / real(6);
-  const real q2 = (real(2) * c + real(5) * d - e) / real(6);
-  const real s0 = a - real(2) * b + c, t0 = a - real(4) * b + real(3) * c;
-  const real s1 = b - real(2) * c + d, t1 = b - d;
-  const real s2 = c - real(2) * d + e, t2 = real(3) * c - real(4) * d + e;
-  const real D0 = real(1e-6) + real(13.0 / 12.0) * s0 * s0 + real(0.25) * t0 * t0;
-  const real D1 = real(1e-6) + real(13.0 / 12.0) * s1 * s1 + real(0.25) * t1 * t1;
-  const real D2 = real(1e-6) + real(13.0 / 12.0) * s2 * s2 + real(0.25) * t2 * t2;
-  const real a0 = real(0.1) / (D0 * D0), a1 = real(0.6) / (D1 * D1), a2 = real(0.3) / (D2 * D2);
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  if constexpr (sizeof(real) == 4) {  // the stage kernel's FP32 form (shared-smoothness WENO)
+    return weno_side(a, b, c, d, e, betas(a, b, c).m, betas(b, c, d).t, betas(c, d, e).p);
+  } else {
+    const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);
+    const real q1 = (-b + real(5) * c + real(2) * d) / real(6);
+    const real q2 = (real(2) * c + real(5) * d - e) / real(6);
+    const real s0 = a - real(2) * b + c, t0 = a - real(4) * b + real(3) * c;
+    const real s1 = b - real(2) * c + d, t1 = b - d;
+    const real s2 = c - real(2) * d + e, t2 = real(3) * c - real(4) * d + e;
+    const real D0 = real(1e-6) + real(13.0 / 12.0) * s0 * s0 + real(0.25) * t0 * t0;
+    const real D1 = real(1e-6) + real(13.0 / 12.0) * s1 * s1 + real(0.25) * t1 * t1;
+    const real D2 = real(1e-6) + real(13.0 / 12.0) * s2 * s2 + real(0.25) * t2 * t2;
+    const real a0 = real(0.1) / (D0 * D0), a1 = real(0.6) / (D1 * D1), a2 = real(0.3) / (D2 * D2);
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  }
 }
 
 // dF_r/dU_s of the Euler flux along x (dir 0) or y (dir 1) at one state.
