@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     mbar_init(&bar[1], 1);
     s_abort = 0;
   }
+  for (int k = tid; k < TL::RED_DOUBLES; k += NT) red[k] = 0.0;
   __syncthreads();
 
   // prologue: the first work item's box
@@ -557,12 +558,39 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   unsigned parity[2] = {0u, 0u};
   int cur_member = -1;
   int it = 0;
+  // Reductions of the outputs (next stage's alpha, next step's dt, FP64 totals) accumulate per warp in
+  // red[warp * 8 + slot] across this CTA's tiles of one member (each tile: a warp shuffle, lane 0
+  // updates its slots) and are flushed -- one block combine and one atomic per slot -- when the member
+  // changes and at the end, instead of a block reduction with two barriers per tile.
+  auto flush = [&]() {
+    if (ctl.mode != 0) return;
+    __syncthreads();
+    if (tid < 8) {
+      double acc = 0.0;
+      for (int wi = 0; wi < NWARPS; ++wi) {
+        const double v = red[wi * 8 + tid];
+        acc = (tid < 3) ? fmax(acc, v) : acc + v;
+      }
+      if (tid == 0 && g.alpha_out) T::atomic_max(&g.alpha_out[0], static_cast<real>(acc));
+      if (tid == 1 && g.alpha_out) T::atomic_max(&g.alpha_out[1], static_cast<real>(acc));
+      if (tid == 2 && ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(acc));
+      if (tid >= 3 && tid < 3 + NF && g.totals) {
+        if constexpr (sizeof(real) == 4)  // the cell volume, applied once
+          acc *= g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
+        atomicAdd(&g.totals[tid - 3], acc);
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < TL::RED_DOUBLES; k += NT) red[k] = 0.0;
+    __syncthreads();
+  };
   for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++it) {
     const int b = it & 1;
     real* sU = sm + (b ? TL::OFF_U1 : TL::OFF_U0);
     const int member = work ? work[w].member : 0;
     const int tile = work ? work[w].tile : w;
     if (member != cur_member) {
+      if (cur_member >= 0) flush();
       __syncthreads();
       if (tid == 0) {
         g = members[member];
@@ -809,7 +837,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       }
     }
 
-    // block reductions: maxima (next alpha / dt) and FP64 totals, one atomic per tile and slot
+    // this tile's warp reductions into the warp's running slots
     if (ctl.mode == 0) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -834,33 +862,19 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
       }
       if (lane == 0) {
-        red[warp * 8 + 0] = static_cast<double>(amx);
-        red[warp * 8 + 1] = static_cast<double>(amy);
-        red[warp * 8 + 2] = static_cast<double>(smx);
+        double* r = red + warp * 8;
+        r[0] = fmax(r[0], static_cast<double>(amx));
+        r[1] = fmax(r[1], static_cast<double>(amy));
+        r[2] = fmax(r[2], static_cast<double>(smx));
         if (want_tot)
-          for (int f = 0; f < NF; ++f) red[warp * 8 + 3 + f] = tot[f];
-      }
-      __syncthreads();
-      if (tid < 8) {
-        double acc = (tid < 3) ? 0.0 : 0.0;
-        for (int wi = 0; wi < NWARPS; ++wi) {
-          const double v = red[wi * 8 + tid];
-          acc = (tid < 3) ? fmax(acc, v) : acc + v;
-        }
-        if (tid == 0 && g.alpha_out) T::atomic_max(&g.alpha_out[0], static_cast<real>(acc));
-        if (tid == 1 && g.alpha_out) T::atomic_max(&g.alpha_out[1], static_cast<real>(acc));
-        if (tid == 2 && ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(acc));
-        if (tid >= 3 && tid < 3 + NF && want_tot) {
-          if constexpr (sizeof(real) == 4)  // the cell volume, applied once
-            acc *= g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
-          atomicAdd(&g.totals[tid - 3], acc);
-        }
+          for (int f = 0; f < NF; ++f) r[3 + f] += tot[f];
       }
     }
     // the next copy overwrites the box: everyone is done reading it (generic proxy) before TMA writes
     __syncthreads();
     fence_proxy_async_smem();
   }
+  if (cur_member >= 0) flush();
 }
 
 }  // namespace hydro
