@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -53,7 +54,8 @@ struct hydro_ctx {
   long long fstride = 0;
   void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
   void* scratch = nullptr;
-  void* params = nullptr;  // device GridParams[7]: normal stages 0..2, frozen stages 3..5, rhs 6
+  void* params = nullptr;  // device GridParams[8]: normal stages 0..2, frozen stages 3..5, rhs 6, and slot 7 =
+                           // stage 2 writing a host-buffer caller's state directly (set per call)
   void* host_scratch = nullptr;  // pinned copy of Scratch
   double* partials = nullptr;
   int partial_blocks = 0;
@@ -378,17 +380,21 @@ static int read_status(hydro_ctx* c, double* t_inout, double* dt_last) {
 
 template <typename real>
 static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double* dt_last, const double* dtl,
-                     const double* al) {
+                     const double* al, real* host_out = nullptr) {
   const bool frozen = dtl != nullptr;
   int rc = pack_state<real>(c, U, t_inout ? *t_inout : 0.0);
   if (rc) return rc;
-  const bool use_graph = !frozen && !c->profiling && nsteps > 1;
+  // host_out: U is the caller's state in mapped host memory (the pack above read it over the host link);
+  // the last step's final stage writes the result straight back there, so no staging copies remain
+  const bool direct = host_out != nullptr && !frozen && nsteps > 0;
+  const int nloop = direct ? nsteps - 1 : nsteps;
+  const bool use_graph = !frozen && !c->profiling && nloop > 1;
   if (use_graph) {
     rc = ensure_graph<real>(c);
     if (rc) return rc;
   }
   Scratch<real>* s = scr<real>(c);
-  for (int st = 0; st < nsteps; ++st) {
+  for (int st = 0; st < nloop; ++st) {
     if (frozen) {
       CK(launch_set_frozen<real>(&s->frozen_dt, dtl[st], &s->frozen_alpha[0][0], al + 6 * st, c->stream));
       c->launches++;
@@ -401,8 +407,23 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
     }
     if (rc) return rc;
   }
-  rc = unpack_state<real>(c, U, 0);
-  if (rc) return rc;
+  if (direct) {
+    GridParams<real> all[7];
+    build_params<real>(c, all);
+    GridParams<real> last = all[2];
+    last.out_dense = host_out;
+    last.dense_fs = (long long)c->cfg.nx * c->cfg.ny;
+    last.dense_vec = (c->cfg.nx % 4 == 0 && reinterpret_cast<uintptr_t>(host_out) % 16 == 0) ? 1 : 0;
+    CK(cudaMemcpyAsync(static_cast<GridParams<real>*>(c->params) + 7, &last, sizeof(last), cudaMemcpyHostToDevice,
+                       c->stream));
+    rc = launch_one<real>(c, 0, 0, 0, RK_A[0], RK_B[0], c->stream);
+    if (!rc) rc = launch_one<real>(c, 1, 1, 0, RK_A[1], RK_B[1], c->stream);
+    if (!rc) rc = launch_one<real>(c, 7, 2, 0, RK_A[2], RK_B[2], c->stream);
+    if (rc) return rc;
+  } else {
+    rc = unpack_state<real>(c, U, 0);
+    if (rc) return rc;
+  }
   if (frozen) {
     double tt = t_inout ? *t_inout : 0.0;
     for (int st = 0; st < nsteps; ++st) tt += dtl[st];
@@ -461,7 +482,7 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
-  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 7 : sizeof(GridParams<float>) * 7;
+  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 8 : sizeof(GridParams<float>) * 8;
   if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->partial_blocks = 4 * c->num_sms;
   if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
@@ -540,6 +561,20 @@ int hydro_step_host(hydro_ctx* c, void* U_host, int nsteps, double* t_inout, dou
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U_host || nsteps < 0) return fail(c, HYDRO_EINVAL, "null state or negative step count");
+  // pinned (page-locked, mapped) host memory: the kernels read and write it directly over the host link
+  cudaPointerAttributes at{};
+  const bool mapped = cudaPointerGetAttributes(&at, U_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      at.devicePointer != nullptr && nsteps > 0;
+  if (!mapped) (void)cudaGetLastError();
+  if (mapped) {
+    if (c->cfg.dtype == HYDRO_F64) {
+      double* dp = static_cast<double*>(at.devicePointer);
+      return step_impl<double>(c, dp, nsteps, t_inout, dt_last, nullptr, nullptr, dp);
+    }
+    float* dp = static_cast<float*>(at.devicePointer);
+    return step_impl<float>(c, dp, nsteps, t_inout, dt_last, nullptr, nullptr, dp);
+  }
+  // pageable memory: stage through a device copy
   rc = ensure_unpadded(c);
   if (rc) return rc;
   const size_t bytes = (size_t)c->nf * c->cfg.nx * c->cfg.ny * c->esize;

@@ -787,16 +787,32 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             }
           }
         }
-        // stores
+        // stores: the padded working state, or (last stage of a host-buffer call) the caller's dense
+        // state in host memory, written directly over the host link
+        if (g.out_dense) {
+          const long long hbase = static_cast<long long>(j) * nx + ib;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          real* dstp = g.out + f * fs + gbase;
-          if (nvalid == 4) {
-            store4(dstp, o[f]);
-          } else {
+          for (int f = 0; f < NF; ++f) {
+            real* dstp = g.out_dense + f * g.dense_fs + hbase;
+            if (nvalid == 4 && g.dense_vec) {
+              store4(dstp, o[f]);
+            } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (e < nvalid) dstp[e] = o[f][e];
+              for (int e = 0; e < 4; ++e)
+                if (e < nvalid) dstp[e] = o[f][e];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            real* dstp = g.out + f * fs + gbase;
+            if (nvalid == 4) {
+              store4(dstp, o[f]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (e < nvalid) dstp[e] = o[f][e];
+            }
           }
         }
         if (ctl.mode == 1) continue;
@@ -805,7 +821,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         for (int e = 0; e < 4; ++e) {
           if (e >= nvalid) break;
           const int i = ib + e;
-          if (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3) {
+          if (!g.out_dense && (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3)) {
             real val[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) val[f] = o[f][e];

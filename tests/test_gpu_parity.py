@@ -318,6 +318,28 @@ def test_frozen_replay_reproduces_the_run_and_host_entry():
     h.close()
 
 
+@pytest.mark.parametrize("dt,n,nsteps,scheme", [("f64", 64, 1, 0), ("f32", 61, 5, 0), ("f32", 64, 3, 1),
+                                                 ("f64", 37, 4, 0)])
+def test_pinned_host_entry_matches_device_steps(dt, n, nsteps, scheme):
+    """Pinned host buffers are read by the pack kernel and written by the last stage directly over the
+    host link (4-wide stores when rows are 16-byte aligned, scalar otherwise): same bits, time and
+    totals as the device entry point."""
+    import torch
+    hydro = _hydro()
+    prob = wl.kelvin_helmholtz(n).with_(scheme=scheme)
+    h = hydro.Hydro(prob, dtype=dt)
+    U = h.state(prob.U0)
+    t, dl = h.step(U, nsteps)
+    tot = h.last_totals()
+    host = torch.from_numpy(np.ascontiguousarray(prob.U0.astype(np.float64 if dt == "f64" else np.float32)))
+    pinned = host.pin_memory()
+    th, dlh = h.step_host(pinned.numpy(), nsteps)
+    assert np.array_equal(pinned.numpy(), U.cpu().numpy())
+    assert th == t and dlh == dl
+    np.testing.assert_allclose(h.last_totals(), tot, rtol=1e-12, atol=1e-300)
+    h.close()
+
+
 def test_nonphysical_state_is_reported():
     hydro = _hydro()
     prob = wl.advected_wave(32)
