@@ -46,6 +46,25 @@ def _dist():
     return rank, world
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value of x over the ranks of the default process group (the slowest replica's time);
+    x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each processed units_per_rank units, timed by the
+    slowest one (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -246,7 +265,7 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     launches = sum(h.launch_count() for h in hs) - l0
     F, B = members[0].nfields, (8 if dtype == "f64" else 4)
     roof, roof_hbm = roofline(F, B, cells, ms / (3 * args.steps), (clk or {}).get("sm_mhz"), alu=(dtype == "f32"))
@@ -257,7 +276,7 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
         sizes = sorted({(p.nx, p.ny) for p in members})
         cfg = {"workload": args.workload, "members": len(members), "cells": cells, "sizes": len(sizes),
                "seed": members[0].seed, "graph": "3 persistent launches per step, replayed from a CUDA graph"}
-        print(json.dumps(_line(args, world, world * cells * args.steps / (ms * 1e-3), ms, dtype, cfg,
+        print(json.dumps(_line(args, world, replica_rate(cells * args.steps, ms * 1e-3, world), ms, dtype, cfg,
                                {"roofline": roof, "roofline_hbm": roof_hbm, "gpu_launches": launches,
                                 "clocks": clk})), flush=True)
     return 0
@@ -283,12 +302,15 @@ def run_gradient(args, prob, dtype, rank, world, barrier):
     h.adjoint_sweep(lam)
     torch.cuda.synchronize()
     adj = time.perf_counter() - t0
+    barrier()
+    fwd, adj = max_over_ranks(fwd, world), max_over_ranks(adj, world)
     h.close()
     if rank == 0:
         cfg = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "checkpoint_every": 20}
         extra = {"adjoint": {"sweep_ms": adj * 1e3, "forward_ms": fwd * 1e3, "adjoint_over_forward": adj / fwd},
                  "e2e": None}
-        print(json.dumps(_line(args, world, world * prob.cells * args.steps / fwd, fwd * 1e3, dtype, cfg, extra)),
+        print(json.dumps(_line(args, world, replica_rate(prob.cells * args.steps, fwd, world), fwd * 1e3, dtype, cfg,
+                               extra)),
               flush=True)
     return 0
 
@@ -348,12 +370,9 @@ def run(args):
     nlaunch_stage, stage_ms = h.stage_timing()
     h.profile(False)
     gpu_launches = h.launch_count() - launches0
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world)
     cells = prob.nx * prob.ny
-    value = world * cells * args.steps / (ms * 1e-3)
+    value = replica_rate(cells * args.steps, ms * 1e-3, world)
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
     traffic = None
     if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast"):
@@ -379,12 +398,15 @@ def run(args):
     h.step_host(Uh_pinned, 1)
     torch.cuda.synchronize()
     ke = max(1, min(args.steps, args.e2e_steps))
+    barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
         h.step_host(Uh_pinned, 1)
     e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_s = max_over_ranks(e2e_s, world)
     state_bytes = F * B * cells
-    e2e = {"value": world * cells * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+    e2e = {"value": replica_rate(cells * ke, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes, "steps": ke}
     # FP32 discrete adjoint of one step (frozen dt / alphas of the step it reverses) and the FP64 plain step
     adjoint = None
