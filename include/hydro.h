@@ -143,6 +143,13 @@ int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dty
  * Allocates its point buffer (2 points per cell) on first use. Synchronises the stream. */
 int hydro_reinit(hydro_ctx* ctx, void* U, int* npoints);
 
+/* Self-test of the device failure path: one thread runs the stage kernel's bounded wait on an mbarrier
+ * that nothing completes, for `polls` polls (1 .. 2^24; ~2^20 take a few milliseconds), and the call
+ * returns what a lost tile copy returns: HYDRO_ETIMEOUT ("a device wait gave up"). No GPU state is left
+ * behind and the context stays usable. HYDRO_EINVAL for polls outside the range. Synchronises the
+ * stream. */
+int hydro_wait_selftest(hydro_ctx* ctx, unsigned polls);
+
 /* Self-gravity potential Phi of the density rho = U[0] on an (r,z) grid (geometry 1), Sec. 2.1:
  * (1/r) d/dr (r dPhi/dr) + d2Phi/dz2 = 4 pi G rho, solved by successive over-relaxation of red-black
  * Gauss-Seidel sweeps (red: i + j even, then black) with

@@ -1321,3 +1321,16 @@ int hydro_exact_sum(hydro_ctx* c, const double* x, long long n, double* out) {
   if (h->nonfinite) return fail(c, HYDRO_ENONPHYSICAL, "a term is inf or NaN");
   return HYDRO_OK;
 }
+
+// ---- failure-path self-test
+
+int hydro_wait_selftest(hydro_ctx* c, unsigned polls) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (polls == 0 || polls > (1u << 24)) return fail(c, HYDRO_EINVAL, "polls must be in 1 .. 2^24");
+  int* err = c->cfg.dtype == HYDRO_F64 ? &scr<double>(c)->err : &scr<float>(c)->err;
+  CK(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  CK(launch_wait_selftest(polls, err, c->stream));
+  c->launches++;
+  return c->cfg.dtype == HYDRO_F64 ? read_status<double>(c, nullptr, nullptr) : read_status<float>(c, nullptr, nullptr);
+}

@@ -110,6 +110,9 @@ cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geomet
 
 // Level-set reinitialisation (reinit_kernel.cuh): front points where phi changes sign between
 // neighbouring cells (linear interpolation), minimum distance of every cell to them, tanh blend.
+// One bounded device wait that nothing completes (polls polls), reporting ERR_TIMEOUT into *err.
+cudaError_t launch_wait_selftest(unsigned polls, int* err, cudaStream_t s);
+
 // Characteristic-wise flux divergence of p_dev->win into p_dev->ext_div (one launch per stage).
 template <typename real>
 cudaError_t launch_char_div(const GridParams<real>* p_dev, int nx, int ny, cudaStream_t s);

@@ -97,13 +97,20 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^28 polls (seconds) and reports ERR_TIMEOUT.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 28); ++it) {
+// Bounded wait on an mbarrier phase: false after `limit` polls (the caller reports ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
   }
   return false;
 }
+
+// The stage kernel's wait for a tile's copies: ~2^28 polls (seconds) before giving up.
+constexpr unsigned TILE_WAIT_POLLS = 1u << 28;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  return mbar_wait_limit(bar, parity, TILE_WAIT_POLLS);
+}
+
 
 // ------------------------------------------------------------------------------ WENO5 pieces
 

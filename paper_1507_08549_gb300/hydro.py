@@ -47,7 +47,7 @@ EXPORTS = [
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
-    "hydro_poisson", "hydro_exact_sum",
+    "hydro_poisson", "hydro_exact_sum", "hydro_wait_selftest",
 ]
 
 _lock = threading.Lock()
@@ -105,6 +105,7 @@ def load(build_if_needed: bool = True):
             "hydro_poisson": ([ctxp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, ip, dp],
                               ctypes.c_int),
             "hydro_exact_sum": ([ctxp, vp, ctypes.c_longlong, dp], ctypes.c_int),
+            "hydro_wait_selftest": ([ctxp, ctypes.c_uint], ctypes.c_int),
             "conserved_totals_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, dp],
                                          ctypes.c_int),
@@ -296,6 +297,11 @@ class Hydro:
         self._check(self.lib.hydro_exact_sum(self.ctx, ctypes.c_void_p(x.data_ptr()), int(x.numel()),
                                              ctypes.byref(out)), "hydro_exact_sum")
         return out.value
+
+    def wait_selftest(self, polls: int = 1 << 16) -> int:
+        """Run the bounded device wait on a barrier nothing completes (hydro_wait_selftest); returns the
+        C return code (HYDRO_ETIMEOUT when the failure path works) without raising."""
+        return int(self.lib.hydro_wait_selftest(self.ctx, int(polls)))
 
     def tile_variants(self):
         n, cur = ctypes.c_int(), ctypes.c_int()
