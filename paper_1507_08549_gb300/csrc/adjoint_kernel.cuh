@@ -332,7 +332,7 @@ template <typename real, int NF>
 __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2 : 1)
     adj_line_kernel(AdjParams<real> P, int tiles_x) {
   using TL = ATile<real, NF>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
   real* sW = sm + TL::OFF_W;
   real* sP = sm + TL::OFF_P;
