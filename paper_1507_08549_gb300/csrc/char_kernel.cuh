@@ -20,7 +20,8 @@
 //
 // FP64: every operation the plain definition writes, in its order, rounded once (products by the 0 and 1
 // entries of R and L included), so D is reproducible bit for bit by a sequential implementation.
-// FP32: the same arithmetic with fused operations and the shared-smoothness WENO of the stage kernel.
+// FP32: fused operations, the shared-smoothness WENO of the stage kernel, and the projections written with
+// the zero, unit and repeated entries of L and R folded out.
 #pragma once
 #include "stage_kernel.cuh"
 
@@ -103,8 +104,12 @@ __device__ __forceinline__ bool char_face(const CharSmem<real>& S, int dir, int 
       {-ut, real(0), real(1), real(0)},
       {O::ml(real(0.5), O::sb(b2, O::ml(un, rcs))), O::ml(real(-0.5), O::sb(O::ml(b1, un), rcs)),
        O::ml(real(-0.5), O::ml(b1, ut)), O::ml(real(0.5), b1)}};
-  // projected split fluxes of the six stencil cells l-2 .. l+3
+  // projected split fluxes of the six stencil cells l-2 .. l+3. FP32 uses the structure of L:
+  // with K = f3 - u_n f1 - u_t f2, P = (b2 f0 + b1 K)/2 and Q = (u_n f0 - f1)/(2c),
+  //   w0 = P + Q, w1 = f0 - 2P, w2 = f2 - u_t f0, w3 = P - Q;
+  // FP64 keeps the plain matrix-vector products (bitwise against the oracle).
   real wp[4][6], wm[4][6];
+  const real hb1 = real(0.5) * b1, hb2 = real(0.5) * b2, hrc = real(0.5) * rcs;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const int rr = r + (k - 2) * dr, cc = c + (k - 2) * dc;
@@ -116,12 +121,26 @@ __device__ __forceinline__ bool char_face(const CharSmem<real>& S, int dir, int 
     real fp[4], fm[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) Ar<real>::split(Fr[q], Ur[q], alpha, fp[q], fm[q]);
+    if constexpr (sizeof(real) == 4) {
+      auto project = [&](const real (&f)[4], real (&w)[4][6]) {
+        const real K = f[3] - un * f[1] - ut * f[2];
+        const real P = hb2 * f[0] + hb1 * K;
+        const real Q = hrc * (un * f[0] - f[1]);
+        w[0][k] = P + Q;
+        w[1][k] = f[0] - real(2) * P;
+        w[2][k] = f[2] - ut * f[0];
+        w[3][k] = P - Q;
+      };
+      project(fp, wp);
+      project(fm, wm);
+    } else {
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      wp[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fp[0]), O::ml(Lm[w][1], fp[1])), O::ml(Lm[w][2], fp[2])),
-                       O::ml(Lm[w][3], fp[3]));
-      wm[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fm[0]), O::ml(Lm[w][1], fm[1])), O::ml(Lm[w][2], fm[2])),
-                       O::ml(Lm[w][3], fm[3]));
+      for (int w = 0; w < 4; ++w) {
+        wp[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fp[0]), O::ml(Lm[w][1], fp[1])), O::ml(Lm[w][2], fp[2])),
+                         O::ml(Lm[w][3], fp[3]));
+        wm[w][k] = O::ad(O::ad(O::ad(O::ml(Lm[w][0], fm[0]), O::ml(Lm[w][1], fm[1])), O::ml(Lm[w][2], fm[2])),
+                         O::ml(Lm[w][3], fm[3]));
+      }
     }
   }
   real wh[4];
@@ -129,15 +148,23 @@ __device__ __forceinline__ bool char_face(const CharSmem<real>& S, int dir, int 
   for (int w = 0; w < 4; ++w)
     wh[w] = O::ad(O::weno(wp[w][0], wp[w][1], wp[w][2], wp[w][3], wp[w][4]),
                   O::weno(wm[w][5], wm[w][4], wm[w][3], wm[w][2], wm[w][1]));
-  const real Rm[4][4] = {{real(1), real(1), real(0), real(1)},
-                         {O::sb(un, cs), un, real(0), O::ad(un, cs)},
-                         {ut, ut, real(1), ut},
-                         {O::sb(h, O::ml(un, cs)), O::ml(real(0.5), q2), ut, O::ad(h, O::ml(un, cs))}};
   real fr[4];
+  if constexpr (sizeof(real) == 4) {  // R w^ with R's structure: S = w0 + w3, D = w3 - w0
+    const real Sm = wh[0] + wh[3], Dd = wh[3] - wh[0];
+    fr[0] = Sm + wh[1];
+    fr[1] = un * fr[0] + cs * Dd;
+    fr[2] = ut * fr[0] + wh[2];
+    fr[3] = h * Sm + un * cs * Dd + real(0.5) * q2 * wh[1] + ut * wh[2];
+  } else {
+    const real Rm[4][4] = {{real(1), real(1), real(0), real(1)},
+                           {O::sb(un, cs), un, real(0), O::ad(un, cs)},
+                           {ut, ut, real(1), ut},
+                           {O::sb(h, O::ml(un, cs)), O::ml(real(0.5), q2), ut, O::ad(h, O::ml(un, cs))}};
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    fr[q] = O::ad(O::ad(O::ad(O::ml(Rm[q][0], wh[0]), O::ml(Rm[q][1], wh[1])), O::ml(Rm[q][2], wh[2])),
-                  O::ml(Rm[q][3], wh[3]));
+    for (int q = 0; q < 4; ++q)
+      fr[q] = O::ad(O::ad(O::ad(O::ml(Rm[q][0], wh[0]), O::ml(Rm[q][1], wh[1])), O::ml(Rm[q][2], wh[2])),
+                    O::ml(Rm[q][3], wh[3]));
+  }
   out[0] = fr[0];
   out[n] = fr[1];
   out[t] = fr[2];
