@@ -441,6 +441,19 @@ def run(args):
         reinit = {"ms": r0_.elapsed_time(r1_), "front_points": npts,
                   "pair_distances_per_s": npts * cells / (r0_.elapsed_time(r1_) * 1e-3)}
     h.close()
+    # measured FMA throughput: the cross-check of the derived arithmetic roofline
+    alu_probe = None
+    if args.workload == "blobs_blast_8192":
+        hp = hydro.Hydro(prob.with_(nx=64, ny=64, U0=prob.U0[:, :64, :64].copy()), dtype="f32")
+        f32 = hp.fma_probe("f32", 65536)
+        f64 = hp.fma_probe("f64", 2048)
+        hp.close()
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        alu_probe = {"fp32_fma_per_s": f32, "fp64_fma_per_s": f64,
+                     "fp32_derived_fma_per_s": sms * 128 * mhz * 1e6, "fp32_measured_over_derived":
+                     f32 / (sms * 128 * mhz * 1e6), "fp64_over_fp32": f64 / f32,
+                     "how": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (hydro_fma_probe)"}
     characteristic = None
     if args.workload == "blobs_blast_8192" and not char and not args.no_char:
         # the characteristic-wise scheme (Roe-averaged eigenvectors) on the same state, FP32
@@ -491,7 +504,7 @@ def run(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
                 "adjoint": adjoint, "fp64_step": fp64, "reinit": reinit,
-                "characteristic": characteristic, "poisson": poisson}
+                "characteristic": characteristic, "poisson": poisson, "alu_probe": alu_probe}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -143,6 +143,12 @@ int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dty
  * Allocates its point buffer (2 points per cell) on first use. Synchronises the stream. */
 int hydro_reinit(hydro_ctx* ctx, void* U, int* npoints);
 
+/* Measured fused multiply-add throughput of the context's GPU in dtype (HYDRO_F32 or HYDRO_F64): every
+ * thread of 8 x 256 threads per SM runs 8 independent FMA chains of 16 x iters FMAs; *fma_per_s receives
+ * FMAs per second (a flop rate is twice that). The cross-check of the arithmetic roofline. Allocates and
+ * frees 8 bytes; synchronises the stream. */
+int hydro_fma_probe(hydro_ctx* ctx, int dtype, int iters, double* fma_per_s);
+
 /* Self-test of the device failure path: one thread runs the stage kernel's bounded wait on an mbarrier
  * that nothing completes, for `polls` polls (1 .. 2^24; ~2^20 take a few milliseconds), and the call
  * returns what a lost tile copy returns: HYDRO_ETIMEOUT ("a device wait gave up"). No GPU state is left

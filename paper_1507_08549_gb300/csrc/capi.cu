@@ -1334,3 +1334,16 @@ int hydro_wait_selftest(hydro_ctx* c, unsigned polls) {
   c->launches++;
   return c->cfg.dtype == HYDRO_F64 ? read_status<double>(c, nullptr, nullptr) : read_status<float>(c, nullptr, nullptr);
 }
+
+// ---- arithmetic peak probe
+
+int hydro_fma_probe(hydro_ctx* c, int dtype, int iters, double* fma_per_s) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!fma_per_s || iters < 1 || (dtype != HYDRO_F32 && dtype != HYDRO_F64))
+    return fail(c, HYDRO_EINVAL, "bad probe arguments");
+  c->launches += 2;
+  if (dtype == HYDRO_F64) CK(run_fma_probe<double>(iters, c->stream, c->num_sms, fma_per_s));
+  else CK(run_fma_probe<float>(iters, c->stream, c->num_sms, fma_per_s));
+  return HYDRO_OK;
+}

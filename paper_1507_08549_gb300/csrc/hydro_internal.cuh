@@ -110,6 +110,10 @@ cudaError_t launch_totals(const real* U, int nx, int ny, int nfields, int geomet
 
 // Level-set reinitialisation (reinit_kernel.cuh): front points where phi changes sign between
 // neighbouring cells (linear interpolation), minimum distance of every cell to them, tanh blend.
+// Measured FMA throughput (FMAs per second) of the current device in precision real.
+template <typename real>
+cudaError_t run_fma_probe(int iters, cudaStream_t st, int num_sms, double* fma_per_s);
+
 // One bounded device wait that nothing completes (polls polls), reporting ERR_TIMEOUT into *err.
 cudaError_t launch_wait_selftest(unsigned polls, int* err, cudaStream_t s);
 

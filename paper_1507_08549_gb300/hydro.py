@@ -47,7 +47,7 @@ EXPORTS = [
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
-    "hydro_poisson", "hydro_exact_sum", "hydro_wait_selftest",
+    "hydro_poisson", "hydro_exact_sum", "hydro_wait_selftest", "hydro_fma_probe",
 ]
 
 _lock = threading.Lock()
@@ -106,6 +106,7 @@ def load(build_if_needed: bool = True):
                               ctypes.c_int),
             "hydro_exact_sum": ([ctxp, vp, ctypes.c_longlong, dp], ctypes.c_int),
             "hydro_wait_selftest": ([ctxp, ctypes.c_uint], ctypes.c_int),
+            "hydro_fma_probe": ([ctxp, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
             "conserved_totals_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, dp],
                                          ctypes.c_int),
@@ -302,6 +303,13 @@ class Hydro:
         """Run the bounded device wait on a barrier nothing completes (hydro_wait_selftest); returns the
         C return code (HYDRO_ETIMEOUT when the failure path works) without raising."""
         return int(self.lib.hydro_wait_selftest(self.ctx, int(polls)))
+
+    def fma_probe(self, dtype="f32", iters: int = 4096) -> float:
+        """Measured FMAs per second of this GPU in the given precision (hydro_fma_probe)."""
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.hydro_fma_probe(self.ctx, _dtype_code(dtype), int(iters), ctypes.byref(out)),
+                    "hydro_fma_probe")
+        return out.value
 
     def tile_variants(self):
         n, cur = ctypes.c_int(), ctypes.c_int()

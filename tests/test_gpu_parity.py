@@ -131,6 +131,29 @@ def test_config2_rayleigh_taylor_reduced_fp64_and_fp32(record_property):
     assert rel_l1(got32, ref, prob.gamma) <= F32_SHOCK
 
 
+def test_config2_fp32_error_growth_over_time(record_property):
+    """The Rayleigh-Taylor mixing is unstable: FP32 and FP64 runs part ways as the instability grows. The
+    FP64 GPU run stays bitwise the oracle's at every checkpoint; the FP32 error is recorded as it grows."""
+    prob = wl.rayleigh_taylor(128, 256, nsteps=1000)
+    hydro = _hydro()
+    h64, h32 = hydro.Hydro(prob, dtype="f64"), hydro.Hydro(prob, dtype="f32")
+    U64, U32 = h64.state(prob.U0), h32.state(prob.U0)
+    ref = prob.U0
+    done = 0
+    for upto in (40, 200, 1000):
+        n = upto - done
+        ref, _, _ = oracle.step(prob, ref, n)
+        h64.step(U64, n)
+        h32.step(U32, n)
+        done = upto
+        assert np.array_equal(U64.cpu().numpy(), ref)
+        err = rel_l1(U32.double().cpu().numpy(), ref, prob.gamma)
+        record_property(f"err:fp32_rel_l1_step{upto}", err)
+        assert np.isfinite(err) and err < 0.1
+    h64.close()
+    h32.close()
+
+
 def test_config2_rayleigh_taylor_full_size_first_steps():
     """Full 1024 x 2048 grid, the launch configuration the benchmark uses, 2 steps in FP64 against
     the oracle on the whole grid."""
