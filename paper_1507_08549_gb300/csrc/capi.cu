@@ -87,6 +87,9 @@ struct hydro_ctx {
   int ck_nsteps = -1, ck_every = 0;
   // characteristic scheme: padded D = dF/dx + dG/dy of the 4 hydro fields, written per stage
   void* char_div = nullptr;
+  // FP64 grids with fewer tiles than half the SMs: the same D, written per stage by a field-split launch
+  // of the stage kernel (4 CTAs per tile) so that more SMs share the FP64 line work
+  void* split_div = nullptr;
   // level-set reinitialisation: front points (x, y pairs) and their count
   void* front = nullptr;
   int* front_count = nullptr;
@@ -198,7 +201,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   base.dt_cur = &s->dt_cur;
   base.t_acc = &s->t_acc;
   base.err = &s->err;
-  base.ext_div = static_cast<const real*>(c->char_div);
+  base.ext_div = static_cast<const real*>(c->char_div ? c->char_div : c->split_div);
   real* A = bufp<real>(c, 0);
   real* B = bufp<real>(c, 1);
   real* C = bufp<real>(c, 2);
@@ -294,6 +297,10 @@ static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double
   }
   if (c->char_div) {  // characteristic scheme: the hydro divergence of this stage's input first
     CK(launch_char_div<real>(p, c->cfg.nx, c->cfg.ny, s));
+    c->launches++;
+  } else if (c->split_div) {  // field split: one CTA per (tile, hydro field) writes the divergence first
+    const StageCtl split{stage, 2, a, b};
+    CK(launch_stage<real>(c->variant, c->nf, p, nullptr, 4 * nwork, split, grid_for(c, 4 * nwork), s));
     c->launches++;
   }
   CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), s));
@@ -478,6 +485,12 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
     if (cudaMalloc(&c->char_div, db) != cudaSuccess) return bail(HYDRO_ECUDA);
     if (cudaMemsetAsync(c->char_div, 0, db, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   }
+  if (cfg->dtype == HYDRO_F64 && cfg->scheme == HYDRO_SCHEME_COMPONENT &&
+      (long long)c->tiles_x * ((cfg->ny + 14) / 15) * 2 < c->num_sms) {
+    const size_t db = (size_t)4 * c->fstride * c->esize;
+    if (cudaMalloc(&c->split_div, db) != cudaSuccess) return bail(HYDRO_ECUDA);
+    if (cudaMemsetAsync(c->split_div, 0, db, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
+  }
   const size_t sb = c->esize == 8 ? sizeof(Scratch<double>) : sizeof(Scratch<float>);
   if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
@@ -526,6 +539,7 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->front);
   cudaFree(c->front_count);
   cudaFree(c->char_div);
+  cudaFree(c->split_div);
   if (c->host_scratch) cudaFreeHost(c->host_scratch);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->done) cudaEventDestroy(c->done);
@@ -825,7 +839,10 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     for (int k = 0; k < n; ++k) {
       GridParams<real> p[7];
       build_params<real>(m[k], p);
-      for (int s = 0; s < 3; ++s) P[(size_t)s * n + k] = p[s];
+      for (int s = 0; s < 3; ++s) {
+        P[(size_t)s * n + k] = p[s];
+        P[(size_t)s * n + k].ext_div = nullptr;  // the batched launch computes every field itself
+      }
     }
     // interleave members so every CTA of the persistent launch sees a mix of grid sizes
     std::vector<int> ntile(n), next(n, 0);

@@ -73,7 +73,8 @@ struct GridParams {
 // Launch-wide stage control.
 struct StageCtl {
   int stage;      // 0, 1, 2
-  int mode;       // 0 RK stage, 1 write L (no blending, no reductions)
+  int mode;       // 0 RK stage, 1 write L (no blending, no reductions), 2 field split: work item w computes
+                  // dF/dx + dG/dy of hydro field w & 3 on tile w >> 2 into ext_div (FP64 grids with few tiles)
   double rk_a;    // out = a U^n + b (W + dt L)
   double rk_b;
 };

@@ -558,8 +558,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   if (warp == 0 && static_cast<int>(blockIdx.x) < nwork) {
     const int w0 = blockIdx.x;
     const int m0 = work ? work[w0].member : 0;
-    issue_box<real, NF, H>(members[m0], work ? work[w0].tile : w0, TY, sm + TL::OFF_U0, &bar[0], lane,
-                           TL::BOX_BYTES);
+    const int t0 = work ? work[w0].tile : ((sizeof(real) == 8 && ctl.mode == 2) ? w0 >> 2 : w0);
+    issue_box<real, NF, H>(members[m0], t0, TY, sm + TL::OFF_U0, &bar[0], lane, TL::BOX_BYTES);
   }
 
   unsigned parity[2] = {0u, 0u};
@@ -595,7 +595,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int b = it & 1;
     real* sU = sm + (b ? TL::OFF_U1 : TL::OFF_U0);
     const int member = work ? work[w].member : 0;
-    const int tile = work ? work[w].tile : w;
+    // mode 2 (field split, FP64 only): item w is field w & 3 of tile w >> 2
+    constexpr bool kSplit = sizeof(real) == 8;
+    const int tile = work ? work[w].tile : ((kSplit && ctl.mode == 2) ? w >> 2 : w);
+    const int split_field = (kSplit && ctl.mode == 2) ? (w & 3) : -1;
     if (member != cur_member) {
       if (cur_member >= 0) flush();
       __syncthreads();
@@ -615,7 +618,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int wn = w + gridDim.x;
     if (warp == 0 && wn < nwork) {
       const int mn = work ? work[wn].member : 0;
-      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : wn, TY, sm + (b ? TL::OFF_U0 : TL::OFF_U1),
+      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : wn), TY,
+                             sm + (b ? TL::OFF_U0 : TL::OFF_U1),
                              &bar[b ^ 1], lane, TL::BOX_BYTES);
     }
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
@@ -684,7 +688,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real alpha = xp ? ax : ay;
       const real rd = xp ? g.rdx : g.rdy;
       const double h = xp ? g.dx : g.dy;
-      for (int item = tid; item < NF * per_c; item += NT) {
+      const int item0 = split_field >= 0 ? split_field * per_c : 0;
+      const int item1 = split_field >= 0 ? item0 + per_c : NF * per_c;
+      for (int item = item0 + tid; item < item1; item += NT) {
         const int c = item / per_c;
         const int rem = item - c * per_c;
         int trow, tcol, brow, bcol;
@@ -704,7 +710,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         const int S = xp ? 1 : W;
         const int DS = xp ? 1 : TX;
         if (c < 4) {
-          if (g.ext_div) continue;  // characteristic scheme: the divergence comes from char_div_kernel
+          // the divergence comes from another launch (char_div_kernel, or mode 2 of this kernel)
+          if (g.ext_div && split_field < 0) continue;
           const int kind = (c == 0) ? 0 : (c == 3) ? 3 : ((c == 1) == xp) ? 1 : 2;
           const real* Uc = sU + (c * H + brow) * W + bcol;
           const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
@@ -726,7 +733,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     // with dV = dx dy (or 2 pi dr dz) applied once at the end
     double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     real totr[5] = {real(0), real(0), real(0), real(0), real(0)};
-    {
+    if (split_field >= 0) {  // field split: this CTA's field's dF/dx + dG/dy goes to the divergence buffer
+      real* D = const_cast<real*>(g.ext_div) + split_field * fs;
+      for (int idx = tid; idx < TY * TX; idx += NT) {
+        const int row = idx / TX, col = idx - row * TX;
+        const int i = x0 + col, j = y0 + row;
+        if (i < g.nx && j < g.ny)
+          D[static_cast<long long>(j + GY) * pitch + i + GX] = sD[(split_field * TY + row) * TX + col];
+      }
+    } else {
       const int nx = g.nx, ny = g.ny;
       const real gamma = g.gamma, grav = g.gravity, sf = g.flame_speed;
       const bool rz = g.geometry == 1;
