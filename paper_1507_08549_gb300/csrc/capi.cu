@@ -420,7 +420,6 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
     GridParams<real> last = all[2];
     last.out_dense = host_out;
     last.dense_fs = (long long)c->cfg.nx * c->cfg.ny;
-    last.dense_vec = (c->cfg.nx % 4 == 0 && reinterpret_cast<uintptr_t>(host_out) % 16 == 0) ? 1 : 0;
     CK(cudaMemcpyAsync(static_cast<GridParams<real>*>(c->params) + 7, &last, sizeof(last), cudaMemcpyHostToDevice,
                        c->stream));
     rc = launch_one<real>(c, 0, 0, 0, RK_A[0], RK_B[0], c->stream);

@@ -67,7 +67,6 @@ struct GridParams {
   const real* ext_div;    // characteristic scheme: D = dF/dx + dG/dy of the hydro fields (padded), else null
   real* out_dense;        // if set: write the output here instead, dense [NF][ny][nx] (host memory), no ghosts
   long long dense_fs;     // nx * ny
-  int dense_vec;          // out_dense rows are 16-byte aligned for 4-wide stores
 };
 
 // Launch-wide stage control.

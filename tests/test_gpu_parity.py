@@ -345,7 +345,7 @@ def test_frozen_replay_reproduces_the_run_and_host_entry():
                                                  ("f64", 37, 4, 0)])
 def test_pinned_host_entry_matches_device_steps(dt, n, nsteps, scheme):
     """Pinned host buffers are read by the pack kernel and written by the last stage directly over the
-    host link (4-wide stores when rows are 16-byte aligned, scalar otherwise): same bits, time and
+    host link: same bits, time and
     totals as the device entry point."""
     import torch
     hydro = _hydro()
