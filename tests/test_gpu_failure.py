@@ -1,4 +1,4 @@
-"""Failure paths on the GPU without a GPU fault: the device's bounded wait (the guard on every tile copy)
+"""Failure paths on the GPU without a GPU fault (and the arithmetic-peak probe): the device's bounded wait (the guard on every tile copy)
 run out on a barrier that nothing completes, and the host watchdog on a stream wait run out by a tiny
 limit. Both return HYDRO_ETIMEOUT and leave the context usable; nothing hangs or traps."""
 import os
@@ -64,3 +64,27 @@ def test_host_watchdog_times_out_and_recovers():
     assert np.array_equal(U.cpu().numpy(), ref.cpu().numpy())
     h.step(U, 1)  # and the context keeps working
     h.close()
+
+
+def test_fma_probe_measures_the_arithmetic_peaks():
+    """The measured FMA rates that cross-check the arithmetic roofline: FP32 within 20 % of 152 SMs x 128
+    lanes x clock (no more than that), FP64 far below FP32 on this part."""
+    import torch
+    hydro = _hydro()
+    prob = wl.advected_wave(32)
+    h = hydro.Hydro(prob, dtype="f32")
+    try:
+        f32 = h.fma_probe("f32", 16384)
+        f64 = h.fma_probe("f64", 256)
+    finally:
+        h.close()
+    props = torch.cuda.get_device_properties(0)
+    derived = props.multi_processor_count * 128 * 2.2e9  # above the maximum SM clock
+    assert 0.5 * derived < f32 <= derived
+    assert 0 < f64 < 0.1 * f32
+    with pytest.raises(hydro.HydroError):
+        h2 = hydro.Hydro(prob, dtype="f32")
+        try:
+            h2.fma_probe("f32", 0)
+        finally:
+            h2.close()
