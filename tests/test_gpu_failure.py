@@ -1,6 +1,7 @@
-"""Failure paths on the GPU without a GPU fault (and the arithmetic-peak probe): the device's bounded wait (the guard on every tile copy)
+"""Failure paths on the GPU without a GPU fault: the device's bounded wait (the guard on every tile copy)
 run out on a barrier that nothing completes, and the host watchdog on a stream wait run out by a tiny
-limit. Both return HYDRO_ETIMEOUT and leave the context usable; nothing hangs or traps."""
+limit. Both return HYDRO_ETIMEOUT and leave the context usable; nothing hangs or traps. Also the
+arithmetic-peak probe that cross-checks the ALU roofline."""
 import os
 import time
 
