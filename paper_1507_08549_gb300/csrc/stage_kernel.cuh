@@ -591,29 +591,23 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   int it = 0;
   // Reductions of the outputs (next stage's alpha, next step's dt, FP64 totals) accumulate per warp in
   // red[warp * 8 + slot] across this CTA's tiles of one member (each tile: a warp shuffle, lane 0
-  // updates its slots) and are flushed -- one block combine and one atomic per slot -- when the member
-  // changes and at the end, instead of a block reduction with two barriers per tile.
-  auto flush = [&]() {
-    if (ctl.mode != 0) return;
-    __syncthreads();
-    if (tid < 8) {
-      double acc = 0.0;
-      for (int wi = 0; wi < NWARPS; ++wi) {
-        const double v = red[wi * 8 + tid];
-        acc = (tid < 3) ? fmax(acc, v) : acc + v;
-      }
-      if (tid == 0 && g.alpha_out) T::atomic_max(&g.alpha_out[0], static_cast<real>(acc));
-      if (tid == 1 && g.alpha_out) T::atomic_max(&g.alpha_out[1], static_cast<real>(acc));
-      if (tid == 2 && ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(acc));
-      if (tid >= 3 && tid < 3 + NF && g.totals) {
-        if constexpr (sizeof(real) == 4)  // the cell volume, applied once
-          acc *= g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
-        atomicAdd(&g.totals[tid - 3], acc);
-      }
+  // updates its slots) and are flushed by each warp's lane 0 -- one atomic per slot, no barrier -- when
+  // the member changes (batched launches change member almost every tile) and at the end.
+  auto flush = [&]() {  // per warp: lane 0 folds its own slots into the member's slots, then clears them
+    if (ctl.mode != 0 || lane != 0) return;
+    double* r = red + warp * 8;
+    if (g.alpha_out) {
+      T::atomic_max(&g.alpha_out[0], static_cast<real>(r[0]));
+      T::atomic_max(&g.alpha_out[1], static_cast<real>(r[1]));
     }
-    __syncthreads();
-    for (int k = tid; k < TL::RED_DOUBLES; k += NT) red[k] = 0.0;
-    __syncthreads();
+    if (ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(r[2]));
+    if (g.totals) {
+      double vol = 1.0;
+      if constexpr (sizeof(real) == 4)  // the cell volume, applied once
+        vol = g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
+      for (int f = 0; f < NF; ++f) atomicAdd(&g.totals[f], r[3 + f] * vol);
+    }
+    for (int k = 0; k < 8; ++k) r[k] = 0.0;
   };
   for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++it) {
     const int b = it & 1;
