@@ -197,18 +197,21 @@ def run_reference(args):
 
 
 # Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
-# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 641.4, 987.2 and 970.4 MB
+# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 644.9, 987.7 and 969.8 MB
 # for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
 # a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (641.4e6 + 987.2e6 + 970.4e6) / 3.0 / (4096 * 4096)
+TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (644.92e6 + 987.74e6 + 969.77e6) / 3.0 / (4096 * 4096)
 
-# FP32 arithmetic operations the stage performs per cell (one per rounded operation of the method, a
-# fused multiply-add counted once), from the kernel's arithmetic with its sharing in place: a WENO5
-# reconstruction 23, a point's split flux and smoothness data 22.9, per 15-cell line 1271 ops for a
-# hydro component (84.7 per cell, 8 lines per cell) and 928 for the level set (61.9 per cell, 2 lines);
-# primitives 12.3 per cell (halo included); the cell phase 61 with the level-set Hamiltonian, 40 without.
+# FP32 arithmetic operations the stage performs per cell (one per rounded operation, a fused multiply-add
+# counted once), from the kernel's arithmetic with its sharing in place and the line halos included. A
+# 15-cell hydro line (one component, one direction): 21 points x 5 (flux 3, split 2), 36 point triplets
+# x 23 (smoothness data, weights and candidate values of one reconstruction direction), 16 faces x 15
+# (two weighted sums of 7 and their sum), 15 differences x 2, and the y pass's accumulation (7.5 per
+# line on average): 1210.5 ops, 80.7 per cell, 8 lines per cell. A level-set line: 20 differences x 2,
+# 18 triplets x 25 (shared by both one-sided derivatives), 15 cells x 14: 700 ops, 46.7 per cell, 2 lines.
+# Primitives 12.3 per cell (halo included); the cell phase 61 with the level-set Hamiltonian, 40 without.
 def alg_ops_per_cell_stage(F):
-    return 8 * 84.7 + 12.3 + (2 * 61.9 + 61.0 if F == 5 else 40.0)
+    return 8 * 80.7 + 12.3 + (2 * 46.7 + 61.0 if F == 5 else 40.0)
 
 
 def roofline(F, B, cells, avg_launch_ms, sm_mhz=None, alu=False, traffic=None):

@@ -80,7 +80,7 @@ __device__ __forceinline__ void weno5_grad_acc(real a, real b, real c, real d, r
 
 template <typename real>
 __device__ __forceinline__ real weno5_plain(real a, real b, real c, real d, real e) {
-  if constexpr (sizeof(real) == 4) {  // the stage kernel's FP32 form (shared-smoothness WENO)
+  if constexpr (sizeof(real) == 4) {  // FP32: shared smoothness data (the stage kernel's weights up to rounding)
     return weno_side(a, b, c, d, e, betas(a, b, c).m, betas(b, c, d).t, betas(c, d, e).p);
   } else {
     const real q0 = (real(2) * a - real(7) * b + real(11) * c) / real(6);

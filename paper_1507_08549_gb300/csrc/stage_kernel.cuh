@@ -158,6 +158,71 @@ __device__ __forceinline__ real weno_side(real a, real b, real c, real d, real e
   return num * T::rcp(den);
 }
 
+// FP32 line form: everything a face needs from one point triplet (L, C, R), formed once per triplet.
+// With s = (L + R) - 2C and t = L - R (array order), the three candidate values a triplet serves are
+//   C + 13/12 s -+ 3/4 t (as the upwind-most stencil: - from the left, + from the right),
+//   C + s/12 - t/4 and C + s/12 + t/4 (the central and the downwind-most stencils),
+// and its three smoothness indicators eps + beta are 13/12 s^2 + {(s - t/2)^2, (t/2)^2, (s + t/2)^2}
+// (the Jiang-Shu beta_0, beta_1, beta_2 in these variables). All three indicators of a face are scaled by
+// 12/13 (the weights only see their ratios), which removes the 13/12 multiply: D = s^2 + (12/13)(...)^2
+// + (12/13) eps, with u = sqrt(12/13) t/2. Each role carries its reciprocal weight already multiplied by
+// the linear weight (1, 6, 3 for the upwind-most, central and downwind-most stencil).
+struct Role32 {
+  float q, w;  // candidate value, d_k / D_k^2 (up to a factor common to the face)
+};
+struct Tri32 {
+  Role32 up, mid, down;  // the triplet as the upwind-most, central, downwind-most stencil of a face
+};
+
+constexpr float TRI_KS = 0.96076892283052284f;  // sqrt(12/13)
+constexpr float TRI_KU = 0.48038446141526142f;  // sqrt(12/13) / 2
+constexpr float TRI_KQ = 0.52041649986653958f;  // sqrt(13/12) / 2: t/4 = KQ u
+constexpr float TRI_EPS_SCALE = 12.0f / 13.0f;
+
+// Smoothness data of a triplet, shared by both reconstruction directions.
+struct TriD32 {
+  float s, u, base, rm, rt6, rp;  // rm = 1/Dm^2, rt6 = 6/Dt^2, rp = 1/Dp^2
+};
+__device__ __forceinline__ TriD32 tri_data(float L, float C, float R, float eps_scaled) {
+  using T = RT<float>;
+  TriD32 d;
+  d.s = T::fma_(-2.0f, C, L + R);
+  d.u = T::mul_(TRI_KU, L - R);
+  const float bs = T::fma_(d.s, d.s, eps_scaled);
+  const float mm = T::fma_(TRI_KS, d.s, -d.u), pp = T::fma_(TRI_KS, d.s, d.u);
+  const float Dm = T::fma_(mm, mm, bs), Dt = T::fma_(d.u, d.u, bs), Dp = T::fma_(pp, pp, bs);
+  d.rm = T::rcp(T::mul_(Dm, Dm));
+  d.rt6 = T::mul_(6.0f, T::rcp(T::mul_(Dt, Dt)));
+  d.rp = T::rcp(T::mul_(Dp, Dp));
+  d.base = T::fma_(1.0f / 12.0f, d.s, C);
+  return d;
+}
+// The triplet's roles for the reconstruction from the left (left_to_right) or from the right. Mirroring
+// the triplet keeps s, negates u and swaps Dm and Dp, so the two directions are mirror images bit for bit.
+__device__ __forceinline__ Tri32 tri_roles(const TriD32& d, bool left_to_right) {
+  using T = RT<float>;
+  const float lo = T::fma_(-TRI_KQ, d.u, d.base), hi = T::fma_(TRI_KQ, d.u, d.base);
+  const float bss = T::add_(d.base, d.s);
+  Tri32 r;
+  r.mid = {left_to_right ? lo : hi, d.rt6};
+  if (left_to_right) {
+    r.up = {T::fma_(-3.0f * TRI_KQ, d.u, bss), d.rm};
+    r.down = {hi, T::mul_(3.0f, d.rp)};
+  } else {
+    r.up = {T::fma_(3.0f * TRI_KQ, d.u, bss), d.rp};
+    r.down = {lo, T::mul_(3.0f, d.rm)};
+  }
+  return r;
+}
+// One face value from the upwind-most, central and downwind-most roles (the same expression for both
+// directions, so mirrored data give mirrored values).
+__device__ __forceinline__ float tri_face(const Role32& a, const Role32& b, const Role32& c) {
+  using T = RT<float>;
+  const float num = T::fma_(c.w, c.q, T::fma_(b.w, b.q, T::mul_(a.w, a.q)));
+  const float den = T::add_(T::add_(a.w, b.w), c.w);
+  return T::mul_(num, T::rcp(den));
+}
+
 // ------------------------------------------------------------------------------ arithmetic policy
 //
 // FP32 (the throughput path): fused multiply-adds, approximate reciprocals, smoothness indicators
@@ -171,7 +236,6 @@ struct Ar;
 
 template <>
 struct Ar<float> {
-  static constexpr bool kExact = false;
   using T = RT<float>;
   static __device__ __forceinline__ void prims(float rho, float mx, float my, float E, float gm1, float& u,
                                                float& v, float& p) {
@@ -237,7 +301,6 @@ struct Ar<float> {
 
 template <>
 struct Ar<double> {
-  static constexpr bool kExact = true;
   static __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
@@ -322,43 +385,71 @@ struct Ar<double> {
 // of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1, where
 // fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). Strides are runtime
 // values so the x and y passes run the same instructions.
-template <typename real, int K>
-__device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const real* __restrict__ Xc,
-                                           const real* __restrict__ vel, const real* __restrict__ pr, int S,
-                                           int VS, int kind, real alpha, real rd, double h,
-                                           real* __restrict__ dst, int DS, bool accumulate) {
-  using A = Ar<real>;
-  real fp[K + 6], fm[K + 6];
-  B3<real> bp[K + 6], bm[K + 6];
-  real fh_prev = real(0);
+//
+// FP32 works on g+- = F +- alpha U = 2 f+- (the 1/2 goes into the final difference; eps scales by 4 with
+// the squared differences, so the weights are those of f+-) through the triplet form above, and forms
+// every flux kind as (U + c_E p) v_n + c_A p (c_E = 1 for energy, c_A = 1 for the normal momentum; the
+// mass flux is rho v_n), so the line has no flux-kind branches.
+template <int K>
+__device__ __forceinline__ void hydro_line_tri(const float* __restrict__ Uc, const float* __restrict__ vel,
+                                               const float* __restrict__ pr, int S, int VS, int kind, float alpha,
+                                               float rd, float* __restrict__ dst, int DS, bool accumulate) {
+  using T = RT<float>;
+  constexpr float EPS = 4e-6f * TRI_EPS_SCALE;
+  const float rdh = T::mul_(0.5f, rd);
+  const float cE = kind == 3 ? 1.0f : 0.0f, cA = kind == 1 ? 1.0f : 0.0f;
+  float gp[K + 6], gm[K + 6];
+  Tri32 tp[K + 6], tm[K + 6];
+  float fh_prev = 0.0f;
 #pragma unroll
   for (int m = 0; m < K + 6; ++m) {
-    const real uu = Uc[m * S];
-    const real F = kind == 0 ? A::flux(0, uu, Xc[m * S], real(0), real(0))
-                             : A::flux(kind, uu, real(0), vel[m * VS], pr[m * S]);
-    A::split(F, uu, alpha, fp[m], fm[m]);
-    if constexpr (!A::kExact) {
-      if (m >= 2) {
-        const int j = m - 1;
-        if (j <= K + 3) bp[j] = betas(fp[j - 1], fp[j], fp[j + 1]);
-        if (j >= 2) bm[j] = betas(fm[j - 1], fm[j], fm[j + 1]);
-      }
+    const float uu = Uc[m * S];
+    const float pq = pr[m * S];
+    const float F = T::fma_(T::fma_(cE, pq, uu), vel[m * VS], T::mul_(cA, pq));
+    gp[m] = T::fma_(alpha, uu, F);
+    gm[m] = T::fma_(-alpha, uu, F);
+    if (m >= 2) {
+      const int j = m - 1;
+      if (j <= K + 3) tp[j] = tri_roles(tri_data(gp[j - 1], gp[j], gp[j + 1], EPS), true);
+      if (j >= 2) tm[j] = tri_roles(tri_data(gm[j - 1], gm[j], gm[j + 1], EPS), false);
     }
     if (m >= 5) {
-      const int f = m - 5;
-      real plus, minus;
-      if constexpr (A::kExact) {
-        plus = A::weno5(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4]);
-        minus = A::weno5(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1]);
-      } else {
-        plus = weno_side(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4], bp[f + 1].m, bp[f + 2].t, bp[f + 3].p);
-        minus = weno_side(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1], bm[f + 4].p, bm[f + 3].t,
-                          bm[f + 2].m);
-      }
-      const real fh = A::sum(plus, minus);
+      const int f = m - 5;  // face f: the left face of run cell f
+      const float plus = tri_face(tp[f + 1].up, tp[f + 2].mid, tp[f + 3].down);
+      const float minus = tri_face(tm[f + 4].up, tm[f + 3].mid, tm[f + 2].down);
+      const float fh = T::add_(plus, minus);
       if (f >= 1) {
-        const real d = A::divided(fh, fh_prev, rd, h);
-        real* o = dst + (f - 1) * DS;
+        const float d = T::mul_(fh - fh_prev, rdh);
+        float* o = dst + (f - 1) * DS;
+        *o = accumulate ? T::add_(*o, d) : d;
+      }
+      fh_prev = fh;
+    }
+  }
+}
+
+// FP64: the textbook WENO5 per face side, in the plain definition's order.
+template <int K>
+__device__ __forceinline__ void hydro_line_f64(const double* __restrict__ Uc, const double* __restrict__ Xc,
+                                               const double* __restrict__ vel, const double* __restrict__ pr, int S,
+                                               int VS, int kind, double alpha, double h, double* __restrict__ dst,
+                                               int DS, bool accumulate) {
+  using A = Ar<double>;
+  double fp[K + 6], fm[K + 6];
+  double fh_prev = 0.0;
+#pragma unroll
+  for (int m = 0; m < K + 6; ++m) {
+    const double uu = Uc[m * S];
+    const double F = kind == 0 ? A::flux(0, uu, Xc[m * S], 0.0, 0.0) : A::flux(kind, uu, 0.0, vel[m * VS], pr[m * S]);
+    A::split(F, uu, alpha, fp[m], fm[m]);
+    if (m >= 5) {
+      const int f = m - 5;
+      const double plus = A::weno5(fp[f], fp[f + 1], fp[f + 2], fp[f + 3], fp[f + 4]);
+      const double minus = A::weno5(fm[f + 5], fm[f + 4], fm[f + 3], fm[f + 2], fm[f + 1]);
+      const double fh = A::sum(plus, minus);
+      if (f >= 1) {
+        const double d = A::divided(fh, fh_prev, 0.0, h);
+        double* o = dst + (f - 1) * DS;
         *o = accumulate ? A::sum(*o, d) : d;
       }
       fh_prev = fh;
@@ -368,34 +459,49 @@ __device__ __forceinline__ void hydro_line(const real* __restrict__ Uc, const re
 
 // One-sided HJ-WENO5 derivatives (Jiang & Peng 2000) of phi along a line of K cells from points
 // m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
-// phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}), stored to om[k*DS], op[k*DS].
-template <typename real, int K>
-__device__ __forceinline__ void phi_line(const real* __restrict__ ph, int S, real rd, double h,
-                                         real* __restrict__ om, real* __restrict__ op, int DS) {
-  using A = Ar<real>;
-  real d[K + 5];
-  B3<real> b[K + 5];
-  real prev = ph[0];
+// phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}), stored to om[k*DS], op[k*DS]. FP32 forms
+// each difference triplet's smoothness data once for both derivatives.
+template <int K>
+__device__ __forceinline__ void phi_line_tri(const float* __restrict__ ph, int S, float rd, float* __restrict__ om,
+                                             float* __restrict__ op, int DS) {
+  constexpr float EPS = 1e-6f * TRI_EPS_SCALE;
+  float d[K + 5];
+  Tri32 tl[K + 5], tr[K + 5];
+  float prev = ph[0];
 #pragma unroll
   for (int n = 0; n < K + 5; ++n) {
-    const real nxt = ph[(n + 1) * S];
-    d[n] = A::divided(nxt, prev, rd, h);
+    const float nxt = ph[(n + 1) * S];
+    d[n] = RT<float>::mul_(nxt - prev, rd);
     prev = nxt;
-    if constexpr (!A::kExact) {
-      if (n >= 2) b[n - 1] = betas(d[n - 2], d[n - 1], d[n]);
+    if (n >= 2) {
+      const int j = n - 1;
+      const TriD32 td = tri_data(d[j - 1], d[j], d[j + 1], EPS);  // shared by both one-sided derivatives
+      tl[j] = tri_roles(td, true);
+      tr[j] = tri_roles(td, false);
     }
     if (n >= 5) {
       const int k = n - 5;
-      real dm, dp;
-      if constexpr (A::kExact) {
-        dm = A::weno5(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4]);
-        dp = A::weno5(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1]);
-      } else {
-        dm = weno_side(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4], b[k + 1].m, b[k + 2].t, b[k + 3].p);
-        dp = weno_side(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1], b[k + 4].p, b[k + 3].t, b[k + 2].m);
-      }
-      om[k * DS] = dm;
-      op[k * DS] = dp;
+      om[k * DS] = tri_face(tl[k + 1].up, tl[k + 2].mid, tl[k + 3].down);
+      op[k * DS] = tri_face(tr[k + 4].up, tr[k + 3].mid, tr[k + 2].down);
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void phi_line_f64(const double* __restrict__ ph, int S, double h, double* __restrict__ om,
+                                             double* __restrict__ op, int DS) {
+  using A = Ar<double>;
+  double d[K + 5];
+  double prev = ph[0];
+#pragma unroll
+  for (int n = 0; n < K + 5; ++n) {
+    const double nxt = ph[(n + 1) * S];
+    d[n] = A::divided(nxt, prev, 0.0, h);
+    prev = nxt;
+    if (n >= 5) {
+      const int k = n - 5;
+      om[k * DS] = A::weno5(d[k], d[k + 1], d[k + 2], d[k + 3], d[k + 4]);
+      op[k * DS] = A::weno5(d[k + 5], d[k + 4], d[k + 3], d[k + 2], d[k + 1]);
     }
   }
 }
@@ -517,9 +623,11 @@ struct Tile {
   static constexpr int OFF_D = OFF_PP + H * W;          // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
   static constexpr int OFF_X = OFF_D + NF * TY * TX;    // [4][TY][TX]  phi_x^-, phi_x^+, phi_y^-, phi_y^+
   static constexpr int ELEMS = OFF_X + (NF == 5 ? 4 * TY * TX : 0);
-  static constexpr int RED_DOUBLES = 20 * 8;            // per-warp partials (<= 20 warps x 8)
+  // per-warp running slots (<= 20 warps): 3 maxima and 5 totals; FP32 adds 5 compensation terms (16 floats)
+  static constexpr int RED_STRIDE = sizeof(real) == 4 ? 16 : 8;
+  static constexpr int RED_ELEMS = 20 * RED_STRIDE;
   static constexpr size_t RED_OFF = ((ELEMS * sizeof(real) + 15) / 16) * 16;
-  static constexpr size_t BYTES = RED_OFF + RED_DOUBLES * sizeof(double) + 32;
+  static constexpr size_t BYTES = RED_OFF + RED_ELEMS * sizeof(real) + 32;
   static constexpr unsigned BOX_BYTES = BOX * sizeof(real);
   static_assert(TX % RUN == 0 && TY % RUN == 0, "tiles are whole runs");
   static_assert(TX % EG == 0, "tile rows are whole cell groups");
@@ -557,8 +665,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   real* sp = sm + TL::OFF_PP;
   real* sD = sm + TL::OFF_D;
   real* sX = sm + TL::OFF_X;
-  double* red = reinterpret_cast<double*>(smem_raw + TL::RED_OFF);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_DOUBLES);  // two barriers, one per box buffer
+  real* red = reinterpret_cast<real*>(smem_raw + TL::RED_OFF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_ELEMS);  // two barriers, one per box buffer
   __shared__ GridParams<real> g;
   __shared__ int s_abort;
   // stage scalars, formed once per CTA and member (dt needs an FP64 division at stage 0; the FP64 pipe
@@ -575,7 +683,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     mbar_init(&bar[1], 1);
     s_abort = 0;
   }
-  for (int k = tid; k < TL::RED_DOUBLES; k += NT) red[k] = 0.0;
+  for (int k = tid; k < TL::RED_ELEMS; k += NT) red[k] = real(0);
   __syncthreads();
 
   // prologue: the first work item's box
@@ -589,25 +697,30 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   unsigned parity[2] = {0u, 0u};
   int cur_member = -1;
   int it = 0;
-  // Reductions of the outputs (next stage's alpha, next step's dt, FP64 totals) accumulate per warp in
-  // red[warp * 8 + slot] across this CTA's tiles of one member (each tile: a warp shuffle, lane 0
+  // Reductions of the outputs (next stage's alpha, next step's dt, totals) accumulate per warp in
+  // red[warp * RED_STRIDE + slot] across this CTA's tiles of one member (each tile: a warp shuffle, lane 0
   // updates its slots) and are flushed by each warp's lane 0 -- one atomic per slot, no barrier -- when
-  // the member changes (batched launches change member almost every tile) and at the end.
+  // the member changes (batched launches change member almost every tile) and at the end. The FP32
+  // kernel keeps its slots in FP32 (maxima are exact; each total is a compensated sum, value + error
+  // term, as accurate as an FP64 running sum) so that its tile loop issues no FP64 instruction.
   auto flush = [&]() {  // per warp: lane 0 folds its own slots into the member's slots, then clears them
     if (ctl.mode != 0 || lane != 0) return;
-    double* r = red + warp * 8;
+    real* r = red + warp * TL::RED_STRIDE;
     if (g.alpha_out) {
-      T::atomic_max(&g.alpha_out[0], static_cast<real>(r[0]));
-      T::atomic_max(&g.alpha_out[1], static_cast<real>(r[1]));
+      T::atomic_max(&g.alpha_out[0], r[0]);
+      T::atomic_max(&g.alpha_out[1], r[1]);
     }
-    if (ctl.stage == 2) T::atomic_max(g.smax, static_cast<real>(r[2]));
+    if (ctl.stage == 2) T::atomic_max(g.smax, r[2]);
     if (g.totals) {
-      double vol = 1.0;
-      if constexpr (sizeof(real) == 4)  // the cell volume, applied once
-        vol = g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
-      for (int f = 0; f < NF; ++f) atomicAdd(&g.totals[f], r[3 + f] * vol);
+      if constexpr (sizeof(real) == 4) {  // the cell volume, applied once
+        const double vol = g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
+        for (int f = 0; f < NF; ++f)
+          atomicAdd(&g.totals[f], (static_cast<double>(r[3 + f]) + static_cast<double>(r[8 + f])) * vol);
+      } else {
+        for (int f = 0; f < NF; ++f) atomicAdd(&g.totals[f], r[3 + f]);
+      }
     }
-    for (int k = 0; k < 8; ++k) r[k] = 0.0;
+    for (int k = 0; k < TL::RED_STRIDE; ++k) r[k] = real(0);
   };
   for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++it) {
     const int b = it & 1;
@@ -734,11 +847,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const real* Uc = sU + (c * H + brow) * W + bcol;
           const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
           const real* vel = xp ? su + trow * W + bcol : sv + brow * TX + tcol;
-          hydro_line<real, K>(Uc, Xc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd, h,
+          if constexpr (sizeof(real) == 4)
+            hydro_line_tri<K>(Uc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd,
+                              sD + (c * TY + trow) * TX + tcol, DS, !xp);
+          else
+            hydro_line_f64<K>(Uc, Xc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, h,
                               sD + (c * TY + trow) * TX + tcol, DS, !xp);
         } else {
           real* om = sX + ((xp ? 0 : 2) * TY + trow) * TX + tcol;
-          phi_line<real, K>(sU + (4 * H + brow) * W + bcol, S, rd, h, om, om + TY * TX, DS);
+          if constexpr (sizeof(real) == 4)
+            phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
+          else
+            phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
         }
       }
       __syncthreads();
@@ -747,8 +867,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
     real amx = real(0), amy = real(0), smx = real(0);
     // totals: FP64 per cell in the FP64 kernel; the FP32 kernel sums U_f (times r in (r,z)) over a thread's
-    // cells and then over its warp in FP32, and the warp partials across the CTA, tiles and grid in FP64,
-    // with dV = dx dy (or 2 pi dr dz) applied once at the end
+    // cells and then over its warp in FP32, the warp partials over the CTA's tiles as compensated FP32
+    // sums and across the grid in FP64, with dV = dx dy (or 2 pi dr dz) applied once at the end
     double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     real totr[5] = {real(0), real(0), real(0), real(0), real(0)};
     if (split_field >= 0) {  // field split: this CTA's field's dF/dx + dG/dy goes to the divergence buffer
@@ -867,8 +987,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const real rho = o[0][e], mx = o[1][e], my = o[2][e], E = o[3][e];
           real p, sx, sy, sm;
           Ar<real>::speeds(rho, mx, my, E, gamma, gm1, p, sx, sy, sm);
-          bool ok = rho > real(0) && p > real(0) && T::finite(E) && T::finite(mx) && T::finite(my) &&
-                    T::finite(sm);
+          // a non-finite momentum or energy makes p NaN or -inf, or c (hence c + |u| + |v|) infinite
+          bool ok = rho > real(0) && p > real(0) && T::finite(sm);
           if (NF == 5) ok = ok && T::finite(o[NF - 1][e]);
           if (!ok) atomicOr(g.err, ERR_NONPHYSICAL);
           amx = fmax(amx, sx);
@@ -901,11 +1021,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       if (want_tot) {
         if constexpr (sizeof(real) == 4) {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
+          for (int f = 0; f < NF; ++f)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) totr[f] += __shfl_xor_sync(0xffffffffu, totr[f], o);
-            tot[f] = static_cast<double>(totr[f]);
-          }
         } else {
 #pragma unroll
           for (int f = 0; f < NF; ++f)
@@ -914,12 +1032,24 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
       }
       if (lane == 0) {
-        double* r = red + warp * 8;
-        r[0] = fmax(r[0], static_cast<double>(amx));
-        r[1] = fmax(r[1], static_cast<double>(amy));
-        r[2] = fmax(r[2], static_cast<double>(smx));
-        if (want_tot)
-          for (int f = 0; f < NF; ++f) r[3 + f] += tot[f];
+        real* r = red + warp * TL::RED_STRIDE;
+        r[0] = fmax(r[0], amx);
+        r[1] = fmax(r[1], amy);
+        r[2] = fmax(r[2], smx);
+        if (want_tot) {
+          if constexpr (sizeof(real) == 4) {
+            for (int f = 0; f < NF; ++f) {  // Knuth's two-sum: r[3+f] + r[8+f] holds the running total
+              const float a = r[3 + f], b = totr[f];
+              const float sum = __fadd_rn(a, b);
+              const float bb = __fsub_rn(sum, a);
+              const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+              r[3 + f] = sum;
+              r[8 + f] = __fadd_rn(r[8 + f], err);
+            }
+          } else {
+            for (int f = 0; f < NF; ++f) r[3 + f] += tot[f];
+          }
+        }
       }
     }
     // the next copy overwrites the box: everyone is done reading it (generic proxy) before TMA writes
