@@ -93,6 +93,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
+// Barrier over `count` threads (whole warps) at named barrier ID (1..15; 0 is __syncthreads').
+template <int ID>
+__device__ __forceinline__ void named_barrier_sync(int count) {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -812,6 +818,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     __syncthreads();
 
     // ---- C/D. x pass then y pass through the same line code: items (field, line, run of 15 cells)
+    // Items [c per_c, (c+1) per_c) of both passes carry field c. When every item has its own thread, the
+    // y pass of hydro field c (which adds to the rows of sD that field c's x pass wrote) only waits for
+    // the warps of field c (named barrier 1 + c), and the level set's two passes share no data at all.
+    constexpr bool kFieldSync = TL::XI_PER_C == TL::YI_PER_C && NF * TL::XI_PER_C <= NT && TL::XI_PER_C % 32 == 0;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       const bool xp = pass == 0;
@@ -861,7 +871,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
         }
       }
-      __syncthreads();
+      if (xp && kFieldSync && split_field < 0) {
+        const int cm = tid / TL::XI_PER_C;  // the field whose lines this thread carries in both passes
+        switch (cm) {  // warp-uniform
+          case 0: named_barrier_sync<1>(TL::XI_PER_C); break;
+          case 1: named_barrier_sync<2>(TL::XI_PER_C); break;
+          case 2: named_barrier_sync<3>(TL::XI_PER_C); break;
+          case 3: named_barrier_sync<4>(TL::XI_PER_C); break;
+          default: break;
+        }
+      } else {
+        __syncthreads();
+      }
     }
 
     // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
