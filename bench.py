@@ -197,10 +197,10 @@ def run_reference(args):
 
 
 # Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
-# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 644.9, 987.7 and 969.8 MB
+# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 643.0, 986.9 and 970.3 MB
 # for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
 # a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (644.92e6 + 987.74e6 + 969.77e6) / 3.0 / (4096 * 4096)
+TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (642.97e6 + 986.94e6 + 970.27e6) / 3.0 / (4096 * 4096)
 
 # FP32 arithmetic operations the stage performs per cell (one per rounded operation, a fused multiply-add
 # counted once), from the kernel's arithmetic with its sharing in place and the line halos included. A
