@@ -663,6 +663,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   using T = RT<real>;
   using TL = Tile<real, NF, TY>;
   constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ;
+  constexpr int DVEC = 16 / sizeof(real);  // elements per 16-byte chunk of a host output row
+  static_assert((TL::OFF_D * sizeof(real)) % 16 == 0 && (TL::OFF_X * sizeof(real)) % 16 == 0 &&
+                    (TY * TX * sizeof(real)) % 16 == 0 && (TX * sizeof(real)) % 16 == 0,
+                "16-byte aligned staging rows");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
@@ -907,6 +911,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real dt = s_dt;
       const real ra = s_ra, rb = s_rb;
       const bool use_un = ra != real(0) && ctl.mode == 0;
+      // host output in whole 16-byte rows: every row of the tile starts on a 16-byte boundary
+      const bool dense_vec = g.out_dense && nx % DVEC == 0 &&
+                             (reinterpret_cast<unsigned long long>(g.out_dense) & 15ull) == 0;
       constexpr int NG = TX / EG;
       for (int it2 = tid; it2 < TY * NG; it2 += NT) {
         const int row = it2 / NG, g4 = it2 - row * NG;
@@ -970,7 +977,14 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
         // stores: the padded working state, or (last stage of a host-buffer call) the caller's dense
         // state in host memory, written directly over the host link
-        if (g.out_dense) {
+        if (dense_vec) {  // staged in this thread's own (consumed) divergence slots, rows written below
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            real* st = (f < 4 ? sD + f * TY * TX : sX) + row * TX + tcol;
+#pragma unroll
+            for (int e = 0; e < EG; ++e) st[e] = o[f][e];
+          }
+        } else if (g.out_dense) {
           const long long hbase = static_cast<long long>(j) * nx + ib;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
@@ -1027,6 +1041,21 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             }
           }
         }
+      }
+    }
+
+    // the tile's host output, staged above, as 16-byte row chunks (full lines over the host link)
+    if (split_field < 0 && g.out_dense && g.nx % DVEC == 0 &&
+        (reinterpret_cast<unsigned long long>(g.out_dense) & 15ull) == 0) {
+      __syncthreads();
+      constexpr int NVR = TX / DVEC;
+      for (int idx = tid; idx < NF * TY * NVR; idx += NT) {
+        const int f = idx / (TY * NVR), rem = idx - f * (TY * NVR), row = rem / NVR, q = rem - row * NVR;
+        const int j = y0 + row, i = x0 + q * DVEC;
+        if (j >= g.ny || i >= g.nx) continue;
+        const real* st = (f < 4 ? sD + f * TY * TX : sX) + row * TX + q * DVEC;
+        *reinterpret_cast<uint4*>(g.out_dense + f * g.dense_fs + static_cast<long long>(j) * g.nx + i) =
+            *reinterpret_cast<const uint4*>(st);
       }
     }
 
