@@ -300,7 +300,14 @@ def run_gradient(args, prob, dtype, rank, world, barrier):
     h.forward_checkpointed(U, args.steps, 20)
     torch.cuda.synchronize()
     fwd = time.perf_counter() - t0
-    lam = torch.ones_like(U)
+    # cotangent of the configuration's objective J = sum (m_x^2 + m_y^2) / (2 rho) dx dy at the final state
+    rho, mx, my = U[0], U[1], U[2]
+    dA = prob.dx * prob.dy
+    lam = torch.zeros_like(U)
+    lam[0] = -0.5 * (mx * mx + my * my) / (rho * rho) * dA
+    lam[1] = mx / rho * dA
+    lam[2] = my / rho * dA
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     h.adjoint_sweep(lam)
     torch.cuda.synchronize()
@@ -322,6 +329,7 @@ def run(args):
     import torch
     import torch.distributed as dist
     from paper_1507_08549_gb300 import hydro
+    from paper_1507_08549_gb300 import workloads as wl
 
     rank, world = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -418,14 +426,18 @@ def run(args):
         h.step(U, 1)
         dtl, al = h.get_log(1)
         h.record(0)
-        lam = torch.ones_like(U)
-        h.adjoint_step(U, lam, float(dtl[0]), al[0].ravel())  # warm-up (allocates the adjoint buffers)
+        # a seeded non-constant cotangent (a constant one would zero every face adjoint in the first
+        # reversed stage and let the line adjoint skip its WENO gradients)
+        gen = torch.Generator(device=U.device).manual_seed(wl.DEFAULT_SEED)
+        lam = torch.rand(U.shape, generator=gen, device=U.device, dtype=U.dtype) * 2 - 1
+        h.adjoint_step(U, lam.clone(), float(dtl[0]), al[0].ravel())  # warm-up (allocates the adjoint buffers)
         torch.cuda.synchronize()
         ka = max(1, args.adjoint_steps)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        for _ in range(ka):
-            h.adjoint_step(U, lam, float(dtl[0]), al[0].ravel())
+        lam_k = [lam.clone() for _ in range(ka)]  # adjoint_step overwrites its cotangent in place
+        for k in range(ka):
+            h.adjoint_step(U, lam_k[k], float(dtl[0]), al[0].ravel())
         a1.record()
         torch.cuda.synchronize()
         adj_ms = a0.elapsed_time(a1) / ka

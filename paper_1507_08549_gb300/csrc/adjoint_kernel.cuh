@@ -229,7 +229,9 @@ constexpr int ATX = 32, ATY = 16, ARUN = 8;   // output points per tile, points 
 template <typename real, int NF>
 __host__ __device__ constexpr int adj_threads() { return sizeof(real) == 4 ? NF * 64 : 256; }
 constexpr int AHX = 6;                        // box halo (hydro needs 5, level set 6)
-constexpr int ABW = ATX + 2 * AHX, ABH = ATY + 2 * AHX;
+// box rows of odd length and output rows of ATX + 1: the 16 rows x 2 runs of an x-pass warp fall on 32
+// distinct banks (a warp's two runs are 16 columns apart), and so do the run outputs the lanes write
+constexpr int ABW = ATX + 2 * AHX + 1, ABH = ATY + 2 * AHX, AOS = ATX + 1;
 
 template <typename real, int NF>
 struct ATile {
@@ -238,12 +240,200 @@ struct ATile {
   static constexpr int OFF_P = OFF_W + NF * BOX;         // [3][ABH][ABW]  u, v, p
   static constexpr int OFF_N = OFF_P + 3 * BOX;          // [NF][ABH][ABW] nu
   static constexpr int OFF_H = OFF_N + NF * BOX;         // [4][ABH][ABW]  hb (level set)
-  static constexpr int OFF_PB = OFF_H + (NF == 5 ? 4 * BOX : 0);  // [4][ATY][ATX] f+bar + f-bar
-  static constexpr int OFF_MB = OFF_PB + 4 * ATY * ATX;  // [4][ATY][ATX] f+bar - f-bar
-  static constexpr int OFF_MU = OFF_MB + 4 * ATY * ATX;  // [NF][ATY][ATX] accumulated mu
-  static constexpr int ELEMS = OFF_MU + NF * ATY * ATX;
+  static constexpr int OFF_PB = OFF_H + (NF == 5 ? 4 * BOX : 0);  // [4][ATY][AOS] f+bar + f-bar
+  static constexpr int OFF_MB = OFF_PB + 4 * ATY * AOS;  // [4][ATY][AOS] f+bar - f-bar
+  static constexpr int OFF_MU = OFF_MB + 4 * ATY * AOS;  // [NF][ATY][AOS] accumulated mu
+  static constexpr int ELEMS = OFF_MU + NF * ATY * AOS;
   static constexpr size_t BYTES = ELEMS * sizeof(real);
 };
+
+// ---- FP32 line adjoints in triplet form. A point triplet (L, C, R) serves three faces of one
+// reconstruction direction, as their upwind-most, central and downwind-most stencil ("up", "mid", "dn").
+// With s = (L + R) - 2C, t = L - R and h_r the role's t_r / 2 (s - t/2, t/2, s + t/2 from the left; s + t/2,
+// -t/2, s - t/2 from the right), the role's candidate value is q_r, its indicator D_r = eps + 13/12 s^2
+// + h_r^2, its weight a_r = d_r / D_r^2 (linear weights 1, 6, 3) and n_r = a_r / D_r. These are formed
+// once per triplet. A face with cotangent gbar then needs W = sum a_r q_r / sum a_r and, per role,
+//   gbar dW/d(a', b', c') = WG dq_r + A (1, -2, 1) + B dt_r,
+//   WG = gbar a_r / sum a,  cg = -2 gbar (q_r - W) n_r / sum a,  A = 13/6 s cg,  B = h_r cg,
+// on the role's three points in reconstruction order, with dq_r = (2, -7, 11)/6, (-1, 5, 2)/6, (2, 5, -1)/6
+// and dt_r = (1, -4, 3), (1, 0, -1), (3, -4, 1) for up, mid, dn (Jiang & Shu's candidate values and
+// smoothness indicators differentiated).
+struct ARole {
+  float q, a, nr, h;
+};
+struct ATri {
+  ARole up, mid, dn;
+  float s13;  // 13/6 s
+};
+struct ATriData {
+  float s, th, mm, pp, rm, rt, rp, base;
+};
+__device__ __forceinline__ ATriData adj_tri_data(float L, float C, float R) {
+  using T = RT<float>;
+  ATriData d;
+  d.s = T::fma_(-2.0f, C, L + R);
+  d.th = 0.5f * (L - R);
+  const float bs = T::fma_((13.0f / 12.0f) * d.s, d.s, 1e-6f);
+  d.mm = d.s - d.th;
+  d.pp = d.s + d.th;
+  d.rm = T::rcp(T::fma_(d.mm, d.mm, bs));
+  d.rt = T::rcp(T::fma_(d.th, d.th, bs));
+  d.rp = T::rcp(T::fma_(d.pp, d.pp, bs));
+  d.base = T::fma_(1.0f / 12.0f, d.s, C);
+  return d;
+}
+__device__ __forceinline__ ATri adj_tri_roles(const ATriData& d, bool left_to_right) {
+  using T = RT<float>;
+  const float bss = d.base + d.s;
+  const float lo = T::fma_(-0.5f, d.th, d.base), hi = T::fma_(0.5f, d.th, d.base);
+  const float at = 6.0f * d.rt * d.rt;
+  ATri r;
+  r.s13 = (13.0f / 6.0f) * d.s;
+  if (left_to_right) {
+    r.up = {T::fma_(-1.5f, d.th, bss), d.rm * d.rm, 0.0f, d.mm};
+    r.up.nr = r.up.a * d.rm;
+    r.mid = {lo, at, at * d.rt, d.th};
+    r.dn = {hi, 3.0f * d.rp * d.rp, 0.0f, d.pp};
+    r.dn.nr = r.dn.a * d.rp;
+  } else {
+    r.up = {T::fma_(1.5f, d.th, bss), d.rp * d.rp, 0.0f, d.pp};
+    r.up.nr = r.up.a * d.rp;
+    r.mid = {hi, at, at * d.rt, -d.th};
+    r.dn = {lo, 3.0f * d.rm * d.rm, 0.0f, d.mm};
+    r.dn.nr = r.dn.a * d.rm;
+  }
+  return r;
+}
+// One role's share of a face's gradient onto its points (reconstruction order a', b', c').
+template <int ROLE>
+__device__ __forceinline__ void adj_role(const ARole& r, float s13, float W, float g, float m2g, float& ga,
+                                         float& gb, float& gc) {
+  using T = RT<float>;
+  constexpr float q0 = ROLE == 0 ? 2.0f / 6.0f : ROLE == 1 ? -1.0f / 6.0f : 2.0f / 6.0f;
+  constexpr float q1 = ROLE == 0 ? -7.0f / 6.0f : 5.0f / 6.0f;
+  constexpr float q2 = ROLE == 0 ? 11.0f / 6.0f : ROLE == 1 ? 2.0f / 6.0f : -1.0f / 6.0f;
+  constexpr float t0 = ROLE == 2 ? 3.0f : 1.0f;
+  constexpr float t1 = ROLE == 1 ? 0.0f : -4.0f;
+  constexpr float t2 = ROLE == 0 ? 3.0f : ROLE == 1 ? -1.0f : 1.0f;
+  const float WG = r.a * g;
+  const float cg = (r.q - W) * r.nr * m2g;
+  const float A = s13 * cg, B = r.h * cg;
+  ga += T::fma_(WG, q0, T::fma_(B, t0, A));
+  gb += (ROLE == 1) ? T::fma_(WG, q1, -2.0f * A) : T::fma_(WG, q1, T::fma_(B, t1, -2.0f * A));
+  gc += T::fma_(WG, q2, T::fma_(B, t2, A));
+}
+// A face's W from its three roles, and the gradient factors gbar / sum a and -2 gbar / sum a.
+__device__ __forceinline__ void adj_face_w(const ARole& u, const ARole& m, const ARole& d, float gbar, float& W,
+                                           float& g, float& m2g) {
+  using T = RT<float>;
+  const float rS = T::rcp((u.a + m.a) + d.a);
+  W = T::fma_(d.a, d.q, T::fma_(m.a, m.q, u.a * u.q)) * rS;
+  g = gbar * rS;
+  m2g = -2.0f * g;
+}
+
+// FP32 hydro line adjoint (same faces, points and outputs as adj_hydro_line below).
+__device__ __forceinline__ void adj_hydro_line_f32(const float* __restrict__ Uc, const float* __restrict__ Xc,
+                                                   const float* __restrict__ vel, const float* __restrict__ pr,
+                                                   const float* __restrict__ nuc, int S, int kind, float alpha,
+                                                   float rd, float* __restrict__ pb, float* __restrict__ mb, int DS) {
+  constexpr int NP = ARUN + 10;  // points, index m + 5
+  float fp[NP], fm[NP], ap[NP], am[NP];
+  ATri tp[NP], tm[NP];  // triplets by centre point
+  auto point = [&](int q) {
+    const int m = q - 5;
+    const float uu = Uc[m * S];
+    float F;
+    if (kind == 0) F = Xc[m * S];
+    else {
+      const float vn = vel[m * S], p = pr[m * S];
+      F = kind == 1 ? uu * vn + p : kind == 2 ? uu * vn : (uu + p) * vn;
+    }
+    fp[q] = 0.5f * (F + alpha * uu);
+    fm[q] = 0.5f * (F - alpha * uu);
+    ap[q] = 0.0f;
+    am[q] = 0.0f;
+  };
+#pragma unroll
+  for (int q = 0; q < 5; ++q) point(q);  // points -5 .. -1
+  tp[1] = adj_tri_roles(adj_tri_data(fp[0], fp[1], fp[2]), true);
+  tp[2] = adj_tri_roles(adj_tri_data(fp[1], fp[2], fp[3]), true);
+  tm[2] = adj_tri_roles(adj_tri_data(fm[1], fm[2], fm[3]), false);
+  tm[3] = adj_tri_roles(adj_tri_data(fm[2], fm[3], fm[4]), false);
+#pragma unroll
+  for (int f = -2; f <= ARUN + 2; ++f) {
+    // face f lies between points f-1 and f; its left-biased stencil is points f-3 .. f+1 (triplets centred
+    // at f-2, f-1, f) and its right-biased one f+2 .. f-2 (triplets centred at f+1, f, f-1)
+    const int q = f + 5;
+    if (q + 2 < NP) point(q + 2);
+    tp[q] = adj_tri_roles(adj_tri_data(fp[q - 1], fp[q], fp[q + 1]), true);
+    tm[q + 1] = adj_tri_roles(adj_tri_data(fm[q], fm[q + 1], fm[q + 2]), false);
+    const float fb = (nuc[f * S] - nuc[(f - 1) * S]) * rd;
+    if (fb != 0.0f) {
+      float W, g, m2g;
+      adj_face_w(tp[q - 2].up, tp[q - 1].mid, tp[q].dn, fb, W, g, m2g);
+      adj_role<0>(tp[q - 2].up, tp[q - 2].s13, W, g, m2g, ap[q - 3], ap[q - 2], ap[q - 1]);
+      adj_role<1>(tp[q - 1].mid, tp[q - 1].s13, W, g, m2g, ap[q - 2], ap[q - 1], ap[q]);
+      adj_role<2>(tp[q].dn, tp[q].s13, W, g, m2g, ap[q - 1], ap[q], ap[q + 1]);
+      adj_face_w(tm[q + 1].up, tm[q].mid, tm[q - 1].dn, fb, W, g, m2g);
+      adj_role<0>(tm[q + 1].up, tm[q + 1].s13, W, g, m2g, am[q + 2], am[q + 1], am[q]);
+      adj_role<1>(tm[q].mid, tm[q].s13, W, g, m2g, am[q + 1], am[q], am[q - 1]);
+      adj_role<2>(tm[q - 1].dn, tm[q - 1].s13, W, g, m2g, am[q], am[q - 1], am[q - 2]);
+    }
+    const int k = f - 3;  // output point completed by this face
+    if (k >= 0 && k < ARUN) {
+      pb[k * DS] = ap[k + 5] + am[k + 5];
+      mb[k * DS] = ap[k + 5] - am[k + 5];
+    }
+  }
+}
+
+// FP32 level-set line adjoint (same cells and outputs as adj_phi_line below): both one-sided
+// derivatives of a cell reconstruct the same differences, so each triplet's data serve both directions.
+__device__ __forceinline__ void adj_phi_line_f32(const float* __restrict__ ph, const float* __restrict__ hm,
+                                                 const float* __restrict__ hp, int S, float rd, float* __restrict__ dst,
+                                                 int DS) {
+  constexpr int ND = ARUN + 11;  // differences D_n, n = -6 .. ARUN+4, index n + 6
+  float D[ND], Db[ND];
+  ATri tl[ND], tr[ND];
+  auto diff = [&](int q) {
+    const int n = q - 6;
+    D[q] = (ph[(n + 1) * S] - ph[n * S]) * rd;
+    Db[q] = 0.0f;
+  };
+  auto tri = [&](int q) {
+    const ATriData d = adj_tri_data(D[q - 1], D[q], D[q + 1]);
+    tl[q] = adj_tri_roles(d, true);
+    tr[q] = adj_tri_roles(d, false);
+  };
+#pragma unroll
+  for (int q = 0; q < 5; ++q) diff(q);
+  tri(1);
+  tri(2);
+  tri(3);
+#pragma unroll
+  for (int i = -3; i <= ARUN + 2; ++i) {
+    const int q = i + 6;
+    if (q + 2 < ND) diff(q + 2);
+    if (q + 1 < ND - 1) tri(q + 1);
+    const float bm = hm[i * S], bp = hp[i * S];
+    float W, g, m2g;
+    if (bm != 0.0f) {
+      adj_face_w(tl[q - 2].up, tl[q - 1].mid, tl[q].dn, bm, W, g, m2g);
+      adj_role<0>(tl[q - 2].up, tl[q - 2].s13, W, g, m2g, Db[q - 3], Db[q - 2], Db[q - 1]);
+      adj_role<1>(tl[q - 1].mid, tl[q - 1].s13, W, g, m2g, Db[q - 2], Db[q - 1], Db[q]);
+      adj_role<2>(tl[q].dn, tl[q].s13, W, g, m2g, Db[q - 1], Db[q], Db[q + 1]);
+    }
+    if (bp != 0.0f) {
+      adj_face_w(tr[q + 1].up, tr[q].mid, tr[q - 1].dn, bp, W, g, m2g);
+      adj_role<0>(tr[q + 1].up, tr[q + 1].s13, W, g, m2g, Db[q + 2], Db[q + 1], Db[q]);
+      adj_role<1>(tr[q].mid, tr[q].s13, W, g, m2g, Db[q + 1], Db[q], Db[q - 1]);
+      adj_role<2>(tr[q - 1].dn, tr[q - 1].s13, W, g, m2g, Db[q], Db[q - 1], Db[q - 2]);
+    }
+    const int k = i - 3;  // output whose two differences are complete
+    if (k >= 0 && k < ARUN) dst[k * DS] += (Db[k - 1 + 6] - Db[k + 6]) * rd;
+  }
+}
 
 // One hydro line of ARUN output points: faces f = -2 .. ARUN+2 relative to the first output point,
 // points m = -5 .. ARUN+4. Writes (f+bar + f-bar) and (f+bar - f-bar) of the outputs. The faces advance
@@ -372,7 +562,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
     sP[1 * TL::BOX + idx] = v;
     sP[2 * TL::BOX + idx] = (gamma - real(1)) * (wv[3] - real(0.5) * (wv[1] * u + wv[2] * v));
   }
-  for (int idx = tid; idx < NF * ATY * ATX; idx += NT) sMU[idx] = real(0);
+  for (int idx = tid; idx < NF * ATY * AOS; idx += NT) sMU[idx] = real(0);
   __syncthreads();
 
 #pragma unroll 1
@@ -381,7 +571,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
     const real alpha = xp ? P.ax : P.ay;
     const real rd = static_cast<real>(1.0 / (xp ? P.dx : P.dy));
     const int S = xp ? 1 : ABW;
-    const int DS = xp ? 1 : ATX;
+    const int DS = xp ? 1 : AOS;
     // items: (field, line, run); x: ATY rows x 4 runs; y: ATX columns x 2 runs
     const int per_c = xp ? ATY * (ATX / ARUN) : ATX * (ATY / ARUN);
     for (int it = tid; it < NF * per_c; it += NT) {
@@ -389,7 +579,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
       int orow, ocol;  // first output point of the run, tile coordinates
       if (xp) {
         orow = rem % ATY;
-        ocol = (rem / ATY) * ARUN;
+        ocol = (((rem / ATY) & 1) * 2 + (rem / (2 * ATY))) * ARUN;  // a warp's two runs 16 columns apart
       } else {
         ocol = rem % ATX;
         orow = (rem / ATX) * ARUN;
@@ -397,13 +587,23 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
       const int bidx = (orow + AHX) * ABW + (ocol + AHX);
       if (c < 4) {
         const int kind = (c == 0) ? 0 : (c == 3) ? 3 : ((c == 1) == xp) ? 1 : 2;
-        adj_hydro_line<real>(sW + c * TL::BOX + bidx, sW + (xp ? 1 : 2) * TL::BOX + bidx,
+        if constexpr (sizeof(real) == 4)
+          adj_hydro_line_f32(sW + c * TL::BOX + bidx, sW + (xp ? 1 : 2) * TL::BOX + bidx,
                              sP + (xp ? 0 : 1) * TL::BOX + bidx, sP + 2 * TL::BOX + bidx, sN + c * TL::BOX + bidx, S,
-                             kind, alpha, rd, sPB + (c * ATY + orow) * ATX + ocol, sMB + (c * ATY + orow) * ATX + ocol,
+                             kind, alpha, rd, sPB + (c * ATY + orow) * AOS + ocol, sMB + (c * ATY + orow) * AOS + ocol,
                              DS);
+        else
+          adj_hydro_line<real>(sW + c * TL::BOX + bidx, sW + (xp ? 1 : 2) * TL::BOX + bidx,
+                               sP + (xp ? 0 : 1) * TL::BOX + bidx, sP + 2 * TL::BOX + bidx, sN + c * TL::BOX + bidx,
+                               S, kind, alpha, rd, sPB + (c * ATY + orow) * AOS + ocol,
+                               sMB + (c * ATY + orow) * AOS + ocol, DS);
       } else if constexpr (NF == 5) {
-        adj_phi_line<real>(sW + 4 * TL::BOX + bidx, sH + (xp ? 0 : 2) * TL::BOX + bidx,
-                                 sH + (xp ? 1 : 3) * TL::BOX + bidx, S, rd, sMU + (4 * ATY + orow) * ATX + ocol, DS);
+        if constexpr (sizeof(real) == 4)
+          adj_phi_line_f32(sW + 4 * TL::BOX + bidx, sH + (xp ? 0 : 2) * TL::BOX + bidx,
+                           sH + (xp ? 1 : 3) * TL::BOX + bidx, S, rd, sMU + (4 * ATY + orow) * AOS + ocol, DS);
+        else
+          adj_phi_line<real>(sW + 4 * TL::BOX + bidx, sH + (xp ? 0 : 2) * TL::BOX + bidx,
+                             sH + (xp ? 1 : 3) * TL::BOX + bidx, S, rd, sMU + (4 * ATY + orow) * AOS + ocol, DS);
       }
     }
     __syncthreads();
@@ -416,8 +616,8 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
       bool any = false;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        pb[r] = sPB[(r * ATY + orow) * ATX + ocol];
-        mb[r] = sMB[(r * ATY + orow) * ATX + ocol];
+        pb[r] = sPB[(r * ATY + orow) * AOS + ocol];
+        mb[r] = sMB[(r * ATY + orow) * AOS + ocol];
         any = any || pb[r] != real(0) || mb[r] != real(0);
       }
       if (!any) continue;  // also skips unfilled corner points
@@ -428,7 +628,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
         real acc = real(0.5) * alpha * mb[s];
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc += real(0.5) * J[r][s] * pb[r];
-        sMU[(s * ATY + orow) * ATX + ocol] += acc;
+        sMU[(s * ATY + orow) * AOS + ocol] += acc;
       }
     }
     __syncthreads();
@@ -444,7 +644,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
     const long long k = static_cast<long long>(gr) * P.pitch + gc;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const real v = sMU[(f * ATY + orow) * ATX + ocol];
+      const real v = sMU[(f * ATY + orow) * AOS + ocol];
       P.mu[f * fs + k] = (ix && iy) ? P.mu[f * fs + k] + v : v;
     }
   }
