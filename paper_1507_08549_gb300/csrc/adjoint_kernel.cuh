@@ -149,6 +149,22 @@ struct AdjParams {
 
 // ---------------------------------------------------------------------------- point terms
 
+// FP32 one-sided derivatives of one cell from its six differences d[0..5] (d[3] is the cell's right
+// difference): phi^- = W(d0 .. d4), phi^+ = W(d5 .. d1), the four difference triplets formed once.
+__device__ __forceinline__ void phi_derivs_f32(const float (&d)[6], float& dm, float& dp) {
+  constexpr float EPS = 1e-6f * TRI_EPS_SCALE;
+  TriD32 t[5];
+  Tri32 l[5], r[5];
+#pragma unroll
+  for (int j = 1; j <= 4; ++j) {
+    t[j] = tri_data(d[j - 1], d[j], d[j + 1], EPS);
+    l[j] = tri_roles(t[j], true);
+    r[j] = tri_roles(t[j], false);
+  }
+  dm = tri_face(l[1].up, l[2].mid, l[3].down);
+  dp = tri_face(r[4].up, r[3].mid, r[2].down);
+}
+
 template <typename real, int NF>
 __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,7 +173,9 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
   const long long fs = P.fstride;
   const long long k = static_cast<long long>(j + GY) * P.pitch + i + GX;
   const real rho = P.W[k], mx = P.W[fs + k], my = P.W[2 * fs + k], E = P.W[3 * fs + k];
-  const real u = mx / rho, v = my / rho;
+  // 1 / rho: an approximate reciprocal in FP32, a true division in FP64
+  const real rr = sizeof(real) == 4 ? static_cast<real>(RT<float>::rcp(static_cast<float>(rho))) : real(1) / rho;
+  const real u = sizeof(real) == 4 ? mx * rr : mx / rho, v = sizeof(real) == 4 ? my * rr : my / rho;
   const real p = (P.gamma - real(1)) * (E - real(0.5) * (mx * u + my * v));
   real nu[NF];
 #pragma unroll
@@ -194,15 +212,27 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
       dxs[q] = (ph[q - 2] - ph[q - 3]) * rdx;                          // D_{i-3+q}
       dys[q] = (ph[(q - 2) * P.pitch] - ph[(q - 3) * P.pitch]) * rdy;  // D_{j-3+q}
     }
-    const real xm = weno5_plain(dxs[0], dxs[1], dxs[2], dxs[3], dxs[4]);
-    const real xq = weno5_plain(dxs[5], dxs[4], dxs[3], dxs[2], dxs[1]);
-    const real ym = weno5_plain(dys[0], dys[1], dys[2], dys[3], dys[4]);
-    const real yq = weno5_plain(dys[5], dys[4], dys[3], dys[2], dys[1]);
+    real xm, xq, ym, yq, Hgx, Hgy;
     const real sf = P.flame_speed;
+    if constexpr (sizeof(real) == 4) {  // the stage kernel's FP32 one-sided derivatives (triplet form)
+      phi_derivs_f32(dxs, xm, xq);
+      phi_derivs_f32(dys, ym, yq);
+      const real gx = real(0.5) * (xm + xq), gy = real(0.5) * (ym + yq);
+      const real n2 = gx * gx + gy * gy;
+      const real rn = n2 > real(0) ? RT<float>::rcp(RT<float>::sqrt_(n2)) : real(0);
+      Hgx = u - sf * gx * rn;
+      Hgy = v - sf * gy * rn;
+    } else {
+      xm = weno5_plain(dxs[0], dxs[1], dxs[2], dxs[3], dxs[4]);
+      xq = weno5_plain(dxs[5], dxs[4], dxs[3], dxs[2], dxs[1]);
+      ym = weno5_plain(dys[0], dys[1], dys[2], dys[3], dys[4]);
+      yq = weno5_plain(dys[5], dys[4], dys[3], dys[2], dys[1]);
+      const real gx = real(0.5) * (xm + xq), gy = real(0.5) * (ym + yq);
+      const real nrm = sqrt(gx * gx + gy * gy);
+      Hgx = u - (nrm > real(0) ? sf * gx / nrm : real(0));
+      Hgy = v - (nrm > real(0) ? sf * gy / nrm : real(0));
+    }
     const real gx = real(0.5) * (xm + xq), gy = real(0.5) * (ym + yq);
-    const real nrm = sqrt(gx * gx + gy * gy);
-    const real Hgx = u - (nrm > real(0) ? sf * gx / nrm : real(0));
-    const real Hgy = v - (nrm > real(0) ? sf * gy / nrm : real(0));
     const real axl = fabs(u) + sf, ayl = fabs(v) + sf;
     const real hbar = -nu[4];  // L_phi = -H_hat
     P.hb[0 * fs + k] = hbar * (real(0.5) * Hgx + real(0.5) * axl);
@@ -213,9 +243,15 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
     const real sv = v > real(0) ? real(1) : (v < real(0) ? real(-1) : real(0));
     const real ub = hbar * (gx - su * real(0.5) * (xq - xm));
     const real vb = hbar * (gy - sv * real(0.5) * (yq - ym));
-    g[0] += ub * (-u / rho) + vb * (-v / rho);
-    g[1] += ub / rho;
-    g[2] += vb / rho;
+    if constexpr (sizeof(real) == 4) {
+      g[0] -= (ub * u + vb * v) * rr;
+      g[1] += ub * rr;
+      g[2] += vb * rr;
+    } else {
+      g[0] += ub * (-u / rho) + vb * (-v / rho);
+      g[1] += ub / rho;
+      g[2] += vb / rho;
+    }
   }
 #pragma unroll
   for (int s = 0; s < 4; ++s) P.mu[s * fs + k] = g[s];

@@ -66,6 +66,9 @@ struct hydro_ctx {
   double* alpha_log = nullptr;
   int log_cap = 0;
   bool track_totals = true;
+  // inside an adjoint sweep: the device error word accumulates over all its steps and is read once at
+  // the end, so the sweep's steps need no host round trip
+  bool defer_status = false;
   // graph of one step
   cudaGraphExec_t step_graph = nullptr;
   long long step_graph_launches = 0;
@@ -348,7 +351,8 @@ static int ensure_graph(hydro_ctx* c) {
 template <typename real>
 static int pack_state(hydro_ctx* c, const real* U, double t0) {
   Scratch<real>* s = scr<real>(c);
-  CK(cudaMemsetAsync(s, 0, offsetof(Scratch<real>, log_count), c->stream));
+  CK(cudaMemsetAsync(s, 0, c->defer_status ? offsetof(Scratch<real>, err) : offsetof(Scratch<real>, log_count),
+                     c->stream));
   GridParams<real> g{};
   GridParams<real> all[7];
   build_params<real>(c, all);
@@ -433,7 +437,7 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
   if (frozen) {
     double tt = t_inout ? *t_inout : 0.0;
     for (int st = 0; st < nsteps; ++st) tt += dtl[st];
-    int r2 = read_status<real>(c, nullptr, nullptr);
+    int r2 = c->defer_status ? HYDRO_OK : read_status<real>(c, nullptr, nullptr);
     if (t_inout) *t_inout = tt;
     if (dt_last && nsteps > 0) *dt_last = dtl[nsteps - 1];
     return r2;
@@ -1032,7 +1036,7 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
   }
   rc = copy_out<real>(c, lam, static_cast<const real*>(c->adj_acc));
   if (rc) return rc;
-  return read_status<real>(c, nullptr, nullptr);
+  return c->defer_status ? HYDRO_OK : read_status<real>(c, nullptr, nullptr);
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, const double alpha[6]) {
@@ -1080,23 +1084,9 @@ int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
 }
 
 template <typename real>
-static int sweep_impl(hydro_ctx* c, real* lam) {
-  const int N = c->ck_nsteps, every = c->ck_every;
-  std::vector<double> dtl(N), al(6 * (size_t)N);
-  int got = 0;
-  int rc = hydro_get_log(c, N, dtl.data(), al.data(), &got);
-  if (rc) return rc;
-  const size_t elems = (size_t)c->nf * c->cfg.nx * c->cfg.ny;
-  const size_t state = elems * sizeof(real);
-  if (c->seg_cap < (size_t)every) {
-    cudaFree(c->seg);
-    c->seg = nullptr;
-    c->seg_cap = 0;
-    CK(cudaMalloc(&c->seg, state * every));
-    c->seg_cap = every;
-  }
-  real* seg = static_cast<real*>(c->seg);
-  const int nseg = (N + every - 1) / every;
+static int sweep_segments(hydro_ctx* c, real* lam, real* seg, int nseg, int every, int N, size_t elems, size_t state,
+                          const std::vector<double>& dtl, const std::vector<double>& al) {
+  int rc = HYDRO_OK;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int s0 = sg * every, s1 = std::min(N, s0 + every);
     // recompute the segment's states from its checkpoint with the recorded dt / alphas
@@ -1114,6 +1104,32 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
     }
   }
   return HYDRO_OK;
+}
+
+template <typename real>
+static int sweep_impl(hydro_ctx* c, real* lam) {
+  const int N = c->ck_nsteps, every = c->ck_every;
+  std::vector<double> dtl(N), al(6 * (size_t)N);
+  int got = 0;
+  int rc = hydro_get_log(c, N, dtl.data(), al.data(), &got);
+  if (rc) return rc;
+  const size_t elems = (size_t)c->nf * c->cfg.nx * c->cfg.ny;
+  const size_t state = elems * sizeof(real);
+  if (c->seg_cap < (size_t)every) {
+    cudaFree(c->seg);
+    c->seg = nullptr;
+    c->seg_cap = 0;
+    CK(cudaMalloc(&c->seg, state * every));
+    c->seg_cap = every;
+  }
+  real* seg = static_cast<real*>(c->seg);
+  const int nseg = (N + every - 1) / every;
+  CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
+  c->defer_status = true;
+  rc = sweep_segments<real>(c, lam, seg, nseg, every, N, elems, state, dtl, al);
+  c->defer_status = false;
+  if (rc) return rc;
+  return read_status<real>(c, nullptr, nullptr);
 }
 
 int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {

@@ -686,7 +686,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NWARPS = NT / 32;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
