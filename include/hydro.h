@@ -99,9 +99,10 @@ int hydro_set_stream(hydro_ctx* ctx, void* stream);
 int hydro_step(hydro_ctx* ctx, void* U, int nsteps, double* t_inout, double* dt_last);
 
 /* Same as hydro_step for a state in HOST memory, on the context's stream. Pinned (page-locked) memory is
- * read and written in place over the host link: the kernel that builds the padded working state reads
- * it, and the last stage of the last step writes the result straight into it (no staging copies).
- * Pageable memory is copied to a device buffer, stepped and copied back. */
+ * used in place: the kernel that builds the padded working state reads it over the host link, and the
+ * last stage of the last step runs in row bands while a second stream of the context copies each finished
+ * band back into it (copy engine, overlapped with the next band). Pageable memory is copied to a device
+ * buffer, stepped and copied back. */
 int hydro_step_host(hydro_ctx* ctx, void* U_host, int nsteps, double* t_inout, double* dt_last);
 
 /* Spatial operator L(U) = -(dF/dx + dG/dy) + S(U) and the level-set right-hand side -H_hat, with the

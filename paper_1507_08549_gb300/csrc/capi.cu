@@ -45,6 +45,12 @@ struct hydro_ctx {
   hydro_config cfg{};
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+  // host-buffer calls: the last stage runs in row bands; a copy stream moves each finished band's rows
+  // to the caller's pinned state while the next band computes
+  static constexpr int NBANDS = 8;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t band_ev[NBANDS] = {};
+  cudaEvent_t copy_done = nullptr;
   int device = 0, num_sms = 0;
   int nf = 4;
   size_t esize = 4;
@@ -54,8 +60,7 @@ struct hydro_ctx {
   long long fstride = 0;
   void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
   void* scratch = nullptr;
-  void* params = nullptr;  // device GridParams[8]: normal stages 0..2, frozen stages 3..5, rhs 6, and slot 7 =
-                           // stage 2 writing a host-buffer caller's state directly (set per call)
+  void* params = nullptr;  // device GridParams[8]: normal stages 0..2, frozen stages 3..5, rhs 6 (7 unused)
   void* host_scratch = nullptr;  // pinned copy of Scratch
   double* partials = nullptr;
   int partial_blocks = 0;
@@ -389,6 +394,51 @@ static int read_status(hydro_ctx* c, double* t_inout, double* dt_last) {
   return HYDRO_OK;
 }
 
+// Last stage of a host-buffer call: the stage kernel runs over row bands of tiles on the context's stream;
+// after each band, the copy stream moves that band's interior rows (every field) from the padded state to
+// the caller's dense pinned state, overlapping the copy engine with the next band's compute. The context's
+// stream then waits for the last copy.
+template <typename real>
+static int last_stage_to_host(hydro_ctx* c, real* host_out) {
+  const hydro_config& g = c->cfg;
+  const int TY = tile_ty(c->variant);
+  const int trows = (g.ny + TY - 1) / TY;
+  const int nb = std::min(hydro_ctx::NBANDS, trows);
+  const GridParams<real>* p = static_cast<const GridParams<real>*>(c->params) + 2;
+  const real* A = bufp<real>(c, 0);
+  const size_t es = sizeof(real);
+  // an externally formed divergence (characteristic scheme, FP64 field split) first, for the whole grid
+  if (c->char_div) {
+    CK(launch_char_div<real>(p, g.nx, g.ny, c->stream));
+    c->launches++;
+  } else if (c->split_div) {
+    const int nall = c->tiles_x * trows;
+    const StageCtl split{2, 2, RK_A[2], RK_B[2]};
+    CK(launch_stage<real>(c->variant, c->nf, p, nullptr, 4 * nall, split, grid_for(c, 4 * nall), c->stream));
+    c->launches++;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const int r0 = b * trows / nb, r1 = (b + 1) * trows / nb;
+    StageCtl ctl{2, 0, RK_A[2], RK_B[2]};
+    ctl.w0 = r0 * c->tiles_x;
+    const int nwork = (r1 - r0) * c->tiles_x;
+    CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), c->stream));
+    c->launches++;
+    CK(cudaEventRecord(c->band_ev[b], c->stream));
+    CK(cudaStreamWaitEvent(c->copy_stream, c->band_ev[b], 0));
+    const int j0 = r0 * TY, j1 = std::min(g.ny, r1 * TY);
+    for (int f = 0; f < c->nf; ++f) {
+      const real* src = A + f * c->fstride + (long long)(j0 + GY) * c->pitch + GX;
+      real* dst = host_out + (size_t)f * g.nx * g.ny + (size_t)j0 * g.nx;
+      CK(cudaMemcpy2DAsync(dst, g.nx * es, src, c->pitch * es, g.nx * es, j1 - j0, cudaMemcpyDeviceToHost,
+                           c->copy_stream));
+    }
+  }
+  CK(cudaEventRecord(c->copy_done, c->copy_stream));
+  CK(cudaStreamWaitEvent(c->stream, c->copy_done, 0));
+  return HYDRO_OK;
+}
+
 template <typename real>
 static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double* dt_last, const double* dtl,
                      const double* al, real* host_out = nullptr) {
@@ -419,16 +469,9 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
     if (rc) return rc;
   }
   if (direct) {
-    GridParams<real> all[7];
-    build_params<real>(c, all);
-    GridParams<real> last = all[2];
-    last.out_dense = host_out;
-    last.dense_fs = (long long)c->cfg.nx * c->cfg.ny;
-    CK(cudaMemcpyAsync(static_cast<GridParams<real>*>(c->params) + 7, &last, sizeof(last), cudaMemcpyHostToDevice,
-                       c->stream));
     rc = launch_one<real>(c, 0, 0, 0, RK_A[0], RK_B[0], c->stream);
     if (!rc) rc = launch_one<real>(c, 1, 1, 0, RK_A[1], RK_B[1], c->stream);
-    if (!rc) rc = launch_one<real>(c, 7, 2, 0, RK_A[2], RK_B[2], c->stream);
+    if (!rc) rc = last_stage_to_host<real>(c, host_out);
     if (rc) return rc;
   } else {
     rc = unpack_state<real>(c, U, 0);
@@ -505,6 +548,10 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMalloc(&c->d_totals, sizeof(double) * 5) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(HYDRO_ECUDA);
+  for (int b = 0; b < hydro_ctx::NBANDS; ++b)
+    if (cudaEventCreateWithFlags(&c->band_ev[b], cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->variant = 1;
   if (upload(c) != HYDRO_OK) return bail(HYDRO_ECUDA);
   *out = c;
@@ -547,6 +594,13 @@ void hydro_destroy(hydro_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->done) cudaEventDestroy(c->done);
   if (c->capture) cudaStreamDestroy(c->capture);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (cudaEvent_t e : c->band_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->copy_done) cudaEventDestroy(c->copy_done);
   delete c;
 }
 

@@ -65,8 +65,6 @@ struct GridParams {
   double* totals_reset;   // totals array to clear (stage 1), may be null
   int* err;               // error bits
   const real* ext_div;    // characteristic scheme: D = dF/dx + dG/dy of the hydro fields (padded), else null
-  real* out_dense;        // if set: write the output here instead, dense [NF][ny][nx] (host memory), no ghosts
-  long long dense_fs;     // nx * ny
 };
 
 // Launch-wide stage control.
@@ -76,6 +74,7 @@ struct StageCtl {
                   // dF/dx + dG/dy of hydro field w & 3 on tile w >> 2 into ext_div (FP64 grids with few tiles)
   double rk_a;    // out = a U^n + b (W + dt L)
   double rk_b;
+  int w0 = 0;     // first tile of the launch (row bands of one stage); work items w -> tile w0 + w
 };
 
 // Batched launch: a table of (member, tile) work items over an array of member parameters.

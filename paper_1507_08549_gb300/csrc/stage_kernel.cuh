@@ -663,10 +663,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   using T = RT<real>;
   using TL = Tile<real, NF, TY>;
   constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ;
-  constexpr int DVEC = 16 / sizeof(real);  // elements per 16-byte chunk of a host output row
-  static_assert((TL::OFF_D * sizeof(real)) % 16 == 0 && (TL::OFF_X * sizeof(real)) % 16 == 0 &&
-                    (TY * TX * sizeof(real)) % 16 == 0 && (TX * sizeof(real)) % 16 == 0,
-                "16-byte aligned staging rows");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
@@ -699,7 +695,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   if (warp == 0 && static_cast<int>(blockIdx.x) < nwork) {
     const int w0 = blockIdx.x;
     const int m0 = work ? work[w0].member : 0;
-    const int t0 = work ? work[w0].tile : ((sizeof(real) == 8 && ctl.mode == 2) ? w0 >> 2 : w0);
+    const int t0 = work ? work[w0].tile : ((sizeof(real) == 8 && ctl.mode == 2) ? w0 >> 2 : ctl.w0 + w0);
     issue_box<real, NF, H>(members[m0], t0, TY, sm + TL::OFF_U0, &bar[0], lane, TL::BOX_BYTES);
   }
 
@@ -737,7 +733,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int member = work ? work[w].member : 0;
     // mode 2 (field split, FP64 only): item w is field w & 3 of tile w >> 2
     constexpr bool kSplit = sizeof(real) == 8;
-    const int tile = work ? work[w].tile : ((kSplit && ctl.mode == 2) ? w >> 2 : w);
+    const int tile = work ? work[w].tile : ((kSplit && ctl.mode == 2) ? w >> 2 : ctl.w0 + w);
     const int split_field = (kSplit && ctl.mode == 2) ? (w & 3) : -1;
     if (member != cur_member) {
       if (cur_member >= 0) flush();
@@ -758,7 +754,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int wn = w + gridDim.x;
     if (warp == 0 && wn < nwork) {
       const int mn = work ? work[wn].member : 0;
-      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : wn), TY,
+      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : ctl.w0 + wn), TY,
                              sm + (b ? TL::OFF_U0 : TL::OFF_U1),
                              &bar[b ^ 1], lane, TL::BOX_BYTES);
     }
@@ -910,9 +906,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real dt = s_dt;
       const real ra = s_ra, rb = s_rb;
       const bool use_un = ra != real(0) && ctl.mode == 0;
-      // host output in whole 16-byte rows: every row of the tile starts on a 16-byte boundary
-      const bool dense_vec = g.out_dense && nx % DVEC == 0 &&
-                             (reinterpret_cast<unsigned long long>(g.out_dense) & 15ull) == 0;
       constexpr int NG = TX / EG;
       for (int it2 = tid; it2 < TY * NG; it2 += NT) {
         const int row = it2 / NG, g4 = it2 - row * NG;
@@ -974,35 +967,16 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             }
           }
         }
-        // stores: the padded working state, or (last stage of a host-buffer call) the caller's dense
-        // state in host memory, written directly over the host link
-        if (dense_vec) {  // staged in this thread's own (consumed) divergence slots, rows written below
+        // stores into the padded working state
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            real* st = (f < 4 ? sD + f * TY * TX : sX) + row * TX + tcol;
-#pragma unroll
-            for (int e = 0; e < EG; ++e) st[e] = o[f][e];
-          }
-        } else if (g.out_dense) {
-          const long long hbase = static_cast<long long>(j) * nx + ib;
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            real* dstp = g.out_dense + f * g.dense_fs + hbase;
+        for (int f = 0; f < NF; ++f) {
+          real* dstp = g.out + f * fs + gbase;
+          if (nvalid == EG) {
+            storeg<EG>(dstp, o[f]);
+          } else {
 #pragma unroll
             for (int e = 0; e < EG; ++e)
               if (e < nvalid) dstp[e] = o[f][e];
-          }
-        } else {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            real* dstp = g.out + f * fs + gbase;
-            if (nvalid == EG) {
-              storeg<EG>(dstp, o[f]);
-            } else {
-#pragma unroll
-              for (int e = 0; e < EG; ++e)
-                if (e < nvalid) dstp[e] = o[f][e];
-            }
           }
         }
         if (ctl.mode == 1) continue;
@@ -1011,7 +985,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         for (int e = 0; e < EG; ++e) {
           if (e >= nvalid) break;
           const int i = ib + e;
-          if (!g.out_dense && (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3)) {
+          if (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3) {
             real val[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) val[f] = o[f][e];
@@ -1040,21 +1014,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             }
           }
         }
-      }
-    }
-
-    // the tile's host output, staged above, as 16-byte row chunks (full lines over the host link)
-    if (split_field < 0 && g.out_dense && g.nx % DVEC == 0 &&
-        (reinterpret_cast<unsigned long long>(g.out_dense) & 15ull) == 0) {
-      __syncthreads();
-      constexpr int NVR = TX / DVEC;
-      for (int idx = tid; idx < NF * TY * NVR; idx += NT) {
-        const int f = idx / (TY * NVR), rem = idx - f * (TY * NVR), row = rem / NVR, q = rem - row * NVR;
-        const int j = y0 + row, i = x0 + q * DVEC;
-        if (j >= g.ny || i >= g.nx) continue;
-        const real* st = (f < 4 ? sD + f * TY * TX : sX) + row * TX + q * DVEC;
-        *reinterpret_cast<uint4*>(g.out_dense + f * g.dense_fs + static_cast<long long>(j) * g.nx + i) =
-            *reinterpret_cast<const uint4*>(st);
       }
     }
 
