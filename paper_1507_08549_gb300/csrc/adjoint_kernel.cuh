@@ -144,6 +144,8 @@ struct AdjParams {
   int geometry;
   real gamma, gravity, flame_speed, ax, ay;
   double dx, dy, x0, dt, a, b;
+  // the same in the working precision, formed on the host (no FP64 arithmetic in the FP32 kernels)
+  real rdx_r, rdy_r, dx_r, x0_r, dt_r, a_r, b_r;
   int acc_mode;      // 0: acc = a nu ; 1: acc += a nu ; 2: acc += out (final stage), write out too
 };
 
@@ -182,7 +184,8 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
   for (int f = 0; f < NF; ++f) nu[f] = P.nu[f * fs + k];
   real g[4] = {real(0), real(0), real(0), real(0)};
   if (P.geometry == 1) {  // sources -(1/r)(m_r, m_r u, m_r v, (E + p) u)
-    const real r = static_cast<real>(P.x0 + (i + 0.5) * P.dx);
+    const real r = sizeof(real) == 4 ? P.x0_r + (static_cast<real>(i) + real(0.5)) * P.dx_r
+                                     : static_cast<real>(P.x0 + (i + 0.5) * P.dx);
     real J[4][4];
     flux_jacobian<real>(0, P.gamma, rho, mx, my, E, J);
     real JS[4][4];
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
   (void)p;
   if constexpr (NF == 5) {
     const real* ph = P.W + 4 * fs + k;
-    const real rdx = static_cast<real>(1.0 / P.dx), rdy = static_cast<real>(1.0 / P.dy);
+    const real rdx = P.rdx_r, rdy = P.rdy_r;
     real dxs[6], dys[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
   for (int pass = 0; pass < 2; ++pass) {
     const bool xp = pass == 0;
     const real alpha = xp ? P.ax : P.ay;
-    const real rd = static_cast<real>(1.0 / (xp ? P.dx : P.dy));
+    const real rd = xp ? P.rdx_r : P.rdy_r;
     const int S = xp ? 1 : ABW;
     const int DS = xp ? 1 : AOS;
     // items: (field, line, run); x: ATY rows x 4 runs; y: ATX columns x 2 runs
@@ -743,7 +746,7 @@ __global__ void __launch_bounds__(256) adj_blend_kernel(AdjParams<real> P) {
       take(i, 2 * ny - 1 - j, false, true);
     }
   }
-  const real dt = static_cast<real>(P.dt), a = static_cast<real>(P.a), b = static_cast<real>(P.b);
+  const real dt = P.dt_r, a = P.a_r, b = P.b_r;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const real nu = P.nu[f * fs + k];

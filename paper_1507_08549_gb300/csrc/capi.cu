@@ -1072,6 +1072,11 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
   P.dy = (g.y1 - g.y0) / g.ny;
   P.x0 = g.x0;
   P.dt = dt;
+  P.rdx_r = static_cast<real>(1.0 / P.dx);
+  P.rdy_r = static_cast<real>(1.0 / P.dy);
+  P.dx_r = static_cast<real>(P.dx);
+  P.x0_r = static_cast<real>(P.x0);
+  P.dt_r = static_cast<real>(dt);
   // reverse stages 2, 1, 0
   const int order[3] = {2, 1, 0};
   for (int q = 0; q < 3; ++q) {
@@ -1083,6 +1088,8 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
     P.ay = static_cast<real>(alpha[2 * k + 1]);
     P.a = RK_A[k];
     P.b = RK_B[k];
+    P.a_r = static_cast<real>(P.a);
+    P.b_r = static_cast<real>(P.b);
     P.acc_mode = (q == 0) ? 0 : (q == 1) ? 1 : 2;
     int nl = 0;
     CK(launch_adjoint_stage<real>(P, c->nf, c->stream, &nl));
