@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
                                                        const real* __restrict__ front, int capacity,
                                                        const int* __restrict__ count, int* err) {
   __shared__ real sx[REINIT_CHUNK], sy[REINIT_CHUNK];
+  __shared__ float2 sxy[sizeof(real) == 4 ? REINIT_CHUNK : 1];  // FP32: a point's x, y in one 8-byte load
   const int m = min(*count, capacity);
   if (*count > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_NONPHYSICAL);
@@ -75,8 +76,12 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
     const int len = min(REINIT_CHUNK, m - base);
     __syncthreads();
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
-      sx[k] = front[2 * (base + k)];
-      sy[k] = front[2 * (base + k) + 1];
+      if constexpr (sizeof(real) == 4) {
+        sxy[k] = make_float2(front[2 * (base + k)], front[2 * (base + k) + 1]);
+      } else {
+        sx[k] = front[2 * (base + k)];
+        sy[k] = front[2 * (base + k) + 1];
+      }
     }
     __syncthreads();
     if (active) {
@@ -89,7 +94,8 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
       } else {
 #pragma unroll 8
         for (int k = 0; k < len; ++k) {
-          const real ex = x - sx[k], ey = y - sy[k];
+          const float2 q = sxy[k];
+          const real ex = x - q.x, ey = y - q.y;
           best = fminf(best, __fmaf_rn(ex, ex, ey * ey));
         }
       }
@@ -98,11 +104,19 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
   if (!active) return;
   const long long g = static_cast<long long>(j) * pitch + i;
   const real s_old = phi[g];
-  const double d = sqrt(static_cast<double>(best));
-  const double d0 = 3.0 * delta, w = delta / 3.0;
-  const double H = (1.0 - tanh((d - d0) / w)) / (1.0 - tanh(-d0 / w));
-  const double sd = s_old > real(0) ? d : -d;
-  phi[g] = static_cast<real>(H * static_cast<double>(s_old) + (1.0 - H) * sd);
+  if constexpr (sizeof(real) == 4) {  // the blend in FP32 too (the FP64 pipe runs at 1/64 of the FP32 rate)
+    const float d = sqrtf(best), df = static_cast<float>(delta);
+    // (d - d0) / w with d0 = 3 delta, w = delta / 3; -d0 / w = -9
+    const float H = (1.0f - tanhf((d - 3.0f * df) * (3.0f / df))) / (1.0f - tanhf(-9.0f));
+    const float sd = s_old > 0.0f ? d : -d;
+    phi[g] = H * s_old + (1.0f - H) * sd;
+  } else {
+    const double d = sqrt(static_cast<double>(best));
+    const double d0 = 3.0 * delta, w = delta / 3.0;
+    const double H = (1.0 - tanh((d - d0) / w)) / (1.0 - tanh(-d0 / w));
+    const double sd = s_old > real(0) ? d : -d;
+    phi[g] = static_cast<real>(H * static_cast<double>(s_old) + (1.0 - H) * sd);
+  }
 }
 
 }  // namespace hydro
