@@ -7,8 +7,9 @@
 //                  shared memory in chunks; squared distances are compared, one square root at the
 //                  end), then S_new = H(d) S_old + (1 - H(d)) d with the sign of S_old and
 //                  H(d) = [1 - tanh((d - d0)/(Delta/3))] / [1 - tanh(-d0/(Delta/3))], d0 = 3 Delta.
-// The point order depends on atomics; the minimum does not, so results are deterministic. FP64 uses
-// the reference definition's operation order (true division, IEEE square root).
+//                  FP64 states, in the reference definition's operation order (true division, IEEE
+//                  square root); FP32 states use distance_kernel_x2 (two cells per thread, packed FP32).
+// The point order depends on atomics; the minimum does not, so results are deterministic.
 #pragma once
 #include "stage_kernel.cuh"
 
@@ -56,8 +57,8 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
                                                        double x0, double y0, double dx, double dy, double delta,
                                                        const real* __restrict__ front, int capacity,
                                                        const int* __restrict__ count, int* err) {
+  static_assert(sizeof(real) == 8, "FP32 states use distance_kernel_x2");
   __shared__ real sx[REINIT_CHUNK], sy[REINIT_CHUNK];
-  __shared__ float2 sxy[sizeof(real) == 4 ? REINIT_CHUNK : 1];  // FP32: a point's x, y in one 8-byte load
   const int m = min(*count, capacity);
   if (*count > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_NONPHYSICAL);
@@ -76,46 +77,91 @@ __global__ void __launch_bounds__(256) distance_kernel(real* __restrict__ phi, i
     const int len = min(REINIT_CHUNK, m - base);
     __syncthreads();
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
-      if constexpr (sizeof(real) == 4) {
-        sxy[k] = make_float2(front[2 * (base + k)], front[2 * (base + k) + 1]);
-      } else {
-        sx[k] = front[2 * (base + k)];
-        sy[k] = front[2 * (base + k) + 1];
-      }
+      sx[k] = front[2 * (base + k)];
+      sy[k] = front[2 * (base + k) + 1];
     }
     __syncthreads();
     if (active) {
-      if constexpr (sizeof(real) == 8) {
-        for (int k = 0; k < len; ++k) {
-          const real ex = __dsub_rn(x, sx[k]), ey = __dsub_rn(y, sy[k]);
-          const real d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
-          best = d2 < best ? d2 : best;
-        }
-      } else {
-#pragma unroll 8
-        for (int k = 0; k < len; ++k) {
-          const float2 q = sxy[k];
-          const real ex = x - q.x, ey = y - q.y;
-          best = fminf(best, __fmaf_rn(ex, ex, ey * ey));
-        }
+      for (int k = 0; k < len; ++k) {
+        const real ex = __dsub_rn(x, sx[k]), ey = __dsub_rn(y, sy[k]);
+        const real d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+        best = d2 < best ? d2 : best;
       }
     }
   }
   if (!active) return;
   const long long g = static_cast<long long>(j) * pitch + i;
   const real s_old = phi[g];
-  if constexpr (sizeof(real) == 4) {  // the blend in FP32 too (the FP64 pipe runs at 1/64 of the FP32 rate)
-    const float d = sqrtf(best), df = static_cast<float>(delta);
-    // (d - d0) / w with d0 = 3 delta, w = delta / 3; -d0 / w = -9
-    const float H = (1.0f - tanhf((d - 3.0f * df) * (3.0f / df))) / (1.0f - tanhf(-9.0f));
+  const double d = sqrt(static_cast<double>(best));
+  const double d0 = 3.0 * delta, w = delta / 3.0;
+  const double H = (1.0 - tanh((d - d0) / w)) / (1.0 - tanh(-d0 / w));
+  const double sd = s_old > real(0) ? d : -d;
+  phi[g] = static_cast<real>(H * static_cast<double>(s_old) + (1.0 - H) * sd);
+}
+
+// FP32: two cells per thread (cells b + t and b + 256 + t of a 512-cell block) in the two lanes of packed
+// f32x2 arithmetic, each lane rounding exactly as the scalar kernel's operations (same distances, same
+// minimum); the points are stored as (-x, -x, -y, -y) so one 16-byte load feeds both lanes.
+template <typename real>  // float only (a template so that only the FP32 translation unit instantiates it)
+__global__ void __launch_bounds__(256) distance_kernel_x2(real* __restrict__ phi, int nx, int ny, int pitch,
+                                                          double x0, double y0, double dx, double dy, double delta,
+                                                          const real* __restrict__ front, int capacity,
+                                                          const int* __restrict__ count, int* err) {
+  static_assert(sizeof(real) == 4, "packed FP32 distance kernel");
+  __shared__ float4 sp[REINIT_CHUNK];
+  const int m = min(*count, capacity);
+  if (*count > capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_NONPHYSICAL);
+    return;
+  }
+  if (m == 0) return;  // no front: S unchanged
+  const long long n = static_cast<long long>(nx) * ny;
+  long long cell[2];
+  bool active[2];
+  float2 X, Y;
+  float* xs = &X.x;
+  float* ys = &Y.x;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    cell[h] = static_cast<long long>(blockIdx.x) * 512 + h * 256 + threadIdx.x;
+    active[h] = cell[h] < n;
+    const int i = active[h] ? static_cast<int>(cell[h] % nx) : 0;
+    const int j = active[h] ? static_cast<int>(cell[h] / nx) : 0;
+    xs[h] = static_cast<float>(__dadd_rn(x0, __dmul_rn(i + 0.5, dx)));
+    ys[h] = static_cast<float>(__dadd_rn(y0, __dmul_rn(j + 0.5, dy)));
+  }
+  float best0 = INFINITY, best1 = INFINITY;
+  for (int base = 0; base < m; base += REINIT_CHUNK) {
+    const int len = min(REINIT_CHUNK, m - base);
+    __syncthreads();
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+      const float px = front[2 * (base + k)], py = front[2 * (base + k) + 1];
+      sp[k] = make_float4(-px, -px, -py, -py);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < len; ++k) {
+      const float4 q = sp[k];
+      const float2 ex = __fadd2_rn(X, make_float2(q.x, q.y));
+      const float2 ey = __fadd2_rn(Y, make_float2(q.z, q.w));
+      const float2 d2 = __ffma2_rn(ex, ex, __fmul2_rn(ey, ey));
+      best0 = fminf(best0, d2.x);
+      best1 = fminf(best1, d2.y);
+    }
+  }
+  const float df = static_cast<float>(delta);
+  const float norm = 1.0f / (1.0f - tanhf(-9.0f));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!active[h]) continue;
+    const int i = static_cast<int>(cell[h] % nx), j = static_cast<int>(cell[h] / nx);
+    const long long g = static_cast<long long>(j) * pitch + i;
+    const float s_old = phi[g];
+    const float d = sqrtf(h ? best1 : best0);
+    // the blend of the scalar kernel: (d - d0) / w with d0 = 3 delta, w = delta / 3
+    const float H = (1.0f - tanhf((d - 3.0f * df) * (3.0f / df))) * norm;
     const float sd = s_old > 0.0f ? d : -d;
     phi[g] = H * s_old + (1.0f - H) * sd;
-  } else {
-    const double d = sqrt(static_cast<double>(best));
-    const double d0 = 3.0 * delta, w = delta / 3.0;
-    const double H = (1.0 - tanh((d - d0) / w)) / (1.0 - tanh(-d0 / w));
-    const double sd = s_old > real(0) ? d : -d;
-    phi[g] = static_cast<real>(H * static_cast<double>(s_old) + (1.0 - H) * sd);
   }
 }
 

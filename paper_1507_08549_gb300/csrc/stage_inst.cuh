@@ -143,8 +143,13 @@ cudaError_t launch_reinit<HYDRO_REAL>(HYDRO_REAL* phi, int nx, int ny, int pitch
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long n = static_cast<long long>(nx) * ny;
+#if HYDRO_REAL_IS_FLOAT
+  distance_kernel_x2<HYDRO_REAL><<<static_cast<unsigned>((n + 511) / 512), 256, 0, s>>>(
+      phi, nx, ny, pitch, x0, y0, dx, dy, dx < dy ? dx : dy, front, capacity, count, err);
+#else
   distance_kernel<HYDRO_REAL><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
       phi, nx, ny, pitch, x0, y0, dx, dy, dx < dy ? dx : dy, front, capacity, count, err);
+#endif
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
