@@ -115,9 +115,10 @@ int hydro_rhs(hydro_ctx* ctx, const void* U, double alpha_x, double alpha_y, voi
 int conserved_totals(hydro_ctx* ctx, const void* U, double out[5]);
 
 /* Totals of the state written by the last completed hydro_step / hydro_batch_step, accumulated by the
- * last stage kernel of each step. FP64 contexts: FP64 sums of U_f dV. FP32 contexts: each warp's cells are
- * summed in FP32 (U_f, times r_i in (r,z)) and the warp partials in FP64, dV applied once, so the result
- * agrees with conserved_totals to about 1e-7 of sum |U_f dV|. Atomics: the last bits may vary between runs. */
+ * last stage kernel of each step. FP64 contexts: FP64 sums of U_f dV. FP32 contexts: each warp's cells of
+ * a tile are summed in FP32 (U_f, times r_i in (r,z)), each warp's tile partials in a compensated FP32
+ * sum (value plus error term), and those across the grid in FP64, dV applied once, so the result agrees
+ * with conserved_totals to about 1e-7 of sum |U_f dV|. Atomics: the last bits may vary between runs. */
 int hydro_last_totals(hydro_ctx* ctx, double out[5]);
 
 /* Conserved totals of a device state WITHOUT allocating anything and without a context, for callers

@@ -596,7 +596,15 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
 #pragma unroll
       for (int q = 0; q < 4; ++q) sH[q * TL::BOX + idx] = in ? P.hb[q * fs + k] : real(0);
     }
-    const real u = wv[1] / wv[0], v = wv[2] / wv[0];
+    real u, v;
+    if constexpr (sizeof(real) == 4) {
+      const real rr = RT<float>::rcp(wv[0]);
+      u = wv[1] * rr;
+      v = wv[2] * rr;
+    } else {
+      u = wv[1] / wv[0];
+      v = wv[2] / wv[0];
+    }
     sP[0 * TL::BOX + idx] = u;
     sP[1 * TL::BOX + idx] = v;
     sP[2 * TL::BOX + idx] = (gamma - real(1)) * (wv[3] - real(0.5) * (wv[1] * u + wv[2] * v));
