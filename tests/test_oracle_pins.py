@@ -317,7 +317,7 @@ def test_gresho_vortex_errors_as_in_table_test2d():
     assert l1[1] < l1[0]
 
 
-def _run_to(prob, t_end):
+def _state_at(prob, t_end):
     U, t = prob.U0, 0.0
     while t < t_end - 1e-12:
         U, t, _ = oracle.step(prob, U, 1, t)
@@ -341,9 +341,9 @@ def test_rz_cylinder_matches_binned_cartesian_explosion():
     # sources dropped) differ some 30 times more.
     errs = []
     for n in (64, 128):
-        cyl = _run_to(_cylinder_strip(n, 1), 0.25)[0, 0]
-        slab = _run_to(_cylinder_strip(n, 0), 0.25)[0, 0]
-        cart = _run_to(wl.explosion(n), 0.25)[0]
+        cyl = _state_at(_cylinder_strip(n, 1), 0.25)[0, 0]
+        slab = _state_at(_cylinder_strip(n, 0), 0.25)[0, 0]
+        cart = _state_at(wl.explosion(n), 0.25)[0]
         x = wl.centres(n, 0.0, 1.5)
         X, Y = np.meshgrid(x, x)
         k = np.floor(np.hypot(X, Y) / (1.5 / n)).astype(int)
