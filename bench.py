@@ -197,10 +197,10 @@ def run_reference(args):
 
 
 # Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
-# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 643.0, 986.9 and 970.3 MB
+# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 641.9, 987.0 and 970.1 MB
 # for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
 # a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (642.97e6 + 986.94e6 + 970.27e6) / 3.0 / (4096 * 4096)
+TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (641.88e6 + 986.99e6 + 970.06e6) / 3.0 / (4096 * 4096)
 
 # FP32 arithmetic operations the stage performs per cell (one per rounded operation, a fused multiply-add
 # counted once), from the kernel's arithmetic with its sharing in place and the line halos included. A
@@ -538,6 +538,45 @@ SOR_OPS_PER_CELL = 16
 FP64_OPS_NOMINAL = 0.625e12
 
 
+def adjoint_timing(args):
+    """FP32 discrete adjoint of one step of a blobs + blast state (--workload blobs_blast_<n>): `warmup`
+    forward steps, the step to reverse recorded (its dt and alphas frozen), one warm-up adjoint step, then
+    `adjoint_steps` timed adjoint steps with a seeded random cotangent, next to `steps` forward steps."""
+    import torch
+    from paper_1507_08549_gb300 import hydro
+    from paper_1507_08549_gb300 import workloads as wl
+    if not args.workload.startswith("blobs_blast"):
+        raise SystemExit("--only-adjoint times a blobs_blast workload")
+    prob = workload(args.workload)
+    h = hydro.Hydro(prob, dtype="f32")
+    U = h.state(prob.U0)
+    h.step(U, args.warmup)
+    h.record(2)
+    h.step(U, 1)
+    dtl, al = h.get_log(1)
+    h.record(0)
+    gen = torch.Generator(device=U.device).manual_seed(wl.DEFAULT_SEED)
+    lam = torch.rand(U.shape, generator=gen, device=U.device, dtype=U.dtype) * 2 - 1
+    h.adjoint_step(U, lam.clone(), float(dtl[0]), al[0].ravel())
+    ka = max(1, args.adjoint_steps)
+    lam_k = [lam.clone() for _ in range(ka)]
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for k in range(ka):
+        h.adjoint_step(U, lam_k[k], float(dtl[0]), al[0].ravel())
+    a1.record()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    h.step(U, args.steps)
+    f1.record()
+    torch.cuda.synchronize()
+    h.close()
+    adj_ms, fwd_ms = a0.elapsed_time(a1) / ka, f0.elapsed_time(f1) / args.steps
+    return {"workload": args.workload, "dtype": "f32", "adjoint_ms_per_step": adj_ms, "forward_ms_per_step": fwd_ms,
+            "adjoint_over_forward": adj_ms / fwd_ms, "adjoint_steps": ka, "cotangent": "seeded uniform [-1, 1]"}
+
+
 def poisson_timing(args):
     """Self-gravity potential of the 1024 x 2048 (r,z) star (hydro_poisson): (a) a fixed number of
     red-black sweeps (tol = 0) from a zero guess, timed with CUDA events after a warm-up solve; (b) a
@@ -629,6 +668,9 @@ def main():
     ap.add_argument("--poisson-sweeps", type=int, default=2048)
     ap.add_argument("--only-poisson", action="store_true",
                     help="time the self-gravity Poisson solve alone and print its JSON (profiling)")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="time the FP32 adjoint step of a blobs + blast workload alone and print its JSON "
+                         "(profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -636,6 +678,9 @@ def main():
         return run_reference(args)
     if args.only_poisson:
         print(json.dumps(poisson_timing(args)), flush=True)
+        return 0
+    if args.only_adjoint:
+        print(json.dumps(adjoint_timing(args)), flush=True)
         return 0
     return run(args)
 

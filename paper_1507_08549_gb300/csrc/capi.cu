@@ -901,17 +901,22 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
         P[(size_t)s * n + k].ext_div = nullptr;  // the batched launch computes every field itself
       }
     }
-    // interleave members so every CTA of the persistent launch sees a mix of grid sizes
-    std::vector<int> ntile(n), next(n, 0);
-    int total = 0;
+    // CTA b of the persistent launch takes items b, b + G, b + 2G, ...: give it a contiguous run of the
+    // member-ordered tile list, so that it changes member (a flush and a parameter reload) only at run
+    // boundaries; every CTA gets the same number of tiles (within one)
+    std::vector<WorkItem> L;
     for (int k = 0; k < n; ++k) {
-      ntile[k] = m[k]->tiles_x * ((m[k]->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
-      total += ntile[k];
+      const int nt = m[k]->tiles_x * ((m[k]->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
+      for (int t = 0; t < nt; ++t) L.push_back(WorkItem{k, t});
     }
-    W.reserve(total);
-    while ((int)W.size() < total)
-      for (int k = 0; k < n; ++k)
-        if (next[k] < ntile[k]) W.push_back(WorkItem{k, next[k]++});
+    const int total = (int)L.size();
+    const int G = grid_for(c, total);
+    W.assign(total, WorkItem{0, 0});
+    for (int b = 0, start = 0; b < G; ++b) {
+      const int cnt = (total - b + G - 1) / G;  // items w = b + kG < total
+      for (int k = 0; k < cnt; ++k) W[b + (size_t)k * G] = L[start + k];
+      start += cnt;
+    }
     CK(cudaMalloc(&c->plan_params, sizeof(GridParams<real>) * P.size()));
     CK(cudaMalloc(&c->plan_work, sizeof(WorkItem) * W.size()));
     CK(cudaMemcpy(c->plan_params, P.data(), sizeof(GridParams<real>) * P.size(), cudaMemcpyHostToDevice));
