@@ -798,7 +798,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     }
     parity[b] ^= 1u;
     __syncthreads();
-    if (s_abort) break;
+    if (s_abort) {
+      // a copy did not complete: before the CTA leaves (and its shared memory is reused), wait, again
+      // with a limit, for the copies it still has in flight (this box and the prefetched next one)
+      if (tid == 0) {
+        mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS);
+        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS);
+      }
+      break;
+    }
 
     // ---- B. primitive variables
     const real gm1 = g.gm1;
