@@ -197,10 +197,10 @@ def run_reference(args):
 
 
 # Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
-# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 641.9, 987.0 and 970.1 MB
+# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 643.2, 986.7 and 969.9 MB
 # for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
 # a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (641.88e6 + 986.99e6 + 970.06e6) / 3.0 / (4096 * 4096)
+TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (643.16e6 + 986.71e6 + 969.93e6) / 3.0 / (4096 * 4096)
 
 # FP32 arithmetic operations the stage performs per cell (one per rounded operation, a fused multiply-add
 # counted once), from the kernel's arithmetic with its sharing in place and the line halos included. A
