@@ -127,6 +127,7 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
 
 template <>
 cudaError_t launch_char_div<HYDRO_REAL>(const GridParams<HYDRO_REAL>* p_dev, int nx, int ny, cudaStream_t s) {
+  constexpr int CY = CharTile<HYDRO_REAL>::CY;
   const dim3 grid((nx + CX - 1) / CX, (ny + CY - 1) / CY);
   char_div_kernel<HYDRO_REAL><<<grid, CHAR_THREADS, 0, s>>>(p_dev);
   return cudaGetLastError();
