@@ -60,7 +60,7 @@ struct hydro_ctx {
   long long fstride = 0;
   void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
   void* scratch = nullptr;
-  void* params = nullptr;  // device GridParams[8]: normal stages 0..2, frozen stages 3..5, rhs 6 (7 unused)
+  void* params = nullptr;  // device GridParams[7]: normal stages 0..2, frozen stages 3..5, rhs 6
   void* host_scratch = nullptr;  // pinned copy of Scratch
   double* partials = nullptr;
   int partial_blocks = 0;
@@ -541,7 +541,7 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
-  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 8 : sizeof(GridParams<float>) * 8;
+  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 7 : sizeof(GridParams<float>) * 7;
   if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->partial_blocks = 4 * c->num_sms;
   if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
