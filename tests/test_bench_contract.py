@@ -1,0 +1,47 @@
+"""The benchmark's JSON contract and its roofline arithmetic, checked on the CPU: the reference arm (the
+FP64 oracle timed on the host) prints one line with the contract's keys, and the HBM roofline and the
+per-cell operation count follow their stated definitions."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "advected_wave_128", "--steps", "2", "--warmup", "3"], capture_output=True, text=True,
+                       cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["config"]["workload"] == "advected_wave_128"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["value"] == pytest.approx(128 * 128 * 2 / (d["ms_per_step"] * 2e-3), rel=1e-9)
+
+
+def test_hbm_roofline_and_operation_count():
+    sys.path.insert(0, ROOT)
+    import bench
+    cells, ms = 8192 * 8192, 3.7
+    hbm, none = bench.roofline(5, 4, cells, ms)
+    assert none is None
+    alg = 8 * 5 * 4 * cells / 3.0  # 8 F B bytes per cell and RK3 step, over 3 launches
+    assert hbm["alg_bytes_per_launch"] == pytest.approx(alg)
+    assert hbm["achieved"] == pytest.approx(alg / (ms * 1e-3) / 1e9)
+    assert hbm["frac"] == pytest.approx(hbm["achieved"] / hbm["peak"])
+    assert hbm["bound"] == "hbm" and hbm["unit"] == "GB/s"
+    # per-cell FP32 operations of a stage: 8 hydro lines of 1210.5 / 15, 2 level-set lines of 700 / 15,
+    # primitives 12.3 and the cell phase 61 (40 without the level set)
+    assert bench.alg_ops_per_cell_stage(5) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 2 * 700 / 15 + 61, abs=0.5)
+    assert bench.alg_ops_per_cell_stage(4) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 40, abs=0.5)
