@@ -6,14 +6,16 @@
 //      (cp.async.bulk, one row per copy, completion on an mbarrier);
 //   B. primitive variables u, v, p at the box points (rcp of rho once per point);
 //   C. x pass: each work item is (field, tile row, run of 15 cells); the split fluxes
-//      f+- = (F +- alpha U)/2, the per-point smoothness data and the 16 face fluxes of the run slide
-//      through registers, so every point's split flux and smoothness indicators are formed once;
-//      the level-set item forms one-sided HJ-WENO5 derivatives the same way;
-//   D. y pass: same on (field, tile column, run of up to 16 cells), accumulating dF/dx + dG/dy in
-//      shared memory; the level-set item closes the local Lax-Friedrichs Hamiltonian;
-//   E. per cell: L = -(dF/dx + dG/dy) + S, the RK blend a U^n + b (W + dt L), vector stores, the
-//      ghost images the boundary conditions ask for, and the reductions the next launches need:
-//      alpha_x, alpha_y of the output (next stage), c + |u| + |v| (next step's dt), FP64 totals.
+//      f+- = (F +- alpha U)/2, the data of every point triplet and the 16 face fluxes of the run slide
+//      through registers, so every point's split flux and every triplet's candidate values, smoothness
+//      indicators and weights are formed once (FP32; FP64 keeps the textbook per-face order); the
+//      level-set item forms the one-sided HJ-WENO5 derivatives the same way;
+//   D. y pass: same on (field, tile column, run of 15 cells), adding dG/dy to dF/dx in shared memory;
+//      the y pass of a hydro field waits only for that field's x-pass warps (named barrier);
+//   E. per 3-cell group: L = -(dF/dx + dG/dy) + S and the level set's local Lax-Friedrichs
+//      Hamiltonian, the RK blend a U^n + b (W + dt L), the stores, the ghost images the boundary
+//      conditions ask for, and the reductions the next launches need: alpha_x, alpha_y of the output
+//      (next stage), c + |u| + |v| (next step's dt), the conserved totals.
 // Lane-to-item maps make every shared-memory access of the passes bank-conflict free (68 = 4 mod 32
 // and 15 = 3 mod 4 spread the 32 lanes of an x-pass warp over all banks).
 #pragma once
