@@ -382,7 +382,16 @@ struct Ar<double> {
     const double e0 = ad(1e-6, b0), e1 = ad(1e-6, b1), e2 = ad(1e-6, b2);
     const double a0 = dv(0.1, ml(e0, e0)), a1 = dv(0.6, ml(e1, e1)), a2 = dv(0.3, ml(e2, e2));
     const double s = ad(ad(a0, a1), a2);
-    return ad(ad(ml(dv(a0, s), q0), ml(dv(a1, s), q1)), ml(dv(a2, s), q2));
+    const double ys = dv(1.0, s);  // the three quotients a_k / s share one correctly rounded reciprocal
+    return ad(ad(ml(div_by(a0, s, ys), q0), ml(div_by(a1, s, ys), q1)), ml(div_by(a2, s, ys), q2));
+  }
+  // RN(a / b) from yb = RN(1 / b): q = RN(a yb) is within an ulp of a / b, the residual a - q b is exact
+  // with a fused multiply-add, and one fused correction q + r yb rounds to the correctly rounded quotient
+  // (Markstein 1990) -- the same double an IEEE division returns, for normal operands and quotients.
+  static __device__ __forceinline__ double div_by(double a, double b, double yb) {
+    const double q = __dmul_rn(a, yb);
+    const double r = __fma_rn(-q, b, a);
+    return __fma_rn(r, yb, q);
   }
 };
 
