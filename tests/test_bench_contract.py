@@ -45,3 +45,25 @@ def test_hbm_roofline_and_operation_count():
     # primitives 12.3 and the cell phase 61 (40 without the level set)
     assert bench.alg_ops_per_cell_stage(5) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 2 * 700 / 15 + 61, abs=0.5)
     assert bench.alg_ops_per_cell_stage(4) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 40, abs=0.5)
+
+
+def _smi(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return f"0, {sm}, {mx}, 1012.45, 0x0000000000000000, {hw}, {hwt}, {swt}, {cap}\n"
+
+
+def test_clock_record_rejection_rules():
+    """A hardware or thermal slowdown rejects the timed region's number, a power cap alone keeps it (and is
+    reported), and a median SM clock well below the maximum with no reason active rejects it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = bench.Clocks.summarise([_smi(1965, 2070), _smi(1980, 2070), "garbage\n", _smi(1950, 2070)])
+    assert ok == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    assert bench.clocks_rejected(ok) is None
+    capped = bench.Clocks.summarise([_smi(1500, 2070, cap="Active"), _smi(1490, 2070, cap="Active")])
+    assert capped["reasons"] == ["sw_power_cap"] and bench.clocks_rejected(capped) is None
+    for kw, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown")):
+        rec = bench.Clocks.summarise([_smi(1900, 2070), _smi(1200, 2070, **{kw: "Active"})])
+        assert rec["reasons"] == [name] and bench.clocks_rejected(rec) == name
+    locked = bench.Clocks.summarise([_smi(1200, 2070)] * 5)
+    assert "no reason" in bench.clocks_rejected(locked)
+    assert bench.Clocks.summarise([]) is None and bench.clocks_rejected(None) is None
