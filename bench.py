@@ -435,9 +435,7 @@ def run(args):
                                                                        "gpu_launches": gpu_launches,
                                                                        "clocks": clk})), flush=True)
         return 0
-    Uh = U.cpu().numpy().copy()
-    if torch.cuda.is_available():
-        Uh_pinned = torch.from_numpy(Uh).pin_memory().numpy()
+    Uh_pinned = U.cpu().pin_memory().numpy()
     h.step_host(Uh_pinned, 1)
     torch.cuda.synchronize()
     ke = max(1, min(args.steps, args.e2e_steps))

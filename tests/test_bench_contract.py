@@ -67,3 +67,87 @@ def test_clock_record_rejection_rules():
     locked = bench.Clocks.summarise([_smi(1200, 2070)] * 5)
     assert "no reason" in bench.clocks_rejected(locked)
     assert bench.Clocks.summarise([]) is None and bench.clocks_rejected(None) is None
+
+
+def test_forward_path_times_again_after_a_rejected_clock_record(monkeypatch, capsys):
+    """The forward path on the CPU with the context, the CUDA events and the clock sampler replaced by fakes:
+    the first timed region's record shows a thermal slowdown, so the region is timed once more and the line
+    carries the second region's time, stage launches and clock record (naming why)."""
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+    from paper_1507_08549_gb300 import hydro
+
+    region_ms = iter([50.0, 20.0])
+    records = iter([{"sm_mhz": 1400.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"], "samples": 9},
+                    {"sm_mhz": 1960.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 9}])
+
+    class Event:  # each region records a start and an end event; the end carries the region's time
+        count = 0
+
+        def __init__(self, enable_timing=False):
+            self.at = 0.0
+
+        def record(self):
+            Event.count += 1
+            self.at = next(region_ms) if Event.count % 2 == 0 else 0.0
+
+        def elapsed_time(self, end):
+            return end.at - self.at
+
+    class Clocks:
+        def __init__(self, index):
+            pass
+
+        def start(self):
+            pass
+
+        def stop(self):
+            return dict(next(records))
+
+    class Ctx:
+        launches = 0
+
+        def __init__(self, prob, dtype):
+            self.steps = 0
+
+        def state(self, U0):
+            return torch.from_numpy(U0.copy())
+
+        def step(self, U, n):
+            self.steps += n
+            Ctx.launches += 3 * n
+            return 0.01 * self.steps, 0.01
+
+        def launch_count(self):
+            return Ctx.launches
+
+        def profile(self, on):
+            if on:
+                self.first = Ctx.launches
+
+        def stage_timing(self):
+            return Ctx.launches - self.first, 0.5 * (Ctx.launches - self.first)
+
+        def tile_variants(self):
+            return 1, 0
+
+        def tile_info(self, v):
+            return {"variant": v}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(bench, "Clocks", Clocks)
+    monkeypatch.setattr(hydro, "Hydro", Ctx)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "advected_wave_128", "--steps", "4", "--warmup", "3",
+                                      "--quick"])
+    assert bench.main() == 0
+    d = json.loads([l for l in capsys.readouterr().out.splitlines() if l.startswith("{")][-1])
+    assert d["ms_per_step"] == pytest.approx(20.0 / 4)
+    assert d["value"] == pytest.approx(128 * 128 * 4 / 20e-3)
+    assert d["clocks"]["remeasured_after"] == "hw_thermal_slowdown" and d["clocks"]["sm_mhz"] == 1960.0
+    assert d["gpu_launches"] == 12 and d["roofline"]["avg_launch_ms"] == pytest.approx(0.5)
