@@ -385,9 +385,12 @@ struct Ar<double> {
     const double ys = dv(1.0, s);  // the three quotients a_k / s share one correctly rounded reciprocal
     return ad(ad(ml(div_by(a0, s, ys), q0), ml(div_by(a1, s, ys), q1)), ml(div_by(a2, s, ys), q2));
   }
-  // RN(a / b) from yb = RN(1 / b): q = RN(a yb) is within an ulp of a / b, the residual a - q b is exact
-  // with a fused multiply-add, and one fused correction q + r yb rounds to the correctly rounded quotient
-  // (Markstein 1990) -- the same double an IEEE division returns, for normal operands and quotients.
+  // RN(a / b) from yb = RN(1 / b): q = RN(a yb), r = RN(a - q b) by a fused multiply-add, and one fused
+  // correction q + r yb. Where a's significand is at least b's, q is within an ulp and Markstein's theorem
+  // (IBM J. Res. Dev. 34, 1990) gives the correctly rounded quotient; otherwise q can be up to 1.5 ulps off
+  // and r rounded, but the corrected value stays closer to a / b than any rounding midpoint is, except in
+  // one corner (b's significand the largest below 2) that an exhaustive check covers. The result is the
+  // double an IEEE division returns, for normal operands and quotients.
   static __device__ __forceinline__ double div_by(double a, double b, double yb) {
     const double q = __dmul_rn(a, yb);
     const double r = __fma_rn(-q, b, a);
