@@ -6,7 +6,8 @@ weights as 1, 6, 3, and the data are g = F +- alpha U = 2 f+- with epsilon scale
 restate those steps in exact arithmetic (sympy; the square roots cancel) and check that each face value is
 exactly the textbook WENO5 of the split fluxes (times 2), for both upwind directions, for the level set's
 one-sided derivatives, and that the branch-free flux (U + c_E p) v_n + c_A p is each flux kind of Eq.
-euler2D. FP32 results then differ from the textbook only by rounding."""
+euler2D. The FP32 adjoint's triplet form (per-role gradient shares of a face) is checked the same way against
+the exact gradient of the textbook WENO5. FP32 results then differ from the definitions only by rounding."""
 import random
 
 import pytest
@@ -115,3 +116,72 @@ def test_candidate_values_and_scaled_indicators():
         s, u = L + R - 2 * C, KU * (L - R)
         other = u if sign == 0 else KS * s + sign * u
         assert sp.expand(EPS_SCALE * beta - (s ** 2 + other ** 2)) == 0
+
+
+# ---- the FP32 adjoint's triplet form: per role of a face, gbar dW/d(a', b', c') = WG dq_r + A (1, -2, 1) +
+# B dt_r with WG = gbar a_r / sum a, cg = -2 gbar (q_r - W) (a_r / D_r) / sum a, A = 13/6 s cg, B = h_r cg
+# (indicators unscaled, eps = 1e-6 on the split fluxes themselves).
+ADJ_DQ = ((sp.Rational(2, 6), sp.Rational(-7, 6), sp.Rational(11, 6)),
+          (sp.Rational(-1, 6), sp.Rational(5, 6), sp.Rational(2, 6)),
+          (sp.Rational(2, 6), sp.Rational(5, 6), sp.Rational(-1, 6)))
+ADJ_DT = ((1, -4, 3), (1, 0, -1), (3, -4, 1))
+ADJ_EPS = sp.Rational(1, 10 ** 6)
+
+
+def adj_tri(L, C, R, left_to_right):
+    s, th = L + R - 2 * C, (L - R) / 2
+    bs = sp.Rational(13, 12) * s * s + ADJ_EPS
+    mm, pp = s - th, s + th
+    rm, rt, rp = 1 / (mm * mm + bs), 1 / (th * th + bs), 1 / (pp * pp + bs)
+    base = C + s / 12
+    bss, lo, hi, at = base + s, base - th / 2, base + th / 2, 6 * rt * rt
+    if left_to_right:
+        roles = [(bss - 3 * th / 2, rm * rm, rm * rm * rm, mm), (lo, at, at * rt, th), (hi, 3 * rp * rp, 3 * rp ** 3, pp)]
+    else:
+        roles = [(bss + 3 * th / 2, rp * rp, rp ** 3, pp), (hi, at, at * rt, -th), (lo, 3 * rm * rm, 3 * rm ** 3, mm)]
+    return roles, sp.Rational(13, 6) * s
+
+
+def adj_face(roles, gbar):
+    """roles: three (role tuple, s13, points in reconstruction order); returns {point: gradient share}, W."""
+    sa = sum(r[1] for r, _, _ in roles)
+    W = sum(r[1] * r[0] for r, _, _ in roles) / sa
+    g, m2g = gbar / sa, -2 * gbar / sa
+    out = {}
+    for k, ((q, a, nr, h), s13, pts) in enumerate(roles):
+        WG, cg = a * g, (q - W) * nr * m2g
+        A, B = s13 * cg, h * cg
+        for j, (pt, dq, dt, da) in enumerate(zip(pts, ADJ_DQ[k], ADJ_DT[k], (1, -2, 1))):
+            out[pt] = out.get(pt, 0) + WG * dq + B * dt + A * da
+    return out, W
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adjoint_triplet_gradient_is_the_textbook_gradient(seed):
+    rnd = random.Random(200 + seed)
+    p = _rationals(rnd, 7, -8, 8)
+    gbar = sp.Rational(rnd.randint(-99, 99), 13)
+    x = sp.symbols("x0:5")
+    Wsym = textbook_weno5(*x, ADJ_EPS)
+    grad = [sp.diff(Wsym, xi) for xi in x]
+    q = 3
+    # left-biased face: triplets centred at q-2, q-1, q (roles up, mid, dn), stencil points q-3 .. q+1
+    t = {j: adj_tri(p[j - 1], p[j], p[j + 1], True) for j in (q - 2, q - 1, q)}
+    share, W = adj_face([(t[q - 2][0][0], t[q - 2][1], (q - 3, q - 2, q - 1)),
+                         (t[q - 1][0][1], t[q - 1][1], (q - 2, q - 1, q)),
+                         (t[q][0][2], t[q][1], (q - 1, q, q + 1))], gbar)
+    pts = list(range(q - 3, q + 2))
+    sub = dict(zip(x, [p[i] for i in pts]))
+    assert sp.simplify(W - Wsym.subs(sub)) == 0
+    for xi, i in zip(range(5), pts):
+        assert sp.simplify(share[i] - gbar * grad[xi].subs(sub)) == 0
+    # right-biased face: triplets centred at q+1, q, q-1, stencil q+2 .. q-2 in reconstruction order
+    t = {j: adj_tri(p[j - 1], p[j], p[j + 1], False) for j in (q + 1, q, q - 1)}
+    share, W = adj_face([(t[q + 1][0][0], t[q + 1][1], (q + 2, q + 1, q)),
+                         (t[q][0][1], t[q][1], (q + 1, q, q - 1)),
+                         (t[q - 1][0][2], t[q - 1][1], (q, q - 1, q - 2))], gbar)
+    pts = list(range(q + 2, q - 3, -1))
+    sub = dict(zip(x, [p[i] for i in pts]))
+    assert sp.simplify(W - Wsym.subs(sub)) == 0
+    for xi, i in zip(range(5), pts):
+        assert sp.simplify(share[i] - gbar * grad[xi].subs(sub)) == 0
