@@ -157,7 +157,10 @@ class Hydro:
         self.problem = problem
         self.code = _dtype_code(dtype)
         self.torch_dtype = torch.float64 if self.code == HYDRO_F64 else torch.float32
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if dev.type != "cuda":
+            raise HydroError(EINVAL, f"device must be a CUDA device, got {dev}")
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.cfg = make_config(problem, self.code)
@@ -178,6 +181,8 @@ class Hydro:
         torch = _torch()
         if not isinstance(U, torch.Tensor) or not U.is_cuda:
             raise HydroError(EINVAL, f"{name} must be a CUDA tensor")
+        if U.device != self.device:
+            raise HydroError(EINVAL, f"{name} is on {U.device}; this context runs on {self.device}")
         if U.dtype != self.torch_dtype or tuple(U.shape) != self.shape or not U.is_contiguous():
             raise HydroError(EINVAL, f"{name} must be a contiguous {self.torch_dtype} tensor of shape {self.shape}")
         return ctypes.c_void_p(U.data_ptr())
@@ -196,6 +201,13 @@ class Hydro:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     # -- entry points
     def step(self, U, nsteps: int, t: float = 0.0):
@@ -367,10 +379,14 @@ def hydro_batch_step(members: list[Hydro], states: list, nsteps: int, t=None):
     """Advance an ensemble (one context per member) with one persistent launch per stage (C ABI
     hydro_batch_step). ``t``: optional list of member times, updated and returned."""
     n = len(members)
+    if n == 0 or len(states) != n:
+        raise HydroError(EINVAL, f"hydro_batch_step: {n} members and {len(states)} states")
     lib = members[0].lib
     ctxs = (ctypes.c_void_p * n)(*[m.ctx.value for m in members])
     ptrs = (ctypes.c_void_p * n)(*[m._ptr(U).value for m, U in zip(members, states)])
-    tt = np.ascontiguousarray(np.zeros(n) if t is None else np.asarray(t, dtype=np.float64))
+    tt = np.ascontiguousarray(np.zeros(n) if t is None else np.asarray(t, dtype=np.float64).ravel())
+    if tt.size != n:
+        raise HydroError(EINVAL, f"hydro_batch_step: {tt.size} member times for {n} members")
     rc = lib.hydro_batch_step(ctxs, ptrs, n, int(nsteps), tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != OK:
         msg = lib.hydro_last_error(members[0].ctx)

@@ -57,3 +57,15 @@ def test_init_rejects_bad_configs_without_touching_the_device():
     assert lib.hydro_step(None, None, 1, None, None) == hydro.EINVAL
     lib.hydro_destroy(None)
     assert lib.hydro_last_error(None) == b"null context"
+
+
+def test_binding_rejects_bad_arguments_on_the_host():
+    """The Python binding refuses a non-CUDA device and mismatched ensemble lists before any CUDA call."""
+    from paper_1507_08549_gb300 import hydro, workloads
+    with pytest.raises(hydro.HydroError) as e:
+        hydro.Hydro(workloads.advected_wave(16), dtype="f64", device="cpu")
+    assert e.value.code == hydro.EINVAL
+    with pytest.raises(hydro.HydroError):
+        hydro.hydro_batch_step([], [], 1)
+    with pytest.raises(hydro.HydroError):
+        hydro.hydro_batch_step([object(), object()], [None], 1)
