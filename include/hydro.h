@@ -222,7 +222,10 @@ int hydro_adjoint_sweep(hydro_ctx* ctx, void* lambda);
 /* Advance nmembers independent grids (each with its own context, all of one dtype and nfields) by
  * nsteps steps: each RK stage of all members is ONE persistent kernel launch that walks a table of
  * (member, tile) work items; the three launches of a step are replayed from a CUDA graph. U[m] is
- * member m's device state, t[m] (host, may be NULL) its time. Runs on members[0]'s stream. */
+ * member m's device state, t[m] (host, may be NULL) its time. Runs on members[0]'s stream. The work table
+ * and graph are kept on members[0] and reused while the same contexts (by identity, not address) with
+ * unchanged parameters come back in the same order; any other call, or a member whose parameters changed
+ * (hydro_record, hydro_set_tile_variant, hydro_autotune), rebuilds them. */
 int hydro_batch_step(hydro_ctx* const* members, void* const* U, int nmembers, int nsteps, double* t);
 
 /* ---- tuning and timing ----------------------------------------------------------------------- */

@@ -3,6 +3,7 @@
 // replay of a step's three stage launches, batched ensembles, the tile autotuner, totals, recording
 // and the bounded host waits. All device work is issued on the context's stream.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -108,8 +109,15 @@ struct hydro_ctx {
   void* pois_host = nullptr;
   cudaGraphExec_t sor_graph = nullptr;
   cudaEvent_t sor_ev[2] = {nullptr, nullptr};
-  // batch plan (kept on the first member)
-  std::vector<hydro_ctx*> plan_members;
+  // identity of this context for batch plans: unique per process, never reused (a destroyed context's
+  // address can come back from the allocator with other buffers behind it)
+  unsigned long long uid = 0;
+  // bumped whenever the device parameters are rebuilt (log buffers, tile variant ...): a batch plan holds
+  // copies of its members' parameters and is valid only for the generations it was built from
+  unsigned long long params_gen = 0;
+  // batch plan (kept on the first member), keyed by the members' (uid, params_gen)
+  std::vector<unsigned long long> plan_members;
+  std::vector<unsigned long long> plan_gens;
   int plan_variant = -1;
   void* plan_params = nullptr;  // device GridParams[3][nmembers]
   void* plan_work = nullptr;    // device WorkItem[nwork]
@@ -256,6 +264,7 @@ static int upload_params(hydro_ctx* c) {
   build_params<real>(c, p);
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
+  ++c->params_gen;
   if (c->step_graph) {
     cudaGraphExecDestroy(c->step_graph);
     c->step_graph = nullptr;
@@ -505,7 +514,9 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   std::string why;
   int rc = validate_config(cfg, &why);
   if (rc) return rc;
+  static std::atomic<unsigned long long> next_uid{1};
   hydro_ctx* c = new hydro_ctx();
+  c->uid = next_uid.fetch_add(1);
   c->cfg = *cfg;
   c->stream = static_cast<cudaStream_t>(stream);
   c->nf = cfg->nfields;
@@ -881,7 +892,7 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     }
   }
   bool same = (int)c->plan_members.size() == n && c->plan_variant == c->variant;
-  for (int k = 0; same && k < n; ++k) same = c->plan_members[k] == m[k];
+  for (int k = 0; same && k < n; ++k) same = c->plan_members[k] == m[k]->uid && c->plan_gens[k] == m[k]->params_gen;
   if (!same) {
     if (c->plan_graph) {
       cudaGraphExecDestroy(c->plan_graph);
@@ -891,6 +902,9 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     cudaFree(c->plan_work);
     c->plan_params = nullptr;
     c->plan_work = nullptr;
+    c->plan_members.clear();  // no plan until the new one is complete (an error below leaves none)
+    c->plan_gens.clear();
+    c->plan_nwork = 0;
     std::vector<GridParams<real>> P(3 * (size_t)n);
     std::vector<WorkItem> W;
     for (int k = 0; k < n; ++k) {
@@ -922,7 +936,10 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     CK(cudaMemcpy(c->plan_params, P.data(), sizeof(GridParams<real>) * P.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->plan_work, W.data(), sizeof(WorkItem) * W.size(), cudaMemcpyHostToDevice));
     c->plan_nwork = total;
-    c->plan_members.assign(m, m + n);
+    for (int k = 0; k < n; ++k) {
+      c->plan_members.push_back(m[k]->uid);
+      c->plan_gens.push_back(m[k]->params_gen);
+    }
     c->plan_variant = c->variant;
   }
   for (int k = 0; k < n; ++k) {
