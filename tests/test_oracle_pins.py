@@ -521,3 +521,35 @@ def test_results_do_not_depend_on_thread_count():
     finally:
         oracle.set_threads(n0)
     assert np.array_equal(a, b)
+
+
+def test_totals_closed_forms():
+    """Conserved totals are sums of U_f dV, dV = dx dy (Cartesian) or 2 pi r_i dr dz (r,z): the midpoint rule
+    is exact for integrands linear in each coordinate, so fields linear in x and y (Cartesian), and fields
+    linear in z on an annulus r0 <= r <= r1 ((r,z), integrand 2 pi r (c + b z)), integrate in closed form.
+    Every field carries different coefficients, so a swapped field or coordinate fails."""
+    nx, ny, x0, x1, y0, y1 = 24, 10, -0.3, 1.1, 0.25, 0.9
+    X, Y = np.meshgrid(wl.centres(nx, x0, x1), wl.centres(ny, y0, y1))
+    coeffs = [(1.0, 0.5, -0.25), (-2.0, 0.1, 0.3), (0.7, -1.0, 0.0), (3.0, 0.0, 2.0), (-0.4, 0.2, 0.6)]
+    U = np.stack([c + a * X + b * Y for c, a, b in coeffs])
+    p = wl.Problem(name="totals", nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, nfields=5,
+                   bc=(wl.TRANSMISSIVE,) * 4, U0=U)
+    out = oracle.totals(p, U)
+    area, xm, ym = (x1 - x0) * (y1 - y0), 0.5 * (x0 + x1), 0.5 * (y0 + y1)
+    for f, (c, a, b) in enumerate(coeffs):
+        assert out[f] == pytest.approx(area * (c + a * xm + b * ym), rel=1e-13, abs=1e-14), f
+    out4 = oracle.totals(p.with_(nfields=4, U0=U[:4]), np.ascontiguousarray(U[:4]))
+    assert np.array_equal(out4[:4], out[:4]) and out4[4] == 0.0
+
+    for r0, r1, bc in ((0.0, 0.5, (wl.AXIS, wl.TRANSMISSIVE, wl.TRANSMISSIVE, wl.TRANSMISSIVE)),
+                       (0.2, 0.7, (wl.TRANSMISSIVE,) * 4)):
+        nr, nz, z0, z1 = 16, 12, -0.4, 0.8
+        R, Z = np.meshgrid(wl.centres(nr, r0, r1), wl.centres(nz, z0, z1))
+        rz_coeffs = [(1.5, 0.0), (0.0, 1.0), (-0.5, 2.0), (2.5, -1.0), (0.25, 0.5)]
+        U = np.stack([c + b * Z for c, b in rz_coeffs])
+        p = wl.Problem(name="totals_rz", nx=nr, ny=nz, x0=r0, x1=r1, y0=z0, y1=z1, geometry=1, nfields=5,
+                       bc=bc, U0=U)
+        out = oracle.totals(p, U)
+        vol, zm = math.pi * (r1 * r1 - r0 * r0) * (z1 - z0), 0.5 * (z0 + z1)
+        for f, (c, b) in enumerate(rz_coeffs):
+            assert out[f] == pytest.approx(vol * (c + b * zm), rel=1e-13, abs=1e-14), (r0, f)
