@@ -243,6 +243,28 @@ def test_cfl_and_alpha_definitions():
     assert oracle.dt(prob, U) == pytest.approx(0.4 * prob.dx / np.max(c + np.abs(u) + np.abs(v)), rel=1e-15)
 
 
+def test_alpha_and_dt_on_a_designed_state():
+    """rho = gamma p makes the sound speed exactly 1. Three marked cells: |u| + c = 4 (the largest in x),
+    |v| + c = 6 (the largest in y) and c + |u| + |v| = 6.5 (the largest for the CFL condition, with the
+    paper's single Delta = min(dx, dy)). Non-square cells either way round and two gammas, so swapping x
+    and y, |u| and |v|, or dx and dy, fails."""
+    for gamma in (1.4, 5.0 / 3.0):
+        for (nx, ny, y1) in ((20, 12, 0.9), (12, 20, 0.3)):
+            rho = np.full((ny, nx), gamma)
+            u = np.zeros((ny, nx))
+            v = np.zeros((ny, nx))
+            u[3, 4] = 3.0                       # |u| + c = 4
+            v[7, 9] = -5.0                      # |v| + c = 6
+            u[9, 2], v[9, 2] = 2.5, -3.0        # c + |u| + |v| = 6.5 (|u| + c = 3.5, |v| + c = 4)
+            prob = wl.Problem(name="speeds", nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=y1, gamma=gamma, cfl=0.37,
+                              bc=(wl.TRANSMISSIVE,) * 4)
+            U = wl.conserved(gamma, rho, u, v, 1.0)
+            ax, ay = oracle.alpha(prob, U)
+            assert ax == pytest.approx(4.0, rel=1e-14) and ay == pytest.approx(6.0, rel=1e-14)
+            delta = min(1.0 / nx, y1 / ny)
+            assert oracle.dt(prob, U) == pytest.approx(0.37 * delta / 6.5, rel=1e-14)
+
+
 # ------------------------------------------------------------------------------------- symmetries
 
 def test_blast_mirror_symmetry_bitwise():
