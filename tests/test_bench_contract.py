@@ -151,3 +151,28 @@ def test_forward_path_times_again_after_a_rejected_clock_record(monkeypatch, cap
     assert d["value"] == pytest.approx(128 * 128 * 4 / 20e-3)
     assert d["clocks"]["remeasured_after"] == "hw_thermal_slowdown" and d["clocks"]["sm_mhz"] == 1960.0
     assert d["gpu_launches"] == 12 and d["roofline"]["avg_launch_ms"] == pytest.approx(0.5)
+
+
+def test_alu_roofline_arithmetic(monkeypatch):
+    """The FP32 stage kernel's roofline: algorithmic operations per launch (operations per cell and stage
+    times cells) over the launch time, against 152 SMs x 128 FP32 lanes x the sampled SM clock; the HBM
+    roofline comes along as the second object."""
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+
+    class Props:
+        multi_processor_count = 152
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: Props())
+    cells, ms = 8192 * 8192, 3.72
+    alu, hbm = bench.roofline(5, 4, cells, ms, sm_mhz=2070.0, alu=True, traffic=3.4664e9)
+    ops = bench.alg_ops_per_cell_stage(5) * cells
+    assert alu["bound"] == "alu" and alu["alg_ops_per_launch"] == pytest.approx(ops)
+    assert alu["achieved"] == pytest.approx(ops / (ms * 1e-3) / 1e12)
+    assert alu["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)
+    assert alu["frac"] == pytest.approx(alu["achieved"] / alu["peak"])
+    assert 0.3 < alu["frac"] < 0.4  # the measured launch time of the 8192^2 blobs + blast stage
+    assert alu["traffic"] == hbm["traffic"] == 3.4664e9
+    assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(8 * 5 * 4 * cells / 3 / (ms * 1e-3) / 1e9 / hbm["peak"])
