@@ -575,3 +575,16 @@ def test_totals_closed_forms():
         vol, zm = math.pi * (r1 * r1 - r0 * r0) * (z1 - z0), 0.5 * (z0 + z1)
         for f, (c, b) in enumerate(rz_coeffs):
             assert out[f] == pytest.approx(vol * (c + b * zm), rel=1e-13, abs=1e-14), (r0, f)
+
+
+def test_input_noise_generator_is_splitmix64():
+    """The per-cell noise of the synthetic inputs is SplitMix64 (Steele, Lea & Flood 2014) applied to
+    seed ^ index. The published generator seeded with 0 starts 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4,
+    0x06c45d188009454f; its k-th output is the output function at the counter k * gamma."""
+    gamma = 0x9E3779B97F4A7C15
+    counters = np.array([0, gamma, (2 * gamma) % (1 << 64)], dtype=np.uint64)
+    assert [int(z) for z in wl.splitmix64(counters)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = wl.uniform_cells(wl.DEFAULT_SEED, 4096, -2.0, 3.0)
+    assert u.min() >= -2.0 and u.max() < 3.0 and abs(u.mean() - 0.5) < 0.1
+    top53 = wl.splitmix64(np.arange(4096, dtype=np.uint64) ^ np.uint64(wl.DEFAULT_SEED)) >> np.uint64(11)
+    np.testing.assert_array_equal(u, -2.0 + 5.0 * (top53.astype(np.float64) / 2.0 ** 53))
