@@ -176,3 +176,13 @@ def test_alu_roofline_arithmetic(monkeypatch):
     assert 0.3 < alu["frac"] < 0.4  # the measured launch time of the 8192^2 blobs + blast stage
     assert alu["traffic"] == hbm["traffic"] == 3.4664e9
     assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(8 * 5 * 4 * cells / 3 / (ms * 1e-3) / 1e9 / hbm["peak"])
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun the reference arm's other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "advected_wave_128", "--steps", "2", "--warmup", "3"], capture_output=True, text=True,
+                       cwd=ROOT, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
