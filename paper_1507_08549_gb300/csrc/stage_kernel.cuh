@@ -252,9 +252,6 @@ struct Ar<float> {
     v = my * rr;
     p = gm1 * T::fma_(-0.5f, T::add_(T::mul_(mx, u), T::mul_(my, v)), E);
   }
-  static __device__ __forceinline__ float flux(int kind, float uu, float X, float vn, float p) {
-    return kind == 0 ? X : (kind == 1) ? T::fma_(uu, vn, p) : (kind == 2) ? T::mul_(uu, vn) : T::mul_(uu + p, vn);
-  }
   static __device__ __forceinline__ void split(float F, float uu, float alpha, float& fp, float& fm) {
     const float hF = 0.5f * F, hal = 0.5f * alpha;
     fp = T::fma_(hal, uu, hF);
