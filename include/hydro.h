@@ -87,7 +87,7 @@ void hydro_destroy(hydro_ctx* ctx);
 /* Message of the last failure on this context ("" if none). Valid until the next call on ctx. */
 const char* hydro_last_error(hydro_ctx* ctx);
 
-/* Rebind the context to another stream. */
+/* Rebind the context to another stream (interface plumbing; no counterpart in the paper). */
 int hydro_set_stream(hydro_ctx* ctx, void* stream);
 
 /* Advance U (device, [nfields][ny][nx], caller-owned) by nsteps SSP-RK3 steps in place (Sec. 2.1).
@@ -98,19 +98,21 @@ int hydro_set_stream(hydro_ctx* ctx, void* stream);
  * rho <= 0 or p <= 0 (U then holds the state of the failing step). Synchronises the stream. */
 int hydro_step(hydro_ctx* ctx, void* U, int nsteps, double* t_inout, double* dt_last);
 
-/* Same as hydro_step for a state in HOST memory, on the context's stream. Pinned (page-locked) memory is
+/* Same as hydro_step (the update of Sec. 2.1) for a state in HOST memory, on the context's stream. Pinned (page-locked) memory is
  * used in place: the kernel that builds the padded working state reads it over the host link, and the
  * last stage of the last step runs in row bands while a second stream of the context copies each finished
  * band back into it (copy engine, overlapped with the next band). Pageable memory is copied to a device
  * buffer, stepped and copied back. */
 int hydro_step_host(hydro_ctx* ctx, void* U_host, int nsteps, double* t_inout, double* dt_last);
 
-/* Spatial operator L(U) = -(dF/dx + dG/dy) + S(U) and the level-set right-hand side -H_hat, with the
- * Lax-Friedrichs speeds given (not computed): L is a device array shaped like U. Asynchronous. */
+/* Spatial operator L(U) = -(dF/dx + dG/dy) + S(U) of Eq. euler2D (Sec. 2.1) and the level-set right-hand
+ * side -H_hat (Sec. 2.2), with the Lax-Friedrichs speeds given (not computed): L is a caller-owned device
+ * array shaped like U. Asynchronous. */
 int hydro_rhs(hydro_ctx* ctx, const void* U, double alpha_x, double alpha_y, void* L);
 
 /* Conserved totals sum_cells U_f dV (f = 0..4; dV = dx dy, or 2 pi r_i dr dz in (r,z)) of a device
- * state, accumulated in FP64 in a fixed order (bitwise repeatable). out[4] is 0 when nfields = 4.
+ * state -- the mass and energy whose relative changes the Gresho test reports (Sec. 5.2) -- accumulated
+ * in FP64 in a fixed order (bitwise repeatable); out is a host array of 5. out[4] is 0 when nfields = 4.
  * Synchronises the stream. */
 int conserved_totals(hydro_ctx* ctx, const void* U, double out[5]);
 
@@ -190,17 +192,22 @@ int hydro_poisson(hydro_ctx* ctx, const void* U, double G, double omega, double 
 int hydro_exact_sum(hydro_ctx* ctx, const double* x, long long n, double* out);
 
 /* ---- recording and the discrete adjoint (frozen alpha and dt) ---------------------------------
- * alpha_x, alpha_y and dt are maxima/minima over the grid and have no derivative; the adjoint and the
- * finite-difference checks freeze them at the values the forward run used. */
+ * The paper has no adjoint: these entry points are the exact discrete adjoint (reverse mode) of the
+ * component-wise update of Sec. 2.1 / 2.2 as this library computes it. alpha_x, alpha_y and dt are
+ * maxima/minima over the grid and have no derivative; the adjoint and the finite-difference checks
+ * freeze them at the values the forward run used. The characteristic scheme has no adjoint here:
+ * HYDRO_EINVAL on such a context. lambda arrays are caller-owned device arrays shaped like U. */
 
 /* Start recording: the next steps log dt (one double per step) and the stage alphas (six doubles per
  * step) for up to max_steps steps. max_steps = 0 stops recording and frees the log. */
 int hydro_record(hydro_ctx* ctx, int max_steps);
 /* Copy the first n logged entries to host arrays dt_log[n], alpha_log[6n]. Returns the number of
- * steps recorded so far through *n_recorded (may be NULL). */
+ * steps recorded so far through *n_recorded (may be NULL). HYDRO_EINVAL for n beyond the recorded
+ * count or null arrays with n > 0. Synchronises the stream. */
 int hydro_get_log(hydro_ctx* ctx, int n, double* dt_log, double* alpha_log, int* n_recorded);
 
-/* Forward map with dt and stage alphas frozen at host-given values (nsteps entries / 6*nsteps). */
+/* Forward map (Sec. 2.1) with dt and stage alphas frozen at host-given values (nsteps entries /
+ * 6*nsteps host doubles). HYDRO_EINVAL for null arrays with nsteps > 0. */
 int hydro_step_frozen(hydro_ctx* ctx, void* U, int nsteps, const double* dt_log, const double* alpha_log);
 
 /* Discrete adjoint of one frozen SSP-RK3 step: lambda (device, shaped like U) holds dJ/dU^{n+1} on
@@ -214,23 +221,28 @@ int hydro_adjoint_step(hydro_ctx* ctx, const void* U_n, void* lambda, double dt,
 int hydro_forward_checkpointed(hydro_ctx* ctx, void* U, int nsteps, int checkpoint_every);
 /* Reverse sweep over the last checkpointed forward run: lambda holds dJ/dU^N on entry and dJ/dU^0 on
  * exit. Segments are recomputed from their checkpoints (two-level checkpointing); the stored run is
- * kept, so the sweep may be repeated for another lambda. */
+ * kept, so the sweep may be repeated for another lambda. HYDRO_ESTATE when no checkpointed run exists. */
 int hydro_adjoint_sweep(hydro_ctx* ctx, void* lambda);
 
 /* ---- batched ensembles ------------------------------------------------------------------------ */
 
 /* Advance nmembers independent grids (each with its own context, all of one dtype and nfields) by
- * nsteps steps: each RK stage of all members is ONE persistent kernel launch that walks a table of
+ * nsteps steps of the update of Sec. 2.1 (each member its own alphas and dt): each RK stage of all members is ONE persistent kernel launch that walks a table of
  * (member, tile) work items; the three launches of a step are replayed from a CUDA graph. U[m] is
  * member m's device state, t[m] (host, may be NULL) its time. Runs on members[0]'s stream. The work table
  * and graph are kept on members[0] and reused while the same contexts (by identity, not address) with
  * unchanged parameters come back in the same order; any other call, or a member whose parameters changed
- * (hydro_record, hydro_set_tile_variant, hydro_autotune), rebuilds them. */
+ * (hydro_record, hydro_set_tile_variant, hydro_autotune), rebuilds them. HYDRO_EINVAL when members differ
+ * in dtype, nfields or device, or use the characteristic scheme; a member's non-physical state or device
+ * timeout is reported with its index in hydro_last_error(members[0]). Synchronises the stream. */
 int hydro_batch_step(hydro_ctx* const* members, void* const* U, int nmembers, int nsteps, double* t);
 
-/* ---- tuning and timing ----------------------------------------------------------------------- */
+/* ---- tuning and timing ------------------------------------------------------------------------
+ * Performance plumbing with no counterpart in the paper; results of the update do not depend on the
+ * tile variant (bitwise). */
 
-/* Number of tile variants and the current one; select a variant (0 .. n-1) for this context. */
+/* Number of tile variants and the current one; select a variant (0 .. n-1) for this context
+ * (HYDRO_EINVAL for no such variant or one that does not fit on the device). */
 int hydro_tile_variants(hydro_ctx* ctx, int* n, int* current);
 int hydro_set_tile_variant(hydro_ctx* ctx, int variant);
 /* Describe a variant: tile width and height in cells, threads per CTA, shared memory bytes. */
