@@ -69,3 +69,19 @@ def test_binding_rejects_bad_arguments_on_the_host():
         hydro.hydro_batch_step([], [], 1)
     with pytest.raises(hydro.HydroError):
         hydro.hydro_batch_step([object(), object()], [None], 1)
+
+
+def test_every_entry_point_is_documented():
+    """Each declaration in include/hydro.h sits under a comment block (one block may describe a pair of
+    related calls declared together)."""
+    lines = open(os.path.join(ROOT, "include", "hydro.h")).read().split("\n")
+    decl = re.compile(r"^\s*(?:[A-Za-z_][\w ]*?[\s\*]+)?((?:hydro_|conserved_totals)\w*)\s*\(")
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m or line.lstrip().startswith(("*", "/*")):
+            continue
+        j = i - 1
+        while j >= 0 and not lines[j].rstrip().endswith("*/"):
+            assert i - j <= 3, f"{m.group(1)} has no comment above it"
+            j -= 1
+        assert j >= 0, m.group(1)
