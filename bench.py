@@ -168,13 +168,19 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def crop(prob, cap: int):
+    """The first min(cap, ny) rows and min(cap, nx) columns of a workload's state as a problem of their
+    own (same spacing, generator and physics; the crop's faces keep the workload's boundary kinds)."""
+    nx, ny = min(cap, prob.nx), min(cap, prob.ny)
+    return prob.with_(nx=nx, ny=ny, x1=prob.x0 + nx * prob.dx, y1=prob.y0 + ny * prob.dy,
+                      U0=np.ascontiguousarray(prob.U0[:, :ny, :nx]))
+
+
 def cpu_baseline(prob, seconds: float = 10.0):
-    """Time the FP64 oracle, as it stands, on all host cores on a 2048 x 2048 crop of the workload
-    (same generator, same physics; periodic crop) until about `seconds` of wall time are spent."""
+    """Time the FP64 oracle, as it stands, on all host cores on a crop of at most 2048 x 2048 cells of
+    the workload until about `seconds` of wall time are spent."""
     import oracle
-    n = min(2048, prob.nx)
-    sub = prob.with_(nx=n, ny=n, x1=prob.x0 + n * prob.dx, y1=prob.y0 + n * prob.dy,
-                     U0=np.ascontiguousarray(prob.U0[:, :n, :n]))
+    sub = crop(prob, 2048)
     oracle.build()
     U = sub.U0
     steps, t0 = 0, time.perf_counter()
@@ -184,8 +190,8 @@ def cpu_baseline(prob, seconds: float = 10.0):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": n * n * steps / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{n}x{n} crop of the workload, {steps} FP64 RK3 steps, {el:.1f} s wall"}
+    return {"value": sub.cells * steps / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{sub.nx}x{sub.ny} crop of the workload, {steps} FP64 RK3 steps, {el:.1f} s wall"}
 
 
 def run_reference(args):
@@ -197,9 +203,7 @@ def run_reference(args):
         prob = max(prob, key=lambda q: q.cells)
     # each reference "step" is one oracle step of the crop; warm-up steps are untimed
     import oracle
-    n = min(1024, prob.nx)
-    sub = prob.with_(nx=n, ny=n, x1=prob.x0 + n * prob.dx, y1=prob.y0 + n * prob.dy,
-                     U0=np.ascontiguousarray(prob.U0[:, :n, :n]))
+    sub = crop(prob, 1024)
     oracle.build()
     U = sub.U0
     for _ in range(args.warmup):
@@ -208,13 +212,13 @@ def run_reference(args):
     for _ in range(args.steps):
         U, _, _ = oracle.step(sub, U, 1)
     el = time.perf_counter() - t0
-    value = n * n * args.steps / el
+    value = sub.cells * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": f"{n}x{n} crop", "cells": n * n},
+            "config": {"workload": args.workload, "sample": f"{sub.nx}x{sub.ny} crop", "cells": sub.cells},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-                             "sample": f"{n}x{n} crop of {args.workload}, {args.steps} FP64 RK3 steps"},
+                             "sample": f"{sub.nx}x{sub.ny} crop of {args.workload}, {args.steps} FP64 RK3 steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -186,3 +186,18 @@ def test_reference_arm_runs_on_rank_zero_only():
                        cwd=ROOT, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_crop_keeps_rows_and_columns_apart():
+    """The oracle legs time a crop of the workload; a grid with fewer rows than columns keeps its rows."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1507_08549_gb300 import workloads as wl
+    p = wl.advected_wave(24, ny=10)
+    sub = bench.crop(p, 16)
+    assert (sub.nx, sub.ny) == (16, 10) and sub.U0.shape == (4, 10, 16)
+    assert sub.dx == p.dx and sub.dy == p.dy and sub.cells == 160
+    oracle.step(sub, sub.U0, 1)  # a consistent problem the oracle accepts
+    line = bench.cpu_baseline(p.with_(nx=24, ny=10), seconds=0.05)
+    assert line["kind"] == "oracle" and line["sample"].startswith("24x10 crop")
