@@ -85,3 +85,21 @@ def test_every_entry_point_is_documented():
             assert i - j <= 3, f"{m.group(1)} has no comment above it"
             j -= 1
         assert j >= 0, m.group(1)
+
+
+def test_context_manager_destroys_the_context_once():
+    from paper_1507_08549_gb300 import hydro
+
+    class Lib:
+        destroyed = []
+
+        def hydro_destroy(self, ctx):
+            Lib.destroyed.append(ctx.value)
+
+    h = hydro.Hydro.__new__(hydro.Hydro)
+    h.lib, h.ctx = Lib(), ctypes.c_void_p(0x1234)
+    with h as inside:
+        assert inside is h
+    assert Lib.destroyed == [0x1234] and not h.ctx.value
+    h.close()
+    assert Lib.destroyed == [0x1234]
