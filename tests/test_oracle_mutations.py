@@ -37,6 +37,18 @@ MUTATIONS = [
      "two_pi * (c->x0 + (i + 1.0) * dx) * dx * dy", "test_oracle_pins.py", "totals_closed_forms"),
     ("front_point_spacing", "hydro_oracle_reinit.inc", "px[m] = xa + dx * (a / (a - b));",
      "px[m] = xa + dy * (a / (a - b));", "test_oracle_reinit.py", "tilted_front_on_unequal_spacing"),
+    ("poisson_east_west", "hydro_oracle_poisson.inc", "aE = rp / (r * dr * dr), aW = rm / (r * dr * dr)",
+     "aE = rm / (r * dr * dr), aW = rp / (r * dr * dr)", "test_oracle_poisson.py", "uniform_sphere_potential"),
+    ("poisson_mirror_mass", "hydro_oracle_poisson.inc", "const double M = zsym ? 2.0 * mass : mass;",
+     "const double M = mass;", "test_oracle_poisson.py", "reflecting_plane_matches_mirrored_full_domain"),
+    ("roe_average_weights", "hydro_oracle_char.inc", "const double un = (s[0] * vn[0] + s[1] * vn[1]) / den;",
+     "const double un = (s[1] * vn[0] + s[0] * vn[1]) / den;", "test_oracle_char.py", "roe_eigen_system"),
+    ("left_eigenvector_sign", "hydro_oracle_char.inc", "{1.0 - b2, b1 * un, b1 * ut, -b1},",
+     "{1.0 + b2, b1 * un, b1 * ut, -b1},", "test_oracle_char.py", "roe_eigen_system"),
+    ("adjoint_indicator_derivative", "hydro_oracle_adjoint.inc", "const double dbeta = 13.0 / 6.0 * sk[k]",
+     "const double dbeta = 13.0 / 12.0 * sk[k]", "test_oracle_adjoint.py", "weno5_gradient_matches_finite_differences"),
+    ("adjoint_gravity_term", "hydro_oracle_adjoint.inc", "g[0] += c->gravity * mu[2 * n + k];",
+     "g[0] += c->gravity * mu[3 * n + k];", "test_oracle_adjoint.py", "rhs_adjoint_dot_product"),
 ]
 
 
