@@ -49,6 +49,10 @@ MUTATIONS = [
      "const double dbeta = 13.0 / 12.0 * sk[k]", "test_oracle_adjoint.py", "weno5_gradient_matches_finite_differences"),
     ("adjoint_gravity_term", "hydro_oracle_adjoint.inc", "g[0] += c->gravity * mu[2 * n + k];",
      "g[0] += c->gravity * mu[3 * n + k];", "test_oracle_adjoint.py", "rhs_adjoint_dot_product"),
+    ("blend_offset", "hydro_oracle_reinit.inc", "const double d0 = 3.0 * delta, w = delta / 3.0;",
+     "const double d0 = 2.0 * delta, w = delta / 3.0;", "test_oracle_reinit.py", "blend_weight_properties"),
+    ("roche_sign", "hydro_oracle_poisson.inc", "{ return -grav_const * M / sqrt(r * r + z * z); }",
+     "{ return grav_const * M / sqrt(r * r + z * z); }", "test_oracle_poisson.py", "uniform_sphere_potential"),
 ]
 
 
