@@ -131,9 +131,14 @@ int hydro_last_totals(hydro_ctx* ctx, double out[5]);
  * array of dtype; the domain (x0, x1, y0, y1) and geometry give dV; out is a host array of 5.
  * Scratch: a file-scope device array of 16384 x 5 + 5 doubles (655 KB) that every GPU loading the
  * library keeps until the process exits; hence ny <= 16384, else HYDRO_ESIZE (nothing launched).
- * The first call on a device looks up that array's device address; make that first call before any
- * CUDA stream capture. All calls share the array: calls that overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller. Runs on `stream` and synchronises it. */
+ * Every call looks up that array's address in the current context (cheap once the module is loaded).
+ * With lazy module loading (the CUDA default) the FIRST call in a context loads the library's device
+ * code, and the driver places the array then: a caller that must not allocate at all makes one
+ * warm-up call beforehand, outside its hook (or sets CUDA_MODULE_LOADING=EAGER). The call cannot be
+ * used during stream capture: it reads the result back and synchronises the stream. All calls share
+ * the array: calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. An error already pending in the calling thread's CUDA state is left in
+ * place and reported as HYDRO_ECUDA without launching. Runs on `stream` and synchronises it. */
 int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dtype, int geometry, double x0,
                              double x1, double y0, double y1, void* stream, double out[5]);
 

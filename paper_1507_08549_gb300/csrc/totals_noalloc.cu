@@ -11,20 +11,14 @@
 // order inside each row), then a fixed-order sum over rows, so a result is bitwise repeatable.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/hydro.h"
 
 namespace {
 
 constexpr int kMaxRows = 16384;  // ny limit: one 5-double partial per row
-constexpr int kMaxDevices = 64;
 
 // per-row partials [kMaxRows][5] followed by the 5 totals
 static __device__ __align__(256) double g_totals_scratch[kMaxRows * 5 + 5];
-
-std::mutex g_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
 
 template <typename real, int NF>
 __global__ void __launch_bounds__(256) row_partials_kernel(const real* __restrict__ U, int nx, int ny,
@@ -70,17 +64,14 @@ __global__ void row_sum_kernel(const double* __restrict__ rows, int ny, double* 
   }
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current device's current context. Looked up on every
+// call: the module (and with it the array) is placed anew when a context is recreated (after
+// cudaDeviceReset, or under another driver-API context), so a cached address could be stale. After
+// the module's first load the lookup allocates nothing.
 int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HYDRO_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_totals_scratch) != cudaSuccess) return HYDRO_ECUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_totals_scratch) != cudaSuccess || !p) return HYDRO_ECUDA;
+  *out = static_cast<double*>(p);
   return HYDRO_OK;
 }
 
@@ -92,9 +83,10 @@ int run(const real* U, int nx, int ny, int nfields, int geometry, double x0, dou
     row_partials_kernel<real, 5><<<blocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, rows);
   else
     row_partials_kernel<real, 4><<<blocks, 256, 0, s>>>(U, nx, ny, geometry, x0, dx, dy, rows);
+  if (cudaPeekAtLastError() != cudaSuccess) return HYDRO_ECUDA;
   double* res = rows + kMaxRows * 5;
   row_sum_kernel<<<1, 32, 0, s>>>(rows, ny, res);
-  if (cudaGetLastError() != cudaSuccess) return HYDRO_ECUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return HYDRO_ECUDA;
   if (cudaMemcpyAsync(out, res, 5 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HYDRO_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return HYDRO_ECUDA;
   return HYDRO_OK;
@@ -108,6 +100,9 @@ int conserved_totals_noalloc(const void* U, int nx, int ny, int nfields, int dty
       (geometry != 0 && geometry != 1) || !(x1 > x0) || !(y1 > y0))
     return HYDRO_EINVAL;
   if (ny > kMaxRows) return HYDRO_ESIZE;
+  // an error left pending by the caller's own earlier work is not this call's: refuse without
+  // launching and without consuming it, so the caller still sees it
+  if (cudaPeekAtLastError() != cudaSuccess) return HYDRO_ECUDA;
   double* rows = nullptr;
   int rc = scratch_address(&rows);
   if (rc) return rc;

@@ -359,17 +359,27 @@ def conserved_totals_noalloc(problem, U, stream=None) -> np.ndarray:
     """Totals of a CUDA tensor state through the allocation-free, context-free C entry point (for
     callers that cannot allocate device memory; see include/hydro.h)."""
     torch = _torch()
-    lib = load()
-    code = HYDRO_F64 if U.dtype == torch.float64 else HYDRO_F32
+    # everything the kernel will read is checked on the host first: a smaller or narrower tensor would
+    # otherwise be read past its end
+    if not isinstance(U, torch.Tensor):
+        raise HydroError(EINVAL, "U must be a torch tensor")
+    if U.dtype not in (torch.float32, torch.float64):
+        raise HydroError(EINVAL, f"U must be float32 or float64, got {U.dtype}")
+    shape = (int(problem.nfields), int(problem.ny), int(problem.nx))
+    if tuple(U.shape) != shape:
+        raise HydroError(EINVAL, f"U has shape {tuple(U.shape)}, the problem needs {shape}")
     if not U.is_cuda or not U.is_contiguous():
         raise HydroError(EINVAL, "U must be a contiguous CUDA tensor")
-    s = stream if stream is not None else torch.cuda.current_stream(U.device)
+    code = HYDRO_F64 if U.dtype == torch.float64 else HYDRO_F32
+    lib = load()
     out = np.zeros(5)
-    rc = lib.conserved_totals_noalloc(ctypes.c_void_p(U.data_ptr()), int(problem.nx), int(problem.ny),
-                                      int(problem.nfields), code, int(problem.geometry), float(problem.x0),
-                                      float(problem.x1), float(problem.y0), float(problem.y1),
-                                      ctypes.c_void_p(s.cuda_stream),
-                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    with torch.cuda.device(U.device):  # the scratch address is looked up in the current device's context
+        s = stream if stream is not None else torch.cuda.current_stream(U.device)
+        rc = lib.conserved_totals_noalloc(ctypes.c_void_p(U.data_ptr()), int(problem.nx), int(problem.ny),
+                                          int(problem.nfields), code, int(problem.geometry), float(problem.x0),
+                                          float(problem.x1), float(problem.y0), float(problem.y1),
+                                          ctypes.c_void_p(s.cuda_stream),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != OK:
         raise HydroError(rc, "conserved_totals_noalloc")
     return out

@@ -103,3 +103,22 @@ def test_context_manager_destroys_the_context_once():
     assert Lib.destroyed == [0x1234] and not h.ctx.value
     h.close()
     assert Lib.destroyed == [0x1234]
+
+
+def test_noalloc_wrapper_refuses_bad_tensors_before_any_launch():
+    """The allocation-free totals wrapper checks dtype and shape on the host: a half-precision or a
+    smaller tensor would otherwise be read past its end by the kernel."""
+    import torch
+    from paper_1507_08549_gb300 import hydro, workloads
+    p = workloads.advected_wave(16)
+    for U in (torch.zeros((4, 16, 16), dtype=torch.float16),
+              torch.zeros((4, 16, 16), dtype=torch.bfloat16),
+              torch.zeros((4, 16, 16), dtype=torch.int32),
+              torch.zeros((4, 16, 15), dtype=torch.float32),
+              torch.zeros((3, 16, 16), dtype=torch.float64),
+              torch.zeros(4 * 16 * 16, dtype=torch.float32)):
+        with pytest.raises(hydro.HydroError) as e:
+            hydro.conserved_totals_noalloc(p, U)
+        assert e.value.code == hydro.EINVAL
+    with pytest.raises(hydro.HydroError):  # right dtype and shape, but not on a CUDA device
+        hydro.conserved_totals_noalloc(p, torch.zeros((4, 16, 16), dtype=torch.float32))
