@@ -224,28 +224,62 @@ def run_reference(args):
     return 0
 
 
-# Measured DRAM traffic of the stage kernel, from an ncu capture of the three stage launches of one RK3 step
-# of the 4096^2 blobs + blast case (dram__bytes_read.sum + dram__bytes_write.sum: 643.2, 986.7 and 969.9 MB
-# for 16.78 M cells; algorithmic 671.1, 1006.6 and 1006.6 MB), as the per-launch average per cell, scaled to
-# a launch by cells processed; None for other states (set to None whenever the stage kernel changes).
-TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 = (643.16e6 + 986.71e6 + 969.93e6) / 3.0 / (4096 * 4096)
+# Measured DRAM traffic of the stage kernel (dram__bytes_read.sum + dram__bytes_write.sum from one ncu
+# capture, averaged over the three stage launches of one RK3 step, per cell), valid only for the kernel
+# source it was captured on: `stage_traffic_per_cell` returns None once stage_kernel.cuh has changed
+# (its SHA-256 differs from the one recorded here).
+STAGE_TRAFFIC = {"stage_kernel_sha256": None, "bytes_per_cell_launch_f32_nf5": None, "capture": None}
 
-# FP32 arithmetic operations the stage performs per cell (one per rounded operation, a fused multiply-add
-# counted once), from the kernel's arithmetic with its sharing in place and the line halos included. A
-# 15-cell hydro line (one component, one direction): 21 points x 5 (flux 3, split 2), 36 point triplets
-# x 23 (smoothness data, weights and candidate values of one reconstruction direction), 16 faces x 15
-# (two weighted sums of 7 and their sum), 15 differences x 2, and the y pass's accumulation (7.5 per
-# line on average): 1210.5 ops, 80.7 per cell, 8 lines per cell. A level-set line: 20 differences x 2,
-# 18 triplets x 25 (shared by both one-sided derivatives), 15 cells x 14: 700 ops, 46.7 per cell, 2 lines.
-# Primitives 12.3 per cell (halo included); the cell phase 61 with the level-set Hamiltonian, 40 without.
-def alg_ops_per_cell_stage(F):
+
+def stage_kernel_sha256() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_1507_08549_gb300", "csrc", "stage_kernel.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def stage_traffic_per_cell():
+    """Measured bytes per cell and stage launch of the current stage kernel source, else None."""
+    if STAGE_TRAFFIC["bytes_per_cell_launch_f32_nf5"] is None:
+        return None
+    if stage_kernel_sha256() != STAGE_TRAFFIC["stage_kernel_sha256"]:
+        return None
+    return STAGE_TRAFFIC["bytes_per_cell_launch_f32_nf5"]
+
+
+# FP32 arithmetic operations per cell and RK stage (one per rounded operation, a fused multiply-add counted
+# once). Per cell, one hydro component and one direction (the method: one point's flux and split, that
+# point's two triplets -- one per reconstruction direction -- and one face): flux 3 + split 2, 2 triplets x 23
+# (smoothness data, weights and candidate values of one reconstruction direction), one face x 15 (two weighted
+# sums of 7 and their sum), one difference x 2, and half an accumulation (the y pass adds to the x pass's
+# value): 68.5 ops, 8 such lines per cell (4 components, 2 directions). The level set per direction: one
+# difference x 2, one triplet x 25 (shared by both one-sided derivatives), one cell x 14: 41 ops, 2 directions.
+# Primitives of the cell: 8 ops. The cell phase (sources, RK blend, next stage's speeds, totals): 61 ops with
+# the level-set Hamiltonian, 40 without.
+METHOD_HYDRO_LINE_CELL = 5 + 2 * 23 + 15 + 2 + 0.5
+METHOD_PHI_LINE_CELL = 2 + 25 + 14
+METHOD_PRIMS_CELL = 8.0
+
+
+def method_ops_per_cell_stage(F):
+    """The method's own operation count per cell and stage (no tile or line halos)."""
+    return 8 * METHOD_HYDRO_LINE_CELL + METHOD_PRIMS_CELL + (2 * METHOD_PHI_LINE_CELL + 61.0 if F == 5 else 40.0)
+
+
+# What the kernel spends, its line halos included: a 15-cell line reads 21 points and forms 36 triplets
+# (18 per reconstruction direction) and 16 faces, so a hydro line costs 21 x 5 + 36 x 23 + 16 x 15 + 15 x 2
+# + 7.5 = 1210.5 ops (80.7 per cell) and a level-set line 20 x 2 + 18 x 25 + 15 x 14 = 700 (46.7 per cell);
+# the primitives are formed on the halo box (12.3 per cell).
+def kernel_ops_per_cell_stage(F):
     return 8 * 80.7 + 12.3 + (2 * 46.7 + 61.0 if F == 5 else 40.0)
 
 
 def roofline(F, B, cells, avg_launch_ms, sm_mhz=None, alu=False, traffic=None):
     """Roofline of the stage kernel. HBM: algorithmic bytes per launch = 8 F B per cell per step (stage 1
     reads U^n and writes U^(1); stages 2 and 3 read U^n and the stage input and write) over 3 launches.
-    ALU (FP32): algorithmic operations per launch against 152 SMs x 128 FP32 lanes x SM clock."""
+    ALU (FP32): the method's operations per launch (method_ops_per_cell_stage, no halo recomputation)
+    against 152 SMs x 128 FP32 lanes x SM clock; the kernel's own count (halos included) is reported beside
+    it as kernel_ops_per_cell."""
     alg_bytes_per_launch = 8 * F * B * cells / 3.0
     achieved = alg_bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
@@ -257,12 +291,14 @@ def roofline(F, B, cells, avg_launch_ms, sm_mhz=None, alu=False, traffic=None):
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = sm_mhz or 2070.0
-    ops = alg_ops_per_cell_stage(F) * cells
+    ops = method_ops_per_cell_stage(F) * cells
     a = ops / (avg_launch_ms * 1e-3) / 1e12
     pk = sms * 128 * mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": a, "peak": pk, "unit": "T FP32 ops/s (FMA = 1)", "frac": a / pk,
             "traffic": traffic, "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
-            "kernel": "stage_kernel", "avg_launch_ms": avg_launch_ms, "alg_ops_per_launch": ops}
+            "kernel": "stage_kernel", "avg_launch_ms": avg_launch_ms, "alg_ops_per_launch": ops,
+            "alg_ops_per_cell": method_ops_per_cell_stage(F), "kernel_ops_per_cell": kernel_ops_per_cell_stage(F),
+            "kernel_ops_frac": kernel_ops_per_cell_stage(F) * cells / (avg_launch_ms * 1e-3) / 1e12 / pk}
     return roof, hbm
 
 
@@ -353,6 +389,116 @@ def run_gradient(args, prob, dtype, rank, world, barrier):
     return 0
 
 
+def _timed(fn, local):
+    """Run fn() between CUDA events on the current stream with the clock sampler running; returns
+    (ms, clocks, fn's result)."""
+    import torch
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), clocks.stop(), out
+
+
+def host_link(nbytes: int, local: int):
+    """Plain copy-engine rates between pinned host memory and the device for one state's worth of bytes:
+    the ceiling of the end-to-end (host-buffer) figure. Best of 3 per direction, CUDA events."""
+    import torch
+    n = nbytes // 4
+    host = torch.empty(n, dtype=torch.float32).pin_memory()
+    dev = torch.empty(n, dtype=torch.float32, device="cuda")
+    dev.copy_(host, non_blocking=True)
+    host.copy_(dev, non_blocking=True)
+    best_h2d = best_d2h = float("inf")
+    for _ in range(3):
+        ms, _, _ = _timed(lambda: dev.copy_(host, non_blocking=True), local)
+        best_h2d = min(best_h2d, ms)
+        ms, _, _ = _timed(lambda: host.copy_(dev, non_blocking=True), local)
+        best_d2h = min(best_d2h, ms)
+    del host, dev
+    return {"bytes": 4 * n, "h2d_gbs": 4 * n / (best_h2d * 1e-3) / 1e9, "d2h_gbs": 4 * n / (best_d2h * 1e-3) / 1e9,
+            "how": "torch copy_ between a pinned host tensor and a device tensor (cudaMemcpyAsync), best of 3"}
+
+
+def config_records(args, local):
+    """Short timed records of the other workload configurations, beside the 8192^2 headline: the plain
+    method (128^2 FP64, 100 steps), the (r,z) Rayleigh-Taylor grid (1024 x 2048, FP32 and FP64), the
+    64-member ensemble (one persistent launch per stage, CUDA graph) and the 256^2 gradient configuration
+    (200 steps, checkpoints every 20, forward and adjoint sweep, FP64 and FP32). Each: cell-updates/s,
+    milliseconds per step, the HBM fraction of its algorithmic bytes and the clocks sampled while it ran."""
+    import torch
+    from paper_1507_08549_gb300 import hydro
+    from paper_1507_08549_gb300 import workloads as wl
+    out = {}
+    peak, _ = _peaks()
+
+    def single(name, prob, dtype, steps, warmup=3):
+        h = hydro.Hydro(prob, dtype=dtype)
+        U = h.state(prob.U0)
+        h.step(U, warmup)
+        ms, clk, _ = _timed(lambda: h.step(U, steps), local)
+        h.close()
+        B = 8 if dtype == "f64" else 4
+        alg = 8 * prob.nfields * B * prob.cells  # bytes per RK3 step
+        rec = {"workload": name, "dtype": dtype, "cells": prob.cells, "steps": steps, "ms_per_step": ms / steps,
+               "value": prob.cells * steps / (ms * 1e-3), "unit": UNIT,
+               "roofline_hbm": {"achieved": alg / (ms / steps * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": alg / (ms / steps * 1e-3) / 1e9 / peak},
+               "l2": ("state in L2" if prob.nfields * B * prob.cells < 129e6 else "state larger than L2"),
+               "clocks": clk}
+        return rec
+
+    out["c1_advected_wave_128_f64"] = single("advected_wave_128", wl.advected_wave(128), "f64", 100)
+    rt = wl.rayleigh_taylor(1024, 2048)
+    out["c2_rayleigh_taylor_1024x2048_f32"] = single("rayleigh_taylor_1024x2048", rt, "f32", 20)
+    out["c2_rayleigh_taylor_1024x2048_f64"] = single("rayleigh_taylor_1024x2048", rt, "f64", 3)
+    del rt
+    # C3: the 64-member ensemble
+    members = wl.quadrant_ensemble(64)
+    hs = [hydro.Hydro(p, dtype="f32") for p in members]
+    Us = [h.state(p.U0) for h, p in zip(hs, members)]
+    cells = sum(p.cells for p in members)
+    hydro.hydro_batch_step(hs, Us, 3)
+    steps = 10
+    ms, clk, _ = _timed(lambda: hydro.hydro_batch_step(hs, Us, steps), local)
+    for h in hs:
+        h.close()
+    alg = 8 * 4 * 4 * cells
+    out["c3_quadrant_ensemble_64_f32"] = {
+        "workload": "quadrant_ensemble_64", "dtype": "f32", "members": len(members), "cells": cells, "steps": steps,
+        "ms_per_step": ms / steps, "value": cells * steps / (ms * 1e-3), "unit": UNIT,
+        "roofline_hbm": {"achieved": alg / (ms / steps * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms / steps * 1e-3) / 1e9 / peak},
+        "note": "timed region includes each call's packing and unpacking of the 64 caller states", "clocks": clk}
+    del hs, Us, members
+    # C4: the gradient configuration
+    prob, _ = wl.fourier_modes(256, nsteps=200)
+    for dtype in ("f64", "f32"):
+        h = hydro.Hydro(prob, dtype=dtype)
+        U = h.state(prob.U0)
+        h.step(U, 3)
+        U = h.state(prob.U0)
+        fwd_ms, clk, _ = _timed(lambda: h.forward_checkpointed(U, 200, 20), local)
+        rho, mx, my = U[0], U[1], U[2]
+        dA = prob.dx * prob.dy
+        lam = torch.zeros_like(U)
+        lam[0] = -0.5 * (mx * mx + my * my) / (rho * rho) * dA
+        lam[1] = mx / rho * dA
+        lam[2] = my / rho * dA
+        adj_ms, clk2, _ = _timed(lambda: h.adjoint_sweep(lam), local)
+        h.close()
+        out[f"c4_fourier_256_gradient_{dtype}"] = {
+            "workload": "fourier_256_adjoint", "dtype": dtype, "cells": prob.cells, "steps": 200,
+            "checkpoint_every": 20, "forward_ms": fwd_ms, "adjoint_sweep_ms": adj_ms,
+            "adjoint_over_forward": adj_ms / fwd_ms, "value": prob.cells * 200 / (fwd_ms * 1e-3), "unit": UNIT,
+            "clocks": clk, "clocks_adjoint": clk2}
+    return out
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -422,9 +568,10 @@ def run(args):
     value = replica_rate(cells * args.steps, ms * 1e-3, world)
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
     traffic = None
-    if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast"):
-        # measured average traffic of a stage launch per cell, times cells
-        traffic = TRAFFIC_BYTES_PER_CELL_LAUNCH_F32_NF5 * cells
+    per_cell = stage_traffic_per_cell()
+    if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast") and per_cell is not None:
+        # measured average traffic of a stage launch per cell of this kernel source, times cells
+        traffic = per_cell * cells
     roof, roof_hbm = roofline(F, B, cells, stage_ms / max(nlaunch_stage, 1), (clk or {}).get("sm_mhz"),
                               alu=(dtype == "f32" and not char), traffic=None if char else traffic)
     if char:  # two kernels per stage (char_div_kernel, stage_kernel), timed together
@@ -453,6 +600,11 @@ def run(args):
     state_bytes = F * B * cells
     e2e = {"value": replica_rate(cells * ke, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes, "steps": ke}
+    del Uh_pinned
+    link = host_link(state_bytes, local)
+    e2e["host_link"] = link
+    # the copies alone bound the end-to-end rate: one state in and one out per step at the plain copy rates
+    e2e["copy_bound_value"] = cells / (state_bytes / (link["h2d_gbs"] * 1e9) + state_bytes / (link["d2h_gbs"] * 1e9))
     # FP32 discrete adjoint of one step (frozen dt / alphas of the step it reverses) and the FP64 plain step
     adjoint = None
     if not args.no_adjoint and args.workload == "blobs_blast_8192" and not char:
@@ -467,9 +619,10 @@ def run(args):
         h.adjoint_step(U, lam.clone(), float(dtl[0]), al[0].ravel())  # warm-up (allocates the adjoint buffers)
         torch.cuda.synchronize()
         ka = max(1, args.adjoint_steps)
+        lam_k = [lam.clone() for _ in range(ka)]  # adjoint_step overwrites its cotangent in place
+        torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        lam_k = [lam.clone() for _ in range(ka)]  # adjoint_step overwrites its cotangent in place
         for k in range(ka):
             h.adjoint_step(U, lam_k[k], float(dtl[0]), al[0].ravel())
         a1.record()
@@ -522,6 +675,7 @@ def run(args):
         hc.close()
         del Uc
     poisson = poisson_timing(args) if args.workload == "blobs_blast_8192" and not args.no_poisson else None
+    configs = config_records(args, local) if args.workload == "blobs_blast_8192" and not args.no_configs else None
     fp64 = None
     if not args.no_fp64 and dtype == "f32" and args.workload == "blobs_blast_8192":
         h64 = hydro.Hydro(prob, dtype="f64")
@@ -553,7 +707,7 @@ def run(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
                 "adjoint": adjoint, "fp64_step": fp64, "reinit": reinit,
-                "characteristic": characteristic, "poisson": poisson, "alu_probe": alu_probe}
+                "characteristic": characteristic, "poisson": poisson, "alu_probe": alu_probe, "configs": configs}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -699,6 +853,7 @@ def main():
                     help="flux reconstruction of the timed run")
     ap.add_argument("--no-char", action="store_true", help="skip the characteristic-scheme timing")
     ap.add_argument("--char-steps", type=int, default=5)
+    ap.add_argument("--no-configs", action="store_true", help="skip the timed records of the other configurations")
     ap.add_argument("--poisson-sweeps", type=int, default=2048)
     ap.add_argument("--only-poisson", action="store_true",
                     help="time the self-gravity Poisson solve alone and print its JSON (profiling)")

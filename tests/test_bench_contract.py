@@ -41,10 +41,17 @@ def test_hbm_roofline_and_operation_count():
     assert hbm["achieved"] == pytest.approx(alg / (ms * 1e-3) / 1e9)
     assert hbm["frac"] == pytest.approx(hbm["achieved"] / hbm["peak"])
     assert hbm["bound"] == "hbm" and hbm["unit"] == "GB/s"
-    # per-cell FP32 operations of a stage: 8 hydro lines of 1210.5 / 15, 2 level-set lines of 700 / 15,
-    # primitives 12.3 and the cell phase 61 (40 without the level set)
-    assert bench.alg_ops_per_cell_stage(5) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 2 * 700 / 15 + 61, abs=0.5)
-    assert bench.alg_ops_per_cell_stage(4) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 40, abs=0.5)
+    # the method's FP32 operations per cell and stage (no halo): per hydro line cell flux + split 5, two
+    # triplets of 23, one face of 15, one difference of 2 and half an accumulation; per level-set line cell
+    # 2 + 25 + 14; primitives 8; the cell phase 61 (40 without the level set)
+    assert bench.method_ops_per_cell_stage(5) == pytest.approx(8 * 68.5 + 8 + 2 * 41 + 61)
+    assert bench.method_ops_per_cell_stage(4) == pytest.approx(8 * 68.5 + 8 + 40)
+    # the kernel's count with its line halos: 8 hydro lines of 1210.5 / 15, 2 level-set lines of 700 / 15,
+    # primitives on the halo box 12.3
+    assert bench.kernel_ops_per_cell_stage(5) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 2 * 700 / 15 + 61, abs=0.5)
+    assert bench.kernel_ops_per_cell_stage(4) == pytest.approx(8 * 1210.5 / 15 + 12.3 + 40, abs=0.5)
+    # a 15-cell line's halo costs the kernel 12-15 % over the method
+    assert 1.12 < bench.kernel_ops_per_cell_stage(5) / bench.method_ops_per_cell_stage(5) < 1.2
 
 
 def _smi(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
@@ -168,12 +175,14 @@ def test_alu_roofline_arithmetic(monkeypatch):
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: Props())
     cells, ms = 8192 * 8192, 3.72
     alu, hbm = bench.roofline(5, 4, cells, ms, sm_mhz=2070.0, alu=True, traffic=3.4664e9)
-    ops = bench.alg_ops_per_cell_stage(5) * cells
+    ops = bench.method_ops_per_cell_stage(5) * cells
     assert alu["bound"] == "alu" and alu["alg_ops_per_launch"] == pytest.approx(ops)
     assert alu["achieved"] == pytest.approx(ops / (ms * 1e-3) / 1e12)
     assert alu["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)
     assert alu["frac"] == pytest.approx(alu["achieved"] / alu["peak"])
-    assert 0.3 < alu["frac"] < 0.4  # the measured launch time of the 8192^2 blobs + blast stage
+    assert 0.28 < alu["frac"] < 0.34  # a 3.72 ms launch of the 8192^2 blobs + blast stage
+    assert alu["kernel_ops_frac"] == pytest.approx(alu["frac"] * bench.kernel_ops_per_cell_stage(5)
+                                                   / bench.method_ops_per_cell_stage(5))
     assert alu["traffic"] == hbm["traffic"] == 3.4664e9
     assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(8 * 5 * 4 * cells / 3 / (ms * 1e-3) / 1e9 / hbm["peak"])
 
