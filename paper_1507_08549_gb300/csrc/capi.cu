@@ -14,6 +14,8 @@
 #include <thread>
 #include <vector>
 
+#include <cudaTypedefs.h>  // cuTensorMapEncodeTiled signature, CUtensorMap
+
 #include "../../include/hydro.h"
 #include "hydro_internal.cuh"
 #include "adjoint_kernel.cuh"
@@ -60,6 +62,7 @@ struct hydro_ctx {
   int pitch = 0, rows = 0, tiles_x = 0, tiles_y = 0;
   long long fstride = 0;
   void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
+  void* tmaps = nullptr;  // device CUtensorMap[3] of A, B, C for the current tile variant's halo box
   void* scratch = nullptr;
   void* params = nullptr;  // device GridParams[7]: normal stages 0..2, frozen stages 3..5, rhs 6
   void* host_scratch = nullptr;  // pinned copy of Scratch
@@ -187,6 +190,38 @@ static real* bufp(hydro_ctx* c, int k) {
 
 static int tile_ty(int variant) { return VARIANTS[variant].ty; }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link against libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of one padded working state: dimensions (pitch, rows, nf) with strides pitch and fstride
+// elements (multiples of 16 bytes: pitch is a multiple of 4), box (68, TY + 6, nf) = one tile's halo box.
+// Tile boxes start at column tx * 60 (240 tx bytes in FP32, 480 tx in FP64: 16-byte aligned) and never
+// leave the allocation (pitch and rows cover whole tiles plus the halo).
+template <typename real>
+static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorMap* out) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return HYDRO_ECUDA;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->rows, (cuuint64_t)c->nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(real), (cuuint64_t)c->fstride * sizeof(real)};
+  const cuuint32_t box[3] = {(cuuint32_t)BOX_W, (cuuint32_t)box_h, (cuuint32_t)c->nf};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r =
+      fn(out, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+         const_cast<void*>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? HYDRO_OK : HYDRO_ECUDA;
+}
+
 // Stage parameters of this context for the current variant.
 template <typename real>
 static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
@@ -223,9 +258,11 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   real* C = bufp<real>(c, 2);
   const real* win[3] = {A, B, C};
   real* outp[3] = {B, C, A};
+  const CUtensorMap* maps = static_cast<const CUtensorMap*>(c->tmaps);
   for (int k = 0; k < 3; ++k) {
     GridParams<real> p = base;
     p.win = win[k];
+    p.tmap_win = maps + k;
     p.un = A;
     p.out = outp[k];
     p.alpha_in = s->alpha[k];
@@ -251,6 +288,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   }
   GridParams<real> r = base;  // L(W) of buffer A into buffer B
   r.win = A;
+  r.tmap_win = maps;
   r.un = A;
   r.out = B;
   r.alpha_in = s->frozen_alpha[0];
@@ -262,7 +300,13 @@ template <typename real>
 static int upload_params(hydro_ctx* c) {
   GridParams<real> p[7];
   build_params<real>(c, p);
+  alignas(64) CUtensorMap maps[3];
+  for (int k = 0; k < 3; ++k) {
+    const int rc = encode_state_map<real>(c, c->buf[k], tile_ty(c->variant) + 2 * GY, &maps[k]);
+    if (rc) return fail(c, rc, "cuTensorMapEncodeTiled failed for the working states");
+  }
   CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
   ++c->params_gen;
   if (c->step_graph) {
@@ -397,6 +441,7 @@ static int read_status(hydro_ctx* c, double* t_inout, double* dt_last) {
   const Scratch<real>* hs = static_cast<const Scratch<real>*>(c->host_scratch);
   if (t_inout) *t_inout = hs->t_acc;
   if (dt_last) *dt_last = hs->dt_cur;
+  if (hs->err & ERR_LAYOUT) return fail(c, HYDRO_ECUDA, "internal: stage kernel shared memory not 128-byte aligned");
   if (hs->err & ERR_TIMEOUT) return fail(c, HYDRO_ETIMEOUT, "a device wait gave up (tile copy did not complete)");
   if (hs->err & ERR_NONPHYSICAL)
     return fail(c, HYDRO_ENONPHYSICAL, "non-finite value, rho <= 0 or p <= 0 in the state");
@@ -554,6 +599,7 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 7 : sizeof(GridParams<float>) * 7;
   if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMalloc(&c->tmaps, 3 * sizeof(CUtensorMap)) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->partial_blocks = 4 * c->num_sms;
   if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMalloc(&c->d_totals, sizeof(double) * 5) != cudaSuccess) return bail(HYDRO_ECUDA);
@@ -583,6 +629,7 @@ void hydro_destroy(hydro_ctx* c) {
   for (int k = 0; k < 3; ++k) cudaFree(c->buf[k]);
   cudaFree(c->scratch);
   cudaFree(c->params);
+  cudaFree(c->tmaps);
   cudaFree(c->partials);
   cudaFree(c->d_totals);
   cudaFree(c->unpadded);
@@ -996,7 +1043,8 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
   for (int k = 0; k < n; ++k) {
     const Scratch<real>* hs = static_cast<const Scratch<real>*>(m[k]->host_scratch);
     if (t) t[k] = hs->t_acc;
-    if (hs->err & ERR_TIMEOUT) worst = fail(c, HYDRO_ETIMEOUT, "member " + std::to_string(k) + ": device wait gave up");
+    if (hs->err & ERR_LAYOUT) worst = fail(c, HYDRO_ECUDA, "internal: stage kernel shared memory not 128-byte aligned");
+    else if (hs->err & ERR_TIMEOUT) worst = fail(c, HYDRO_ETIMEOUT, "member " + std::to_string(k) + ": device wait gave up");
     else if ((hs->err & ERR_NONPHYSICAL) && worst == HYDRO_OK)
       worst = fail(c, HYDRO_ENONPHYSICAL, "member " + std::to_string(k) + ": non-physical state");
   }

@@ -4,7 +4,8 @@
 // Padded device layout of a working state (one plane per field, `fstride` elements apart):
 //   cell (i, j) of the nx x ny interior sits at element (j + GY) * pitch + (i + GX)
 // with GX = 4 ghost columns on the left (three are used; the fourth keeps every interior row 16-byte
-// aligned so that tiles move with 16-byte bulk copies and 4-wide vector stores) and GY = 3 ghost rows.
+// aligned, so tile boxes start on 16-byte boundaries for the TMA tensor copies and 4-wide vector stores
+// line up) and GY = 3 ghost rows.
 // pitch and the row count cover whole tiles plus the halo, so tile halo boxes never leave the
 // allocation; cells beyond the grid are dead and masked.
 #pragma once
@@ -21,7 +22,9 @@ constexpr int BOX_W = 68;    // smem row pitch; 68 = 4 (mod 32) makes the x-pass
 constexpr int RUN = 15;      // cells per line work item, in x and in y (4 items per tile row)
 
 enum Bc { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECT = 2, BC_AXIS = 3 };
-enum ErrBits { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2 };
+// ERR_LAYOUT: a launch found its shared-memory buffers off the alignment the TMA copies need and did
+// nothing (an internal error; no copy was issued)
+enum ErrBits { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2, ERR_LAYOUT = 4 };
 
 // Tile variants: tile height TY (a multiple of the 15-cell run) and threads per CTA. Per field the
 // x pass has 4 runs per row (rows padded to 8-row lane groups) and the y pass one run per 15 rows and
@@ -37,6 +40,7 @@ constexpr Variant VARIANTS[NUM_VARIANTS] = {{15, 160}, {15, 320}, {30, 640}};
 template <typename real>
 struct GridParams {
   const real* win;   // stage input W (padded)
+  const void* tmap_win;  // device CUtensorMap of win: (x, y, field) with one tile's halo box as its box
   const real* un;    // U^n (padded), read when rk_a != 0
   real* out;         // stage output (padded) or L (mode RHS)
   long long fstride; // elements between field planes

@@ -2,8 +2,9 @@
 // level-set scalar (Leung, Chu & Lin 2015, Sec. 2.1 Eq. euler2D and Sec. 2.2), for sm_103a.
 //
 // One CTA processes one 60 x TY tile per work item (persistent loop over items):
-//   A. the (TY+6) x 68 halo box of every field is moved into shared memory by TMA bulk copies
-//      (cp.async.bulk, one row per copy, completion on an mbarrier);
+//   A. the (TY+6) x 68 halo box of every field is moved into shared memory by one TMA tensor copy
+//      (cp.async.bulk.tensor.3d over (x, y, field) of the padded state, issued by one thread one tile
+//      ahead, completion on an mbarrier);
 //   B. primitive variables u, v, p at the box points (rcp of rho once per point);
 //   C. x pass: each work item is (field, tile row, run of 15 cells); the split fluxes
 //      f+- = (F +- alpha U)/2, the data of every point triplet and the 16 face fluxes of the run slide
@@ -87,12 +88,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Global -> shared bulk copy (TMA, non-tensor); bytes and both addresses are multiples of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+// One box of a 3-D tensor map (x innermost, then y, then field) into shared memory (TMA, tiled mode),
+// completion on an mbarrier. The map lives in global memory (written from the host before the launch);
+// dst is 128-byte aligned and x * sizeof(element) is a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // Barrier over `count` threads (whole warps) at named barrier ID (1..15; 0 is __syncthreads').
@@ -631,10 +635,11 @@ struct Tile {
   static constexpr int XI_PER_C = TYP * NQ;             // x-pass items per field (multiple of 32)
   static constexpr int YI_PER_C = 64 * NQY;             // y-pass items per field (60 columns padded to 64)
   static constexpr int BOX = NF * H * W;                // elements of one halo box
-  // shared-memory carve-up (elements of real)
+  // shared-memory carve-up (elements of real); each box buffer starts on a 128-byte boundary (TMA)
+  static constexpr int BOX_PAD = ((BOX * (int)sizeof(real) + 127) / 128) * 128 / (int)sizeof(real);
   static constexpr int OFF_U0 = 0;                      // [NF][H][W]   halo box, buffer 0
-  static constexpr int OFF_U1 = OFF_U0 + BOX;           // [NF][H][W]   halo box, buffer 1
-  static constexpr int OFF_PU = OFF_U1 + BOX;           // [TY][W]      u on the tile rows
+  static constexpr int OFF_U1 = OFF_U0 + BOX_PAD;       // [NF][H][W]   halo box, buffer 1
+  static constexpr int OFF_PU = OFF_U1 + BOX_PAD;       // [TY][W]      u on the tile rows
   static constexpr int OFF_PV = OFF_PU + TY * W;        // [H][TX]      v on the tile columns
   static constexpr int OFF_PP = OFF_PV + H * TX;        // [H][W]       p
   static constexpr int OFF_D = OFF_PP + H * W;          // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
@@ -650,19 +655,16 @@ struct Tile {
   static_assert(TX % EG == 0, "tile rows are whole cell groups");
 };
 
-// Issue the TMA bulk copies of one tile's halo box (warp 0; lane 0 arms the barrier first).
-template <typename real, int NF, int H>
-__device__ __forceinline__ void issue_box(const GridParams<real>& m, int tile, int TY, real* box, uint64_t* bar,
-                                          int lane, unsigned bytes) {
-  const int tx = tile % m.tiles_x, ty = tile / m.tiles_x;
-  const int x0 = tx * TILE_X, y0 = ty * TY;
-  if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
-  __syncwarp();
-  for (int r = lane; r < NF * H; r += 32) {
-    const int f = r / H, row = r - f * H;
-    const real* src = m.win + f * m.fstride + static_cast<long long>(y0 + row) * m.pitch + x0;
-    bulk_g2s(box + r * BOX_W, src, BOX_W * sizeof(real), bar);
-  }
+// Issue the TMA copy of one tile's halo box (one thread): arm the barrier with the box's bytes, then one
+// tensor copy of the (68, TY + 6, NF) box at padded column tx * 60, row ty * TY.
+template <typename real>
+__device__ __forceinline__ void issue_box(const GridParams<real>* m, int tile, int TY, real* box, uint64_t* bar,
+                                          unsigned bytes) {
+  const int tiles_x = m->tiles_x;
+  const void* map = m->tmap_win;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  mbar_arrive_expect_tx(bar, bytes);
+  tma_load_3d(box, map, tx * TILE_X, ty * TY, 0, bar);
 }
 
 // ------------------------------------------------------------------------------ the stage kernel
@@ -689,11 +691,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   // stage scalars, formed once per CTA and member (dt needs an FP64 division at stage 0; the FP64 pipe
   // is 1/64 of the FP32 rate, so no per-thread FP64 work stays in the tile loop of the FP32 kernel)
   __shared__ double s_dtd;
-  __shared__ real s_dt, s_ra, s_rb;
+  __shared__ real s_dt, s_ra, s_rb, s_ax, s_ay;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
 
+  // the tensor copies write 128-byte aligned buffers: a launch that finds its dynamic shared memory
+  // elsewhere reports it and returns before any copy (the same address for every thread)
+  if ((smem_u32(smem_raw) & 127u) != 0u) {
+    if (tid == 0 && nwork > 0) atomicOr(members[work ? work[0].member : 0].err, ERR_LAYOUT);
+    return;
+  }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -703,11 +711,11 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   __syncthreads();
 
   // prologue: the first work item's box
-  if (warp == 0 && static_cast<int>(blockIdx.x) < nwork) {
+  if (tid == 0 && static_cast<int>(blockIdx.x) < nwork) {
     const int w0 = blockIdx.x;
     const int m0 = work ? work[w0].member : 0;
     const int t0 = work ? work[w0].tile : ((sizeof(real) == 8 && ctl.mode == 2) ? w0 >> 2 : ctl.w0 + w0);
-    issue_box<real, NF, H>(members[m0], t0, TY, sm + TL::OFF_U0, &bar[0], lane, TL::BOX_BYTES);
+    issue_box<real>(members + m0, t0, TY, sm + TL::OFF_U0, &bar[0], TL::BOX_BYTES);
   }
 
   unsigned parity[2] = {0u, 0u};
@@ -757,17 +765,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         s_dt = static_cast<real>(d);
         s_ra = static_cast<real>(ctl.rk_a);
         s_rb = static_cast<real>(ctl.rk_b);
+        s_ax = g.alpha_in[0];  // the Lax-Friedrichs speeds, written by the previous launch
+        s_ay = g.alpha_in[1];
       }
       __syncthreads();
       cur_member = member;
     }
     // prefetch the next item's box into the other buffer (free since the previous tile ended)
     const int wn = w + gridDim.x;
-    if (warp == 0 && wn < nwork) {
+    if (tid == 0 && wn < nwork) {
       const int mn = work ? work[wn].member : 0;
-      issue_box<real, NF, H>(members[mn], work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : ctl.w0 + wn), TY,
-                             sm + (b ? TL::OFF_U0 : TL::OFF_U1),
-                             &bar[b ^ 1], lane, TL::BOX_BYTES);
+      issue_box<real>(members + mn, work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : ctl.w0 + wn), TY,
+                      sm + (b ? TL::OFF_U0 : TL::OFF_U1), &bar[b ^ 1], TL::BOX_BYTES);
     }
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int x0 = tx * TX, y0 = ty * TY;
@@ -775,7 +784,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int pitch = g.pitch;
 
     // stage scalars (overlap with the copies)
-    const real ax = g.alpha_in[0], ay = g.alpha_in[1];
+    const real ax = s_ax, ay = s_ay;
     if (tile == 0 && tid == 0 && ctl.mode == 0) {
       const double dtd = s_dtd;  // once per grid and stage
       if (ctl.stage == 0) {
@@ -946,9 +955,28 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             loadg<EG>(sv + srow * TX + tcol, v4);
             loadg<EG>(sp + srow * W + scol, p4);
           }
+          // every U^n value of the group is loaded before any is used: one memory latency, not one per field
+          real unv[NF][EG];
+          if (use_un) {
+            if (nvalid == EG) {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) loadg<EG>(g.un + f * fs + gbase, unv[f]);
+            } else {
+#pragma unroll
+              for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EG; ++e) unv[f][e] = (e < nvalid) ? g.un[f * fs + gbase + e] : real(0);
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int e = 0; e < EG; ++e) unv[f][e] = real(0);
+          }
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            real Uv[EG], Dv[EG], un[EG];
+            real Uv[EG], Dv[EG];
+            const real (&un)[EG] = unv[f];
             loadg<EG>(sU + (f * H + srow) * W + scol, Uv);
             if (f < 4) {
               if (g.ext_div) {
@@ -964,14 +992,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               loadg<EG>(sX + (3 * TY + row) * TX + tcol, yq);
 #pragma unroll
               for (int e = 0; e < EG; ++e) Dv[e] = Ar<real>::hamiltonian(u4[e], v4[e], sf, xm[e], xq[e], ym[e], yq[e]);
-            }
-            if (use_un) {
-              if (nvalid == EG) {
-                loadg<EG>(g.un + f * fs + gbase, un);
-              } else {
-#pragma unroll
-                for (int e = 0; e < EG; ++e) un[e] = (e < nvalid) ? g.un[f * fs + gbase + e] : real(0);
-              }
             }
 #pragma unroll
             for (int e = 0; e < EG; ++e) {
