@@ -263,6 +263,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
     GridParams<real> p = base;
     p.win = win[k];
     p.tmap_win = maps + k;
+    p.tmap_un = maps;
     p.un = A;
     p.out = outp[k];
     p.alpha_in = s->alpha[k];
@@ -289,6 +290,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   GridParams<real> r = base;  // L(W) of buffer A into buffer B
   r.win = A;
   r.tmap_win = maps;
+  r.tmap_un = maps;
   r.un = A;
   r.out = B;
   r.alpha_in = s->frozen_alpha[0];

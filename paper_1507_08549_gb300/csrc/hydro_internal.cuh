@@ -42,6 +42,7 @@ struct GridParams {
   const real* win;   // stage input W (padded)
   const void* tmap_win;  // device CUtensorMap of win: (x, y, field) with one tile's halo box as its box
   const real* un;    // U^n (padded), read when rk_a != 0
+  const void* tmap_un;   // device CUtensorMap of un (the same box), for L2 prefetches
   real* out;         // stage output (padded) or L (mode RHS)
   long long fstride; // elements between field planes
   int nx, ny, pitch;

@@ -99,6 +99,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
       : "memory");
 }
 
+// L2 prefetch of one box of a 3-D tensor map (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_l2_3d(const void* tmap, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tmap), "r"(x), "r"(y),
+               "r"(z)
+               : "memory");
+}
+
 // Barrier over `count` threads (whole warps) at named barrier ID (1..15; 0 is __syncthreads').
 template <int ID>
 __device__ __forceinline__ void named_barrier_sync(int count) {
@@ -656,15 +663,17 @@ struct Tile {
 };
 
 // Issue the TMA copy of one tile's halo box (one thread): arm the barrier with the box's bytes, then one
-// tensor copy of the (68, TY + 6, NF) box at padded column tx * 60, row ty * TY.
+// tensor copy of the (68, TY + 6, NF) box at padded column tx * 60, row ty * TY. With prefetch_un, the
+// same box of U^n is prefetched into L2 for the tile's per-cell phase. m may point to shared memory.
 template <typename real>
 __device__ __forceinline__ void issue_box(const GridParams<real>* m, int tile, int TY, real* box, uint64_t* bar,
-                                          unsigned bytes) {
+                                          unsigned bytes, bool prefetch_un) {
   const int tiles_x = m->tiles_x;
   const void* map = m->tmap_win;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   mbar_arrive_expect_tx(bar, bytes);
   tma_load_3d(box, map, tx * TILE_X, ty * TY, 0, bar);
+  if (prefetch_un) tma_prefetch_l2_3d(m->tmap_un, tx * TILE_X, ty * TY, 0);
 }
 
 // ------------------------------------------------------------------------------ the stage kernel
@@ -710,12 +719,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   for (int k = tid; k < TL::RED_ELEMS; k += NT) red[k] = real(0);
   __syncthreads();
 
+  // the blend of stages 2 and 3 reads U^n in the per-cell phase: its tile box is prefetched into L2 with
+  // the halo box
+  const bool prefetch_un = ctl.mode == 0 && ctl.rk_a != 0.0;
   // prologue: the first work item's box
   if (tid == 0 && static_cast<int>(blockIdx.x) < nwork) {
     const int w0 = blockIdx.x;
     const int m0 = work ? work[w0].member : 0;
     const int t0 = work ? work[w0].tile : ((sizeof(real) == 8 && ctl.mode == 2) ? w0 >> 2 : ctl.w0 + w0);
-    issue_box<real>(members + m0, t0, TY, sm + TL::OFF_U0, &bar[0], TL::BOX_BYTES);
+    issue_box<real>(members + m0, t0, TY, sm + TL::OFF_U0, &bar[0], TL::BOX_BYTES, prefetch_un);
   }
 
   unsigned parity[2] = {0u, 0u};
@@ -775,8 +787,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     const int wn = w + gridDim.x;
     if (tid == 0 && wn < nwork) {
       const int mn = work ? work[wn].member : 0;
-      issue_box<real>(members + mn, work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : ctl.w0 + wn), TY,
-                      sm + (b ? TL::OFF_U0 : TL::OFF_U1), &bar[b ^ 1], TL::BOX_BYTES);
+      // the member's parameters come from the shared copy when the next item is of the same member
+      issue_box<real>(mn == member ? &g : members + mn,
+                      work ? work[wn].tile : ((kSplit && ctl.mode == 2) ? wn >> 2 : ctl.w0 + wn), TY,
+                      sm + (b ? TL::OFF_U0 : TL::OFF_U1), &bar[b ^ 1], TL::BOX_BYTES, prefetch_un);
     }
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int x0 = tx * TX, y0 = ty * TY;
@@ -849,6 +863,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     // y pass of hydro field c (which adds to the rows of sD that field c's x pass wrote) only waits for
     // the warps of field c (named barrier 1 + c), and the level set's two passes share no data at all.
     constexpr bool kFieldSync = TL::XI_PER_C == TL::YI_PER_C && NF * TL::XI_PER_C <= NT && TL::XI_PER_C % 32 == 0;
+    // with one thread per item, the level set's threads (whose lines are cheaper) also form its
+    // Hamiltonian at every tile cell once their y pass is done, into the level set's divergence slot
+    constexpr bool kPhiH = NF == 5 && kFieldSync;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       const bool xp = pass == 0;
@@ -896,6 +913,16 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
           else
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
+        }
+      }
+      if (kPhiH && !xp && split_field < 0 && tid >= 4 * TL::XI_PER_C) {
+        named_barrier_sync<5>(TL::XI_PER_C);  // the level set's x- and y-pass derivatives are all in sX
+        const real sfl = g.flame_speed;
+        for (int idx = tid - 4 * TL::XI_PER_C; idx < TY * TX; idx += TL::XI_PER_C) {
+          const int row = idx / TX, col = idx - row * TX;
+          const real* xq = sX + row * TX + col;
+          sD[(4 * TY + row) * TX + col] = Ar<real>::hamiltonian(su[row * W + col + 4], sv[(row + 3) * TX + col], sfl,
+                                                               xq[0], xq[TY * TX], xq[2 * TY * TX], xq[3 * TY * TX]);
         }
       }
       if (xp && kFieldSync && split_field < 0) {
@@ -949,7 +976,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
             for (int e = 0; e < EG; ++e) rr[e] = Ar<real>::radius(g, ib + e);
           }
-          const bool need_prims = rz || grav != real(0) || NF == 5;
+          const bool need_prims = rz || grav != real(0) || (NF == 5 && !kPhiH);
           if (need_prims) {
             loadg<EG>(su + row * W + scol, u4);
             loadg<EG>(sv + srow * TX + tcol, v4);
@@ -984,6 +1011,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               } else {
                 loadg<EG>(sD + (f * TY + row) * TX + tcol, Dv);
               }
+            } else if constexpr (kPhiH) {  // level set: its Hamiltonian, formed by the level-set threads
+              loadg<EG>(sD + (4 * TY + row) * TX + tcol, Dv);
             } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
               real xm[EG], xq[EG], ym[EG], yq[EG];
               loadg<EG>(sX + (0 * TY + row) * TX + tcol, xm);
