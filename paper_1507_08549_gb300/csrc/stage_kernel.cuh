@@ -411,19 +411,17 @@ struct Ar<double> {
 //
 // One line of K cells: points m = 0 .. K+5 (cells -3 .. K+2 of the run), faces f = 0 .. K (left face
 // of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1, where
-// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). The FP32 line takes
-// its strides (points S, velocities VS, outputs DS) as compile-time values, one instance per pass, so
-// every shared-memory access is an immediate offset from the line's base pointers; FP64 takes them at
-// run time.
+// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). Strides are runtime
+// values so the x and y passes run the same instructions.
 //
 // FP32 works on g+- = F +- alpha U = 2 f+- (the 1/2 goes into the final difference; eps scales by 4 with
 // the squared differences, so the weights are those of f+-) through the triplet form above, and forms
 // every flux kind as (U + c_E p) v_n + c_A p (c_E = 1 for energy, c_A = 1 for the normal momentum; the
 // mass flux is rho v_n), so the line has no flux-kind branches.
-template <int K, int S, int VS, int DS, bool accumulate>
+template <int K>
 __device__ __forceinline__ void hydro_line_tri(const float* __restrict__ Uc, const float* __restrict__ vel,
-                                               const float* __restrict__ pr, int kind, float alpha, float rd,
-                                               float* __restrict__ dst) {
+                                               const float* __restrict__ pr, int S, int VS, int kind, float alpha,
+                                               float rd, float* __restrict__ dst, int DS, bool accumulate) {
   using T = RT<float>;
   constexpr float EPS = 4e-6f * TRI_EPS_SCALE;
   const float rdh = T::mul_(0.5f, rd);
@@ -491,9 +489,9 @@ __device__ __forceinline__ void hydro_line_f64(const double* __restrict__ Uc, co
 // m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
 // phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}), stored to om[k*DS], op[k*DS]. FP32 forms
 // each difference triplet's smoothness data once for both derivatives.
-template <int K, int S, int DS>
-__device__ __forceinline__ void phi_line_tri(const float* __restrict__ ph, float rd, float* __restrict__ om,
-                                             float* __restrict__ op) {
+template <int K>
+__device__ __forceinline__ void phi_line_tri(const float* __restrict__ ph, int S, float rd, float* __restrict__ om,
+                                             float* __restrict__ op, int DS) {
   constexpr float EPS = 1e-6f * TRI_EPS_SCALE;
   float d[K + 5];
   Tri32 tl[K + 5], tr[K + 5];
@@ -903,24 +901,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const real* Uc = sU + (c * H + brow) * W + bcol;
           const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
           const real* vel = xp ? su + trow * W + bcol : sv + brow * TX + tcol;
-          if constexpr (sizeof(real) == 4) {
-            if (xp)
-              hydro_line_tri<K, 1, 1, 1, false>(Uc, vel, sp + brow * W + bcol, kind, alpha, rd,
-                                                sD + (c * TY + trow) * TX + tcol);
-            else
-              hydro_line_tri<K, W, TX, TX, true>(Uc, vel, sp + brow * W + bcol, kind, alpha, rd,
-                                                 sD + (c * TY + trow) * TX + tcol);
-          } else
+          if constexpr (sizeof(real) == 4)
+            hydro_line_tri<K>(Uc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd,
+                              sD + (c * TY + trow) * TX + tcol, DS, !xp);
+          else
             hydro_line_f64<K>(Uc, Xc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, h,
                               sD + (c * TY + trow) * TX + tcol, DS, !xp);
         } else {
           real* om = sX + ((xp ? 0 : 2) * TY + trow) * TX + tcol;
-          if constexpr (sizeof(real) == 4) {
-            if (xp)
-              phi_line_tri<K, 1, 1>(sU + (4 * H + brow) * W + bcol, rd, om, om + TY * TX);
-            else
-              phi_line_tri<K, W, TX>(sU + (4 * H + brow) * W + bcol, rd, om, om + TY * TX);
-          } else
+          if constexpr (sizeof(real) == 4)
+            phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
+          else
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
         }
       }
