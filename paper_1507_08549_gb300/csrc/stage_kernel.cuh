@@ -863,9 +863,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     // y pass of hydro field c (which adds to the rows of sD that field c's x pass wrote) only waits for
     // the warps of field c (named barrier 1 + c), and the level set's two passes share no data at all.
     constexpr bool kFieldSync = TL::XI_PER_C == TL::YI_PER_C && NF * TL::XI_PER_C <= NT && TL::XI_PER_C % 32 == 0;
-    // with one thread per item, the level set's threads (whose lines are cheaper) also form its
-    // Hamiltonian at every tile cell once their y pass is done, into the level set's divergence slot
-    constexpr bool kPhiH = NF == 5 && kFieldSync;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       const bool xp = pass == 0;
@@ -913,16 +910,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
           else
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
-        }
-      }
-      if (kPhiH && !xp && split_field < 0 && tid >= 4 * TL::XI_PER_C) {
-        named_barrier_sync<5>(TL::XI_PER_C);  // the level set's x- and y-pass derivatives are all in sX
-        const real sfl = g.flame_speed;
-        for (int idx = tid - 4 * TL::XI_PER_C; idx < TY * TX; idx += TL::XI_PER_C) {
-          const int row = idx / TX, col = idx - row * TX;
-          const real* xq = sX + row * TX + col;
-          sD[(4 * TY + row) * TX + col] = Ar<real>::hamiltonian(su[row * W + col + 4], sv[(row + 3) * TX + col], sfl,
-                                                               xq[0], xq[TY * TX], xq[2 * TY * TX], xq[3 * TY * TX]);
         }
       }
       if (xp && kFieldSync && split_field < 0) {
@@ -976,7 +963,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
             for (int e = 0; e < EG; ++e) rr[e] = Ar<real>::radius(g, ib + e);
           }
-          const bool need_prims = rz || grav != real(0) || (NF == 5 && !kPhiH);
+          const bool need_prims = rz || grav != real(0) || NF == 5;
           if (need_prims) {
             loadg<EG>(su + row * W + scol, u4);
             loadg<EG>(sv + srow * TX + tcol, v4);
@@ -1011,8 +998,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               } else {
                 loadg<EG>(sD + (f * TY + row) * TX + tcol, Dv);
               }
-            } else if constexpr (kPhiH) {  // level set: its Hamiltonian, formed by the level-set threads
-              loadg<EG>(sD + (4 * TY + row) * TX + tcol, Dv);
             } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
               real xm[EG], xq[EG], ym[EG], yq[EG];
               loadg<EG>(sX + (0 * TY + row) * TX + tcol, xm);
