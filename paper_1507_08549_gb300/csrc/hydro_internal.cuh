@@ -28,16 +28,13 @@ enum ErrBits { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2, ERR_LAYOUT = 4 };
 
 // Tile variants: tile height TY (a multiple of the 15-cell run) and threads per CTA. Per field the
 // x pass has 4 runs per row (rows padded to 8-row lane groups) and the y pass one run per 15 rows and
-// column (columns padded to 64); 320 threads give one item per thread for TY = 15. The FP32 kernel of
-// 192 threads runs the hydro lines as packed field pairs (fields 0 and 1, 2 and 3 in the two lanes of
-// packed FP32 instructions): 2 pairs x 64 items + 64 level-set items, one per thread.
+// column (columns padded to 64); 320 threads give about one item per thread for TY = 15.
 struct Variant {
   int ty, threads;
 };
 constexpr int NUM_VARIANTS = 3;
 constexpr int MAX_TY = 30;
-constexpr int PACKED_THREADS = 192;
-constexpr Variant VARIANTS[NUM_VARIANTS] = {{15, PACKED_THREADS}, {15, 320}, {30, 640}};
+constexpr Variant VARIANTS[NUM_VARIANTS] = {{15, 160}, {15, 320}, {30, 640}};
 
 // Per-grid parameters of one stage launch (one ensemble member).
 template <typename real>

@@ -456,113 +456,6 @@ __device__ __forceinline__ void hydro_line_tri(const float* __restrict__ Uc, con
   }
 }
 
-// ------------------------------------------------------------------------------ packed FP32 pairs
-//
-// Two lines of the same direction and position but different fields (a field pair) in the two lanes of
-// packed FP32 instructions (fma.rn.f32x2 and kin): every lane performs exactly the rounded operations
-// hydro_line_tri performs for its field, in the same order, so the results are the same bits; a packed
-// instruction issues two of them. Reciprocals stay scalar (one per lane).
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(RT<float>::rcp(a.x), RT<float>::rcp(a.y)); }
-
-struct Role2 {
-  float2 q, w;
-};
-struct Tri2 {
-  Role2 up, mid, down;
-};
-struct TriD2 {
-  float2 s, u, base, rm, rt6, rp;
-};
-// tri_data of two triplets, lane by lane
-__device__ __forceinline__ TriD2 tri_data2(float2 L, float2 C, float2 R, float eps_scaled) {
-  TriD2 d;
-  d.s = fma2(f2(-2.0f), C, add2(L, R));
-  d.u = mul2(f2(TRI_KU), sub2(L, R));
-  const float2 bs = fma2(d.s, d.s, f2(eps_scaled));
-  const float2 mm = fma2(f2(TRI_KS), d.s, f2(-d.u.x, -d.u.y)), pp = fma2(f2(TRI_KS), d.s, d.u);
-  const float2 Dm = fma2(mm, mm, bs), Dt = fma2(d.u, d.u, bs), Dp = fma2(pp, pp, bs);
-  d.rm = rcp2(mul2(Dm, Dm));
-  d.rt6 = mul2(f2(6.0f), rcp2(mul2(Dt, Dt)));
-  d.rp = rcp2(mul2(Dp, Dp));
-  d.base = fma2(f2(1.0f / 12.0f), d.s, C);
-  return d;
-}
-// tri_roles of two triplets, lane by lane
-__device__ __forceinline__ Tri2 tri_roles2(const TriD2& d, bool left_to_right) {
-  const float2 lo = fma2(f2(-TRI_KQ), d.u, d.base), hi = fma2(f2(TRI_KQ), d.u, d.base);
-  const float2 bss = add2(d.base, d.s);
-  Tri2 r;
-  r.mid = {left_to_right ? lo : hi, d.rt6};
-  if (left_to_right) {
-    r.up = {fma2(f2(-3.0f * TRI_KQ), d.u, bss), d.rm};
-    r.down = {hi, mul2(f2(3.0f), d.rp)};
-  } else {
-    r.up = {fma2(f2(3.0f * TRI_KQ), d.u, bss), d.rp};
-    r.down = {lo, mul2(f2(3.0f), d.rm)};
-  }
-  return r;
-}
-// tri_face of two faces, lane by lane
-__device__ __forceinline__ float2 tri_face2(const Role2& a, const Role2& b, const Role2& c) {
-  const float2 num = fma2(c.w, c.q, fma2(b.w, b.q, mul2(a.w, a.q)));
-  const float2 den = add2(add2(a.w, b.w), c.w);
-  return mul2(num, rcp2(den));
-}
-
-// hydro_line_tri for the field pair (U0, U1) sharing the velocity and pressure of the line; cE, cA are
-// the flux-kind constants per lane, d0 and d1 the two fields' outputs.
-template <int K>
-__device__ __forceinline__ void hydro_line_pair(const float* __restrict__ U0, const float* __restrict__ U1,
-                                                const float* __restrict__ vel, const float* __restrict__ pr, int S,
-                                                int VS, float2 cE, float2 cA, float alpha, float rd,
-                                                float* __restrict__ d0, float* __restrict__ d1, int DS,
-                                                bool accumulate) {
-  constexpr float EPS = 4e-6f * TRI_EPS_SCALE;
-  const float2 rdh = f2(RT<float>::mul_(0.5f, rd));
-  float2 gp[K + 6], gm[K + 6];
-  Tri2 tp[K + 6], tm[K + 6];
-  float2 fh_prev = f2(0.0f);
-#pragma unroll
-  for (int m = 0; m < K + 6; ++m) {
-    const float2 uu = f2(U0[m * S], U1[m * S]);
-    const float2 pq = f2(pr[m * S]);
-    const float2 F = fma2(fma2(cE, pq, uu), f2(vel[m * VS]), mul2(cA, pq));
-    gp[m] = fma2(f2(alpha), uu, F);
-    gm[m] = fma2(f2(-alpha), uu, F);
-    if (m >= 2) {
-      const int j = m - 1;
-      if (j <= K + 3) tp[j] = tri_roles2(tri_data2(gp[j - 1], gp[j], gp[j + 1], EPS), true);
-      if (j >= 2) tm[j] = tri_roles2(tri_data2(gm[j - 1], gm[j], gm[j + 1], EPS), false);
-    }
-    if (m >= 5) {
-      const int f = m - 5;
-      const float2 plus = tri_face2(tp[f + 1].up, tp[f + 2].mid, tp[f + 3].down);
-      const float2 minus = tri_face2(tm[f + 4].up, tm[f + 3].mid, tm[f + 2].down);
-      const float2 fh = add2(plus, minus);
-      if (f >= 1) {
-        const float2 d = mul2(sub2(fh, fh_prev), rdh);
-        float* o0 = d0 + (f - 1) * DS;
-        float* o1 = d1 + (f - 1) * DS;
-        if (accumulate) {
-          const float2 acc = add2(f2(*o0, *o1), d);
-          *o0 = acc.x;
-          *o1 = acc.y;
-        } else {
-          *o0 = d.x;
-          *o1 = d.y;
-        }
-      }
-      fh_prev = fh;
-    }
-  }
-}
-
 // FP64: the textbook WENO5 per face side, in the plain definition's order.
 template <int K>
 __device__ __forceinline__ void hydro_line_f64(const double* __restrict__ Uc, const double* __restrict__ Xc,
@@ -792,10 +685,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   using T = RT<real>;
   using TL = Tile<real, NF, TY>;
   constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ;
-  // FP32 with PACKED_THREADS threads: hydro lines as packed field pairs, one line item per thread
-  constexpr bool kPacked = sizeof(real) == 4 && NT == PACKED_THREADS;
-  constexpr int EGk = kPacked ? 5 : EG;
-  static_assert(TX % EGk == 0, "tile rows are whole cell groups");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
@@ -969,62 +858,6 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     }
     __syncthreads();
 
-    // ---- C/D (packed kernel): items (field pair or level set, line, run of 15 cells), one per thread;
-    // the y pass of a pair waits only for that pair's x-pass warps, the level set's not at all
-    if constexpr (kPacked) {
-      constexpr int PI = TL::XI_PER_C;
-      static_assert(TL::XI_PER_C == TL::YI_PER_C && PI % 32 == 0 && 3 * PI <= NT, "one packed item per thread");
-      const int c = tid / PI;  // 0: fields 0 and 1, 1: fields 2 and 3, 2: level set (warp-uniform)
-      const int rem = tid - c * PI;
-#pragma unroll 1
-      for (int pass = 0; pass < 2; ++pass) {
-        const bool xp = pass == 0;
-        const real alpha = xp ? ax : ay;
-        const real rd = xp ? g.rdx : g.rdy;
-        int trow, tcol, brow, bcol;
-        bool active = c < (NF == 5 ? 3 : 2);
-        if (xp) {
-          trow = (rem / (8 * NQ)) * 8 + (rem & 7);
-          tcol = ((rem >> 3) % NQ) * K;
-          active = active && trow < TY;
-          brow = trow + 3;
-          bcol = tcol + 1;
-        } else {
-          tcol = rem & 63;
-          trow = (rem >> 6) * K;
-          active = active && tcol < TX;
-          brow = trow;
-          bcol = tcol + 4;
-        }
-        const int S = xp ? 1 : W;
-        const int DS = xp ? 1 : TX;
-        if (active) {
-          if (c < 2) {
-            if (!g.ext_div) {
-              const int f0 = 2 * c;
-              // flux kinds of the pair's fields along this direction, as (U + cE p) v_n + cA p
-              const int k0 = f0 == 0 ? 0 : (xp ? 2 : 1), k1 = f0 == 0 ? (xp ? 1 : 2) : 3;
-              const float2 cE = f2(k0 == 3 ? 1.0f : 0.0f, k1 == 3 ? 1.0f : 0.0f);
-              const float2 cA = f2(k0 == 1 ? 1.0f : 0.0f, k1 == 1 ? 1.0f : 0.0f);
-              const real* vel = xp ? su + trow * W + bcol : sv + brow * TX + tcol;
-              hydro_line_pair<K>(sU + (f0 * H + brow) * W + bcol, sU + ((f0 + 1) * H + brow) * W + bcol, vel,
-                                 sp + brow * W + bcol, S, xp ? 1 : TX, cE, cA, alpha, rd,
-                                 sD + (f0 * TY + trow) * TX + tcol, sD + ((f0 + 1) * TY + trow) * TX + tcol, DS,
-                                 !xp);
-            }
-          } else {
-            real* om = sX + ((xp ? 0 : 2) * TY + trow) * TX + tcol;
-            phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
-          }
-        }
-        if (xp) {
-          if (c == 0) named_barrier_sync<1>(PI);
-          if (c == 1) named_barrier_sync<2>(PI);
-        } else {
-          __syncthreads();
-        }
-      }
-    } else {
     // ---- C/D. x pass then y pass through the same line code: items (field, line, run of 15 cells)
     // Items [c per_c, (c+1) per_c) of both passes carry field c. When every item has its own thread, the
     // y pass of hydro field c (which adds to the rows of sD that field c's x pass wrote) only waits for
@@ -1092,10 +925,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         __syncthreads();
       }
     }
-    }  // packed / scalar passes
 
-    // ---- E. per cell: sources, RK blend, stores, ghost images, reductions (groups of EGk cells of a
-    // row: 300 groups of 3 for 320 threads, 180 groups of 5 for the 192 threads of the packed kernel)
+    // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
     real amx = real(0), amy = real(0), smx = real(0);
     // totals: FP64 per cell in the FP64 kernel; the FP32 kernel sums U_f (times r in (r,z)) over a thread's
     // cells and then over its warp in FP32, the warp partials over the CTA's tiles as compensated FP32
@@ -1117,67 +948,67 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real dt = s_dt;
       const real ra = s_ra, rb = s_rb;
       const bool use_un = ra != real(0) && ctl.mode == 0;
-      constexpr int NG = TX / EGk;
+      constexpr int NG = TX / EG;
       for (int it2 = tid; it2 < TY * NG; it2 += NT) {
         const int row = it2 / NG, g4 = it2 - row * NG;
-        const int j = y0 + row, ib = x0 + EGk * g4;
+        const int j = y0 + row, ib = x0 + EG * g4;
         if (j >= ny || ib >= nx) continue;
-        const int nvalid = min(EGk, nx - ib);
+        const int nvalid = min(EG, nx - ib);
         const long long gbase = static_cast<long long>(j + GY) * pitch + ib + GX;
-        const int srow = row + 3, scol = 4 + EGk * g4, tcol = EGk * g4;
-        real o[NF][EGk];
+        const int srow = row + 3, scol = 4 + EG * g4, tcol = EG * g4;
+        real o[NF][EG];
         {
-          real u4[EGk], v4[EGk], p4[EGk], rr[EGk];
+          real u4[EG], v4[EG], p4[EG], rr[EG];
           if (rz) {
 #pragma unroll
-            for (int e = 0; e < EGk; ++e) rr[e] = Ar<real>::radius(g, ib + e);
+            for (int e = 0; e < EG; ++e) rr[e] = Ar<real>::radius(g, ib + e);
           }
           const bool need_prims = rz || grav != real(0) || NF == 5;
           if (need_prims) {
-            loadg<EGk>(su + row * W + scol, u4);
-            loadg<EGk>(sv + srow * TX + tcol, v4);
-            loadg<EGk>(sp + srow * W + scol, p4);
+            loadg<EG>(su + row * W + scol, u4);
+            loadg<EG>(sv + srow * TX + tcol, v4);
+            loadg<EG>(sp + srow * W + scol, p4);
           }
           // every U^n value of the group is loaded before any is used: one memory latency, not one per field
-          real unv[NF][EGk];
+          real unv[NF][EG];
           if (use_un) {
-            if (nvalid == EGk) {
+            if (nvalid == EG) {
 #pragma unroll
-              for (int f = 0; f < NF; ++f) loadg<EGk>(g.un + f * fs + gbase, unv[f]);
+              for (int f = 0; f < NF; ++f) loadg<EG>(g.un + f * fs + gbase, unv[f]);
             } else {
 #pragma unroll
               for (int f = 0; f < NF; ++f)
 #pragma unroll
-                for (int e = 0; e < EGk; ++e) unv[f][e] = (e < nvalid) ? g.un[f * fs + gbase + e] : real(0);
+                for (int e = 0; e < EG; ++e) unv[f][e] = (e < nvalid) ? g.un[f * fs + gbase + e] : real(0);
             }
           } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f)
 #pragma unroll
-              for (int e = 0; e < EGk; ++e) unv[f][e] = real(0);
+              for (int e = 0; e < EG; ++e) unv[f][e] = real(0);
           }
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            real Uv[EGk], Dv[EGk];
-            const real (&un)[EGk] = unv[f];
-            loadg<EGk>(sU + (f * H + srow) * W + scol, Uv);
+            real Uv[EG], Dv[EG];
+            const real (&un)[EG] = unv[f];
+            loadg<EG>(sU + (f * H + srow) * W + scol, Uv);
             if (f < 4) {
               if (g.ext_div) {
-                loadg<EGk>(g.ext_div + f * fs + gbase, Dv);
+                loadg<EG>(g.ext_div + f * fs + gbase, Dv);
               } else {
-                loadg<EGk>(sD + (f * TY + row) * TX + tcol, Dv);
+                loadg<EG>(sD + (f * TY + row) * TX + tcol, Dv);
               }
             } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
-              real xm[EGk], xq[EGk], ym[EGk], yq[EGk];
-              loadg<EGk>(sX + (0 * TY + row) * TX + tcol, xm);
-              loadg<EGk>(sX + (1 * TY + row) * TX + tcol, xq);
-              loadg<EGk>(sX + (2 * TY + row) * TX + tcol, ym);
-              loadg<EGk>(sX + (3 * TY + row) * TX + tcol, yq);
+              real xm[EG], xq[EG], ym[EG], yq[EG];
+              loadg<EG>(sX + (0 * TY + row) * TX + tcol, xm);
+              loadg<EG>(sX + (1 * TY + row) * TX + tcol, xq);
+              loadg<EG>(sX + (2 * TY + row) * TX + tcol, ym);
+              loadg<EG>(sX + (3 * TY + row) * TX + tcol, yq);
 #pragma unroll
-              for (int e = 0; e < EGk; ++e) Dv[e] = Ar<real>::hamiltonian(u4[e], v4[e], sf, xm[e], xq[e], ym[e], yq[e]);
+              for (int e = 0; e < EG; ++e) Dv[e] = Ar<real>::hamiltonian(u4[e], v4[e], sf, xm[e], xq[e], ym[e], yq[e]);
             }
 #pragma unroll
-            for (int e = 0; e < EGk; ++e) {
+            for (int e = 0; e < EG; ++e) {
               real S = real(0);
               if (f < 4 && (rz || grav != real(0))) {
                 const real rho = sU[(0 * H + srow) * W + scol + e], mr = sU[(1 * H + srow) * W + scol + e];
@@ -1193,18 +1024,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           real* dstp = g.out + f * fs + gbase;
-          if (nvalid == EGk) {
-            storeg<EGk>(dstp, o[f]);
+          if (nvalid == EG) {
+            storeg<EG>(dstp, o[f]);
           } else {
 #pragma unroll
-            for (int e = 0; e < EGk; ++e)
+            for (int e = 0; e < EG; ++e)
               if (e < nvalid) dstp[e] = o[f][e];
           }
         }
         if (ctl.mode == 1) continue;
         // ghost images and reductions
 #pragma unroll
-        for (int e = 0; e < EGk; ++e) {
+        for (int e = 0; e < EG; ++e) {
           if (e >= nvalid) break;
           const int i = ib + e;
           if (i < 3 || i >= nx - 3 || j < 3 || j >= ny - 3) {
