@@ -296,16 +296,20 @@ struct ATile {
 //   WG = gbar a_r / sum a,  cg = -2 gbar (q_r - W) n_r / sum a,  A = 13/6 s cg,  B = h_r cg,
 // on the role's three points in reconstruction order, with dq_r = (2, -7, 11)/6, (-1, 5, 2)/6, (2, 5, -1)/6
 // and dt_r = (1, -4, 3), (1, 0, -1), (3, -4, 1) for up, mid, dn (Jiang & Shu's candidate values and
-// smoothness indicators differentiated).
+// smoothness indicators differentiated). q_r - W is not formed as a difference of the two (close on
+// smooth data, so its FP32 rounding would be amplified): with w_r = a_r / sum a, the candidate
+// differences q_up - q_mid = (s_up - s_mid) / 3 and q_mid - q_dn = (s_dn - s_mid) / 6 (exact identities of
+// the candidate values) give q_up - W = w_mid D01 + w_dn D02, q_mid - W = w_dn D12 - w_up D01,
+// q_dn - W = -(w_up D02 + w_mid D12), from the triplets' second differences s.
 struct ARole {
-  float q, a, nr, h;
+  float a, nr, h;  // weight, weight / D, the role's half-difference h_r
 };
 struct ATri {
   ARole up, mid, dn;
   float s13;  // 13/6 s
 };
 struct ATriData {
-  float s, th, mm, pp, rm, rt, rp, base;
+  float s, th, mm, pp, rm, rt, rp;
 };
 __device__ __forceinline__ ATriData adj_tri_data(float L, float C, float R) {
   using T = RT<float>;
@@ -318,34 +322,30 @@ __device__ __forceinline__ ATriData adj_tri_data(float L, float C, float R) {
   d.rm = T::rcp(T::fma_(d.mm, d.mm, bs));
   d.rt = T::rcp(T::fma_(d.th, d.th, bs));
   d.rp = T::rcp(T::fma_(d.pp, d.pp, bs));
-  d.base = T::fma_(1.0f / 12.0f, d.s, C);
   return d;
 }
 __device__ __forceinline__ ATri adj_tri_roles(const ATriData& d, bool left_to_right) {
-  using T = RT<float>;
-  const float bss = d.base + d.s;
-  const float lo = T::fma_(-0.5f, d.th, d.base), hi = T::fma_(0.5f, d.th, d.base);
   const float at = 6.0f * d.rt * d.rt;
   ATri r;
   r.s13 = (13.0f / 6.0f) * d.s;
   if (left_to_right) {
-    r.up = {T::fma_(-1.5f, d.th, bss), d.rm * d.rm, 0.0f, d.mm};
+    r.up = {d.rm * d.rm, 0.0f, d.mm};
     r.up.nr = r.up.a * d.rm;
-    r.mid = {lo, at, at * d.rt, d.th};
-    r.dn = {hi, 3.0f * d.rp * d.rp, 0.0f, d.pp};
+    r.mid = {at, at * d.rt, d.th};
+    r.dn = {3.0f * d.rp * d.rp, 0.0f, d.pp};
     r.dn.nr = r.dn.a * d.rp;
   } else {
-    r.up = {T::fma_(1.5f, d.th, bss), d.rp * d.rp, 0.0f, d.pp};
+    r.up = {d.rp * d.rp, 0.0f, d.pp};
     r.up.nr = r.up.a * d.rp;
-    r.mid = {hi, at, at * d.rt, -d.th};
-    r.dn = {lo, 3.0f * d.rm * d.rm, 0.0f, d.mm};
+    r.mid = {at, at * d.rt, -d.th};
+    r.dn = {3.0f * d.rm * d.rm, 0.0f, d.mm};
     r.dn.nr = r.dn.a * d.rm;
   }
   return r;
 }
 // One role's share of a face's gradient onto its points (reconstruction order a', b', c').
 template <int ROLE>
-__device__ __forceinline__ void adj_role(const ARole& r, float s13, float W, float g, float m2g, float& ga,
+__device__ __forceinline__ void adj_role(const ARole& r, float s13, float qmw, float g, float m2g, float& ga,
                                          float& gb, float& gc) {
   using T = RT<float>;
   constexpr float q0 = ROLE == 0 ? 2.0f / 6.0f : ROLE == 1 ? -1.0f / 6.0f : 2.0f / 6.0f;
@@ -355,18 +355,26 @@ __device__ __forceinline__ void adj_role(const ARole& r, float s13, float W, flo
   constexpr float t1 = ROLE == 1 ? 0.0f : -4.0f;
   constexpr float t2 = ROLE == 0 ? 3.0f : ROLE == 1 ? -1.0f : 1.0f;
   const float WG = r.a * g;
-  const float cg = (r.q - W) * r.nr * m2g;
+  const float cg = qmw * r.nr * m2g;  // qmw = q_r - W
   const float A = s13 * cg, B = r.h * cg;
   ga += T::fma_(WG, q0, T::fma_(B, t0, A));
   gb += (ROLE == 1) ? T::fma_(WG, q1, -2.0f * A) : T::fma_(WG, q1, T::fma_(B, t1, -2.0f * A));
   gc += T::fma_(WG, q2, T::fma_(B, t2, A));
 }
-// A face's W from its three roles, and the gradient factors gbar / sum a and -2 gbar / sum a.
-__device__ __forceinline__ void adj_face_w(const ARole& u, const ARole& m, const ARole& d, float gbar, float& W,
-                                           float& g, float& m2g) {
+// A face's q_r - W for its three roles (from the triplets' 13/6 s values, see above), and the gradient
+// factors gbar / sum a and -2 gbar / sum a.
+__device__ __forceinline__ void adj_face_w(const ARole& u, const ARole& m, const ARole& d, float su13, float sm13,
+                                           float sd13, float gbar, float& eu, float& em, float& ed, float& g,
+                                           float& m2g) {
   using T = RT<float>;
   const float rS = T::rcp((u.a + m.a) + d.a);
-  W = T::fma_(d.a, d.q, T::fma_(m.a, m.q, u.a * u.q)) * rS;
+  const float wu = u.a * rS, wm = m.a * rS, wd = d.a * rS;
+  const float D01 = (su13 - sm13) * (2.0f / 13.0f);  // q_up - q_mid = (s_up - s_mid) / 3
+  const float D12 = (sd13 - sm13) * (1.0f / 13.0f);  // q_mid - q_dn = (s_dn - s_mid) / 6
+  const float D02 = D01 + D12;
+  eu = T::fma_(wm, D01, wd * D02);
+  em = T::fma_(wd, D12, -(wu * D01));
+  ed = -T::fma_(wu, D02, wm * D12);
   g = gbar * rS;
   m2g = -2.0f * g;
 }
@@ -409,15 +417,17 @@ __device__ __forceinline__ void adj_hydro_line_f32(const float* __restrict__ Uc,
     tm[q + 1] = adj_tri_roles(adj_tri_data(fm[q], fm[q + 1], fm[q + 2]), false);
     const float fb = (nuc[f * S] - nuc[(f - 1) * S]) * rd;
     if (fb != 0.0f) {
-      float W, g, m2g;
-      adj_face_w(tp[q - 2].up, tp[q - 1].mid, tp[q].dn, fb, W, g, m2g);
-      adj_role<0>(tp[q - 2].up, tp[q - 2].s13, W, g, m2g, ap[q - 3], ap[q - 2], ap[q - 1]);
-      adj_role<1>(tp[q - 1].mid, tp[q - 1].s13, W, g, m2g, ap[q - 2], ap[q - 1], ap[q]);
-      adj_role<2>(tp[q].dn, tp[q].s13, W, g, m2g, ap[q - 1], ap[q], ap[q + 1]);
-      adj_face_w(tm[q + 1].up, tm[q].mid, tm[q - 1].dn, fb, W, g, m2g);
-      adj_role<0>(tm[q + 1].up, tm[q + 1].s13, W, g, m2g, am[q + 2], am[q + 1], am[q]);
-      adj_role<1>(tm[q].mid, tm[q].s13, W, g, m2g, am[q + 1], am[q], am[q - 1]);
-      adj_role<2>(tm[q - 1].dn, tm[q - 1].s13, W, g, m2g, am[q], am[q - 1], am[q - 2]);
+      float eu, em, ed, g, m2g;
+      adj_face_w(tp[q - 2].up, tp[q - 1].mid, tp[q].dn, tp[q - 2].s13, tp[q - 1].s13, tp[q].s13, fb, eu, em, ed, g,
+                 m2g);
+      adj_role<0>(tp[q - 2].up, tp[q - 2].s13, eu, g, m2g, ap[q - 3], ap[q - 2], ap[q - 1]);
+      adj_role<1>(tp[q - 1].mid, tp[q - 1].s13, em, g, m2g, ap[q - 2], ap[q - 1], ap[q]);
+      adj_role<2>(tp[q].dn, tp[q].s13, ed, g, m2g, ap[q - 1], ap[q], ap[q + 1]);
+      adj_face_w(tm[q + 1].up, tm[q].mid, tm[q - 1].dn, tm[q + 1].s13, tm[q].s13, tm[q - 1].s13, fb, eu, em, ed, g,
+                 m2g);
+      adj_role<0>(tm[q + 1].up, tm[q + 1].s13, eu, g, m2g, am[q + 2], am[q + 1], am[q]);
+      adj_role<1>(tm[q].mid, tm[q].s13, em, g, m2g, am[q + 1], am[q], am[q - 1]);
+      adj_role<2>(tm[q - 1].dn, tm[q - 1].s13, ed, g, m2g, am[q], am[q - 1], am[q - 2]);
     }
     const int k = f - 3;  // output point completed by this face
     if (k >= 0 && k < ARUN) {
@@ -456,18 +466,20 @@ __device__ __forceinline__ void adj_phi_line_f32(const float* __restrict__ ph, c
     if (q + 2 < ND) diff(q + 2);
     if (q + 1 < ND - 1) tri(q + 1);
     const float bm = hm[i * S], bp = hp[i * S];
-    float W, g, m2g;
+    float eu, em, ed, g, m2g;
     if (bm != 0.0f) {
-      adj_face_w(tl[q - 2].up, tl[q - 1].mid, tl[q].dn, bm, W, g, m2g);
-      adj_role<0>(tl[q - 2].up, tl[q - 2].s13, W, g, m2g, Db[q - 3], Db[q - 2], Db[q - 1]);
-      adj_role<1>(tl[q - 1].mid, tl[q - 1].s13, W, g, m2g, Db[q - 2], Db[q - 1], Db[q]);
-      adj_role<2>(tl[q].dn, tl[q].s13, W, g, m2g, Db[q - 1], Db[q], Db[q + 1]);
+      adj_face_w(tl[q - 2].up, tl[q - 1].mid, tl[q].dn, tl[q - 2].s13, tl[q - 1].s13, tl[q].s13, bm, eu, em, ed, g,
+                 m2g);
+      adj_role<0>(tl[q - 2].up, tl[q - 2].s13, eu, g, m2g, Db[q - 3], Db[q - 2], Db[q - 1]);
+      adj_role<1>(tl[q - 1].mid, tl[q - 1].s13, em, g, m2g, Db[q - 2], Db[q - 1], Db[q]);
+      adj_role<2>(tl[q].dn, tl[q].s13, ed, g, m2g, Db[q - 1], Db[q], Db[q + 1]);
     }
     if (bp != 0.0f) {
-      adj_face_w(tr[q + 1].up, tr[q].mid, tr[q - 1].dn, bp, W, g, m2g);
-      adj_role<0>(tr[q + 1].up, tr[q + 1].s13, W, g, m2g, Db[q + 2], Db[q + 1], Db[q]);
-      adj_role<1>(tr[q].mid, tr[q].s13, W, g, m2g, Db[q + 1], Db[q], Db[q - 1]);
-      adj_role<2>(tr[q - 1].dn, tr[q - 1].s13, W, g, m2g, Db[q], Db[q - 1], Db[q - 2]);
+      adj_face_w(tr[q + 1].up, tr[q].mid, tr[q - 1].dn, tr[q + 1].s13, tr[q].s13, tr[q - 1].s13, bp, eu, em, ed, g,
+                 m2g);
+      adj_role<0>(tr[q + 1].up, tr[q + 1].s13, eu, g, m2g, Db[q + 2], Db[q + 1], Db[q]);
+      adj_role<1>(tr[q].mid, tr[q].s13, em, g, m2g, Db[q + 1], Db[q], Db[q - 1]);
+      adj_role<2>(tr[q - 1].dn, tr[q - 1].s13, ed, g, m2g, Db[q], Db[q - 1], Db[q - 2]);
     }
     const int k = i - 3;  // output whose two differences are complete
     if (k >= 0 && k < ARUN) dst[k * DS] += (Db[k - 1 + 6] - Db[k + 6]) * rd;

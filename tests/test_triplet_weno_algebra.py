@@ -120,7 +120,10 @@ def test_candidate_values_and_scaled_indicators():
 
 # ---- the FP32 adjoint's triplet form: per role of a face, gbar dW/d(a', b', c') = WG dq_r + A (1, -2, 1) +
 # B dt_r with WG = gbar a_r / sum a, cg = -2 gbar (q_r - W) (a_r / D_r) / sum a, A = 13/6 s cg, B = h_r cg
-# (indicators unscaled, eps = 1e-6 on the split fluxes themselves).
+# (indicators unscaled, eps = 1e-6 on the split fluxes themselves), where q_r - W is formed from the
+# triplets' second differences: w_r = a_r / sum a, D01 = (s_up - s_mid) / 3, D12 = (s_dn - s_mid) / 6,
+# D02 = D01 + D12, q_up - W = w_mid D01 + w_dn D02, q_mid - W = w_dn D12 - w_up D01,
+# q_dn - W = -(w_up D02 + w_mid D12).
 ADJ_DQ = ((sp.Rational(2, 6), sp.Rational(-7, 6), sp.Rational(11, 6)),
           (sp.Rational(-1, 6), sp.Rational(5, 6), sp.Rational(2, 6)),
           (sp.Rational(2, 6), sp.Rational(5, 6), sp.Rational(-1, 6)))
@@ -147,9 +150,15 @@ def adj_face(roles, gbar):
     sa = sum(r[1] for r, _, _ in roles)
     W = sum(r[1] * r[0] for r, _, _ in roles) / sa
     g, m2g = gbar / sa, -2 * gbar / sa
+    w = [r[1] / sa for r, _, _ in roles]
+    su13, sm13, sd13 = (s13 for _, s13, _ in roles)
+    d01, d12 = (su13 - sm13) * sp.Rational(2, 13), (sd13 - sm13) * sp.Rational(1, 13)
+    d02 = d01 + d12
+    qmw = (w[1] * d01 + w[2] * d02, w[2] * d12 - w[0] * d01, -(w[0] * d02 + w[1] * d12))
     out = {}
     for k, ((q, a, nr, h), s13, pts) in enumerate(roles):
-        WG, cg = a * g, (q - W) * nr * m2g
+        assert sp.simplify(qmw[k] - (q - W)) == 0  # the candidate-difference identity
+        WG, cg = a * g, qmw[k] * nr * m2g
         A, B = s13 * cg, h * cg
         for j, (pt, dq, dt, da) in enumerate(zip(pts, ADJ_DQ[k], ADJ_DT[k], (1, -2, 1))):
             out[pt] = out.get(pt, 0) + WG * dq + B * dt + A * da
