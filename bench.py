@@ -318,6 +318,7 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
     hs = [hydro.Hydro(p, dtype=dtype) for p in members]
     Us = [h.state(p.U0) for h, p in zip(hs, members)]
     cells = sum(p.cells for p in members)
+    tune_ms, best = hydro.hydro_batch_autotune(hs, Us, steps=3) if args.autotune else (None, None)
     hydro.hydro_batch_step(hs, Us, args.warmup)
     torch.cuda.synchronize()
     l0 = sum(h.launch_count() for h in hs)
@@ -342,7 +343,9 @@ def run_ensemble(args, members, dtype, rank, world, barrier):
     if rank == 0:
         sizes = sorted({(p.nx, p.ny) for p in members})
         cfg = {"workload": args.workload, "members": len(members), "cells": cells, "sizes": len(sizes),
-               "seed": members[0].seed, "graph": "3 persistent launches per step, replayed from a CUDA graph"}
+               "seed": members[0].seed, "graph": "3 persistent launches per step, replayed from a CUDA graph",
+               "autotune": None if best is None else {"best": hydro.batch_trial(best),
+                                                      "trials_ms_per_step": [round(float(x), 4) for x in tune_ms]}}
         print(json.dumps(_line(args, world, replica_rate(cells * args.steps, ms * 1e-3, world), ms, dtype, cfg,
                                {"roofline": roof, "roofline_hbm": roof_hbm, "gpu_launches": launches,
                                 "clocks": clk})), flush=True)
@@ -464,6 +467,9 @@ def config_records(args, local):
     cells = sum(p.cells for p in members)
     hydro.hydro_batch_step(hs, Us, 3)
     steps = 10
+    ms_default, _, _ = _timed(lambda: hydro.hydro_batch_step(hs, Us, steps), local)
+    tune_ms, best = hydro.hydro_batch_autotune(hs, Us, steps=3)
+    hydro.hydro_batch_step(hs, Us, 1)
     ms, clk, _ = _timed(lambda: hydro.hydro_batch_step(hs, Us, steps), local)
     for h in hs:
         h.close()
@@ -473,7 +479,11 @@ def config_records(args, local):
         "ms_per_step": ms / steps, "value": cells * steps / (ms * 1e-3), "unit": UNIT,
         "roofline_hbm": {"achieved": alg / (ms / steps * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (ms / steps * 1e-3) / 1e9 / peak},
-        "note": "timed region includes each call's packing and unpacking of the 64 caller states", "clocks": clk}
+        "note": "timed region includes each call's packing and unpacking of the 64 caller states", "clocks": clk,
+        "default_plan_ms_per_step": ms_default / steps,
+        "autotune": {"best": hydro.batch_trial(best), "trials_ms_per_step": {
+            f"v{hydro.batch_trial(i)['variant']}_w{hydro.batch_trial(i)['waves']}_{hydro.batch_trial(i)['layout']}":
+            round(float(x), 4) for i, x in enumerate(tune_ms)}}}
     del hs, Us, members
     # C4: the gradient configuration
     prob, _ = wl.fourier_modes(256, nsteps=200)

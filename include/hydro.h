@@ -256,6 +256,18 @@ int hydro_tile_info(hydro_ctx* ctx, int variant, int* tile_x, int* tile_y, int* 
  * fastest; per-variant milliseconds per step go to ms_out[n] (may be NULL). */
 int hydro_autotune(hydro_ctx* ctx, const void* U, int steps, double* ms_out);
 
+/* Autotuner of a batched ensemble's plan (the members and states of hydro_batch_step). Times, on the
+ * batch's own mixed-size work list, every combination of tile variant v (0 .. 2), persistent grid size w
+ * (0: one wave of resident CTAs, 1: two waves) and work-list layout l (0: each CTA a contiguous run of
+ * the member-ordered tiles, row by row; 1: the same run with each member's tiles column by column; 2: the
+ * tiles dealt out one by one), `steps` graph-replayed steps each after one untimed step, on the members'
+ * working copies: U is read, never written. Keeps the fastest as the plan of later hydro_batch_step calls
+ * with these members (members[0] holds it). ms_out[18] (may be NULL) receives ms per step of trial
+ * (v * 2 + w) * 3 + l, -1 where the variant does not fit; *best (may be NULL) the trial kept. Errors as
+ * hydro_batch_step; a non-physical state does not stop the timing. Synchronises the stream. */
+int hydro_batch_autotune(hydro_ctx* const* members, void* const* U, int nmembers, int steps, double* ms_out,
+                         int* best);
+
 /* Per-launch timing of the stage kernels: with enable = 1, every stage launch is bracketed by CUDA
  * events on the context's stream; hydro_stage_timing returns the launches and the summed device time
  * since the last enable (synchronises the stream). */

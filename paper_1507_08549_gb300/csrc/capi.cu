@@ -122,10 +122,15 @@ struct hydro_ctx {
   std::vector<unsigned long long> plan_members;
   std::vector<unsigned long long> plan_gens;
   int plan_variant = -1;
+  int plan_waves = 0, plan_layout = -1;  // the plan's grid size (CTA waves) and work-list layout
+  int plan_grid = 0;
   void* plan_params = nullptr;  // device GridParams[3][nmembers]
   void* plan_work = nullptr;    // device WorkItem[nwork]
   int plan_nwork = 0;
   cudaGraphExec_t plan_graph = nullptr;
+  // batch plan shape chosen by hydro_batch_autotune (on the first member): persistent CTAs in
+  // batch_waves waves of (CTAs per SM x SMs), work-list layout (BatchLayout)
+  int batch_waves = 1, batch_layout = 0;
   std::string err;
 };
 
@@ -929,8 +934,18 @@ int hydro_autotune(hydro_ctx* c, const void* U, int steps, double* ms_out) {
 
 // ---- batched ensembles
 
+// Work-list layouts of a batch plan. The list of (member, tile) items is member-ordered; each persistent
+// CTA takes a contiguous run of it (RUNS_ROWS: a member's tiles row by row; RUNS_COLUMNS: column by
+// column, so that a CTA's consecutive tiles share halo rows), or the items are dealt out one by one
+// (INTERLEAVED: CTA b takes items b, b + G, ...).
+enum BatchLayout { BATCH_RUNS_ROWS = 0, BATCH_RUNS_COLUMNS = 1, BATCH_INTERLEAVED = 2, BATCH_LAYOUTS = 3 };
+constexpr int BATCH_WAVES = 2;  // grid sizes tried: 1 or 2 waves of resident CTAs
+
+// ms_graph != null: time the graph replays of the nsteps steps alone (events) into *ms_graph;
+// writeback = false: the members' working states are stepped but U is neither written nor t updated.
 template <typename real>
-static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, double* t) {
+static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, double* t, bool writeback = true,
+                      double* ms_graph = nullptr) {
   hydro_ctx* c = m[0];
   // every member on the first member's tile variant
   for (int k = 0; k < n; ++k) {
@@ -940,7 +955,8 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
       if (rc) return fail(c, rc, "member " + std::to_string(k) + ": " + m[k]->err);
     }
   }
-  bool same = (int)c->plan_members.size() == n && c->plan_variant == c->variant;
+  bool same = (int)c->plan_members.size() == n && c->plan_variant == c->variant &&
+              c->plan_waves == c->batch_waves && c->plan_layout == c->batch_layout;
   for (int k = 0; same && k < n; ++k) same = c->plan_members[k] == m[k]->uid && c->plan_gens[k] == m[k]->params_gen;
   if (!same) {
     if (c->plan_graph) {
@@ -964,22 +980,32 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
         P[(size_t)s * n + k].ext_div = nullptr;  // the batched launch computes every field itself
       }
     }
-    // CTA b of the persistent launch takes items b, b + G, b + 2G, ...: give it a contiguous run of the
-    // member-ordered tile list, so that it changes member (a flush and a parameter reload) only at run
-    // boundaries; every CTA gets the same number of tiles (within one)
+    // CTA b of the persistent launch takes items b, b + G, b + 2G, ...: with the RUNS layouts it gets a
+    // contiguous run of the member-ordered tile list, so that it changes member (a flush and a parameter
+    // reload) only at run boundaries; every CTA gets the same number of tiles (within one)
     std::vector<WorkItem> L;
     for (int k = 0; k < n; ++k) {
-      const int nt = m[k]->tiles_x * ((m[k]->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
-      for (int t = 0; t < nt; ++t) L.push_back(WorkItem{k, t});
+      const int tx_n = m[k]->tiles_x, ty_n = (m[k]->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant);
+      if (c->batch_layout == BATCH_RUNS_COLUMNS) {
+        for (int tx = 0; tx < tx_n; ++tx)
+          for (int ty = 0; ty < ty_n; ++ty) L.push_back(WorkItem{k, ty * tx_n + tx});
+      } else {
+        for (int t = 0; t < tx_n * ty_n; ++t) L.push_back(WorkItem{k, t});
+      }
     }
     const int total = (int)L.size();
-    const int G = grid_for(c, total);
-    W.assign(total, WorkItem{0, 0});
-    for (int b = 0, start = 0; b < G; ++b) {
-      const int cnt = (total - b + G - 1) / G;  // items w = b + kG < total
-      for (int k = 0; k < cnt; ++k) W[b + (size_t)k * G] = L[start + k];
-      start += cnt;
+    const int G = std::max(1, std::min(total, grid_for(c, total) * std::max(1, c->batch_waves)));
+    if (c->batch_layout == BATCH_INTERLEAVED) {
+      W = L;
+    } else {
+      W.assign(total, WorkItem{0, 0});
+      for (int b = 0, start = 0; b < G; ++b) {
+        const int cnt = (total - b + G - 1) / G;  // items w = b + kG < total
+        for (int k = 0; k < cnt; ++k) W[b + (size_t)k * G] = L[start + k];
+        start += cnt;
+      }
     }
+    c->plan_grid = G;
     CK(cudaMalloc(&c->plan_params, sizeof(GridParams<real>) * P.size()));
     CK(cudaMalloc(&c->plan_work, sizeof(WorkItem) * W.size()));
     CK(cudaMemcpy(c->plan_params, P.data(), sizeof(GridParams<real>) * P.size(), cudaMemcpyHostToDevice));
@@ -990,6 +1016,8 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
       c->plan_gens.push_back(m[k]->params_gen);
     }
     c->plan_variant = c->variant;
+    c->plan_waves = c->batch_waves;
+    c->plan_layout = c->batch_layout;
   }
   for (int k = 0; k < n; ++k) {
     hydro_ctx* mk = m[k];
@@ -1002,7 +1030,7 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
                          t ? t[k] : 0.0, c->stream));
     c->launches++;
   }
-  const int grid = grid_for(c, c->plan_nwork);
+  const int grid = c->plan_grid;
   const GridParams<real>* P = static_cast<const GridParams<real>*>(c->plan_params);
   const WorkItem* W = static_cast<const WorkItem*>(c->plan_work);
   auto launch3 = [&](cudaStream_t s) -> int {
@@ -1023,17 +1051,24 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
   }
+  cudaEvent_t g0 = nullptr, g1 = nullptr;
+  if (ms_graph) {
+    CK(cudaEventCreate(&g0));
+    CK(cudaEventCreate(&g1));
+    CK(cudaEventRecord(g0, c->stream));
+  }
   for (int s = 0; s < nsteps; ++s) {
     CK(cudaGraphLaunch(c->plan_graph, c->stream));
     c->launches += 3;
   }
+  if (ms_graph) CK(cudaEventRecord(g1, c->stream));
   int worst = HYDRO_OK;
   for (int k = 0; k < n; ++k) {
     hydro_ctx* mk = m[k];
     // members' unpack and status copies go on the batch stream
     cudaStream_t keep = mk->stream;
     mk->stream = c->stream;
-    int rc = unpack_state<real>(mk, static_cast<real*>(U[k]), 0);
+    int rc = writeback ? unpack_state<real>(mk, static_cast<real*>(U[k]), 0) : HYDRO_OK;
     if (!rc) {
       CK(cudaMemcpyAsync(mk->host_scratch, mk->scratch, sizeof(Scratch<real>), cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1041,10 +1076,17 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     if (rc) return fail(c, rc, mk->err);
   }
   int rc = wait_stream(c);
+  if (ms_graph) {
+    float ms = 0.f;
+    if (!rc) cudaEventElapsedTime(&ms, g0, g1);
+    *ms_graph = ms;
+    cudaEventDestroy(g0);
+    cudaEventDestroy(g1);
+  }
   if (rc) return rc;
   for (int k = 0; k < n; ++k) {
     const Scratch<real>* hs = static_cast<const Scratch<real>*>(m[k]->host_scratch);
-    if (t) t[k] = hs->t_acc;
+    if (t && writeback) t[k] = hs->t_acc;
     if (hs->err & ERR_LAYOUT) worst = fail(c, HYDRO_ECUDA, "internal: stage kernel shared memory not 128-byte aligned");
     else if (hs->err & ERR_TIMEOUT) worst = fail(c, HYDRO_ETIMEOUT, "member " + std::to_string(k) + ": device wait gave up");
     else if ((hs->err & ERR_NONPHYSICAL) && worst == HYDRO_OK)
@@ -1053,11 +1095,8 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
   return worst;
 }
 
-int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nsteps, double* t) {
-  if (!members || !U || n < 1 || nsteps < 0) return HYDRO_EINVAL;
+static int batch_check(hydro_ctx* const* members, void* const* U, int n) {
   hydro_ctx* c = members[0];
-  int rc = check_ctx(c);
-  if (rc) return rc;
   for (int k = 0; k < n; ++k) {
     if (!members[k] || !U[k]) return fail(c, HYDRO_EINVAL, "null member or state");
     if (members[k]->cfg.dtype != c->cfg.dtype || members[k]->nf != c->nf || members[k]->device != c->device)
@@ -1065,8 +1104,74 @@ int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nstep
     if (members[k]->cfg.scheme != HYDRO_SCHEME_COMPONENT)
       return fail(c, HYDRO_EINVAL, "batched steps take component-wise contexts (step characteristic ones one by one)");
   }
+  return HYDRO_OK;
+}
+
+int hydro_batch_step(hydro_ctx* const* members, void* const* U, int n, int nsteps, double* t) {
+  if (!members || !U || n < 1 || nsteps < 0) return HYDRO_EINVAL;
+  hydro_ctx* c = members[0];
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  rc = batch_check(members, U, n);
+  if (rc) return rc;
   if (c->cfg.dtype == HYDRO_F64) return batch_impl<double>(members, U, n, nsteps, t);
   return batch_impl<float>(members, U, n, nsteps, t);
+}
+
+int hydro_batch_autotune(hydro_ctx* const* members, void* const* U, int n, int steps, double* ms_out, int* best) {
+  if (!members || !U || n < 1 || steps < 1) return HYDRO_EINVAL;
+  hydro_ctx* c = members[0];
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  rc = batch_check(members, U, n);
+  if (rc) return rc;
+  const bool f64 = c->cfg.dtype == HYDRO_F64;
+  const int keep_v = c->variant, keep_w = c->batch_waves, keep_l = c->batch_layout;
+  double best_ms = 1e300;
+  int best_i = -1;
+  for (int v = 0; v < NUM_VARIANTS; ++v) {
+    const bool fits = (f64 ? stage_ctas_per_sm<double>(v, c->nf) : stage_ctas_per_sm<float>(v, c->nf)) >= 1;
+    for (int w = 0; w < BATCH_WAVES; ++w) {
+      for (int l = 0; l < BATCH_LAYOUTS; ++l) {
+        const int i = (v * BATCH_WAVES + w) * BATCH_LAYOUTS + l;
+        double ms = -1.0;
+        if (fits) {
+          c->variant = v;
+          c->batch_waves = w + 1;
+          c->batch_layout = l;
+          // one untimed step (plan, graph), then `steps` timed graph replays; U is only read
+          rc = f64 ? batch_impl<double>(members, U, n, 1, nullptr, false) : batch_impl<float>(members, U, n, 1, nullptr, false);
+          double g = 0.0;
+          if (!rc || rc == HYDRO_ENONPHYSICAL)
+            rc = f64 ? batch_impl<double>(members, U, n, steps, nullptr, false, &g)
+                     : batch_impl<float>(members, U, n, steps, nullptr, false, &g);
+          if (rc && rc != HYDRO_ENONPHYSICAL) {
+            c->variant = keep_v;
+            c->batch_waves = keep_w;
+            c->batch_layout = keep_l;
+            return rc;
+          }
+          ms = g / steps;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_i = i;
+          }
+        }
+        if (ms_out) ms_out[i] = ms;
+      }
+    }
+  }
+  if (best_i < 0) {
+    c->variant = keep_v;
+    c->batch_waves = keep_w;
+    c->batch_layout = keep_l;
+    return fail(c, HYDRO_EINVAL, "no tile variant fits the device");
+  }
+  c->variant = best_i / (BATCH_WAVES * BATCH_LAYOUTS);
+  c->batch_waves = (best_i / BATCH_LAYOUTS) % BATCH_WAVES + 1;
+  c->batch_layout = best_i % BATCH_LAYOUTS;
+  if (best) *best = best_i;
+  return upload(c);
 }
 
 // ---- discrete adjoint (frozen dt and stage alphas) and two-level checkpointing

@@ -45,7 +45,8 @@ EXPORTS = [
     "hydro_init", "hydro_destroy", "hydro_last_error", "hydro_set_stream", "hydro_step", "hydro_step_host",
     "hydro_rhs", "conserved_totals", "hydro_last_totals", "hydro_record", "hydro_get_log", "hydro_step_frozen",
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
-    "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_profile",
+    "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_batch_autotune",
+    "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
     "hydro_poisson", "hydro_exact_sum", "hydro_wait_selftest", "hydro_fma_probe",
 ]
@@ -98,6 +99,8 @@ def load(build_if_needed: bool = True):
             "hydro_set_tile_variant": ([ctxp, ctypes.c_int], ctypes.c_int),
             "hydro_tile_info": ([ctxp, ctypes.c_int, ip, ip, ip, ip], ctypes.c_int),
             "hydro_autotune": ([ctxp, vp, ctypes.c_int, dp], ctypes.c_int),
+            "hydro_batch_autotune": ([ctypes.POINTER(ctxp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, dp, ip],
+                                     ctypes.c_int),
             "hydro_profile": ([ctxp, ctypes.c_int], ctypes.c_int),
             "hydro_stage_timing": ([ctxp, ip, dp], ctypes.c_int),
             "hydro_launch_count": ([ctxp], ctypes.c_longlong),
@@ -402,6 +405,36 @@ def hydro_batch_step(members: list[Hydro], states: list, nsteps: int, t=None):
         msg = lib.hydro_last_error(members[0].ctx)
         raise HydroError(rc, f"hydro_batch_step: {msg.decode() if msg else ''}")
     return tt
+
+
+BATCH_TUNE_TRIALS = 18  # 3 tile variants x 2 grid sizes x 3 work-list layouts
+
+
+def batch_trial(i: int) -> dict:
+    """The plan of autotuner trial i: tile variant, CTA waves and work-list layout."""
+    return {"variant": i // 6, "waves": (i // 3) % 2 + 1,
+            "layout": ("runs_rows", "runs_columns", "interleaved")[i % 3]}
+
+
+def hydro_batch_autotune(members: list, states: list, steps: int = 3):
+    """Time every batch plan (tile variant x grid size x work-list layout) on this ensemble's work list and
+    keep the fastest for later hydro_batch_step calls with these members (C ABI hydro_batch_autotune; the
+    states are read, not written). Returns (ms per step of each of the 18 trials, -1 if it does not fit;
+    the index kept)."""
+    n = len(members)
+    if n == 0 or len(states) != n:
+        raise HydroError(EINVAL, f"hydro_batch_autotune: {n} members and {len(states)} states")
+    lib = members[0].lib
+    ctxs = (ctypes.c_void_p * n)(*[m.ctx.value for m in members])
+    ptrs = (ctypes.c_void_p * n)(*[m._ptr(U).value for m, U in zip(members, states)])
+    ms = np.full(BATCH_TUNE_TRIALS, -1.0)
+    best = ctypes.c_int(-1)
+    rc = lib.hydro_batch_autotune(ctxs, ptrs, n, int(steps), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.byref(best))
+    if rc != OK:
+        msg = lib.hydro_last_error(members[0].ctx)
+        raise HydroError(rc, f"hydro_batch_autotune: {msg.decode() if msg else ''}")
+    return ms, best.value
 
 
 def _autograd():

@@ -477,3 +477,32 @@ def test_batched_ensemble_ctas_cross_members(record_property):
             record_property("err:fp32_rel_l1_ensemble45_worst", worst)
         for h in hs:
             h.close()
+
+
+def test_batch_autotune_keeps_the_fastest_plan(record_property):
+    """The ensemble autotuner times all 18 plans (tile variant x grid size x work-list layout) on the batch's
+    own work list, leaves the caller's states untouched, keeps the fastest trial, and the tuned plan gives
+    the same bits as the default plan (the plans differ only in which CTA computes which tile)."""
+    import torch
+    hydro = _hydro()
+    members = wl.quadrant_ensemble(12, seed=3, sizes=(128, 256), nsteps=4)
+    hs = [hydro.Hydro(p, dtype="f32") for p in members]
+    Us = [h.state(p.U0) for h, p in zip(hs, members)]
+    before = [U.clone() for U in Us]
+    ms, best = hydro.hydro_batch_autotune(hs, Us, steps=2)
+    assert all(torch.equal(a, b) for a, b in zip(before, Us))
+    fits = ms > 0
+    assert fits.sum() >= 12 and best >= 0 and ms[best] == ms[fits].min()
+    default = (1 * 2 + 0) * 3 + 0  # variant 1, one wave of CTAs, row-ordered runs
+    record_property("err:batch_tuned_over_default_ms", ms[best] / ms[default])
+    t = hydro.hydro_batch_step(hs, Us, 4)
+    hd = [hydro.Hydro(p, dtype="f32") for p in members]
+    Ud = [h.state(p.U0) for h, p in zip(hd, members)]
+    td = hydro.hydro_batch_step(hd, Ud, 4)
+    for a, b in zip(Us, Ud):
+        assert torch.equal(a, b)
+    np.testing.assert_array_equal(t, td)
+    ref, _, _ = oracle.step(members[0], members[0].U0, 4)
+    assert rel_l1(Us[0].double().cpu().numpy(), ref) <= F32_SHOCK
+    for h in hs + hd:
+        h.close()
