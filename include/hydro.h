@@ -229,6 +229,17 @@ int hydro_forward_checkpointed(hydro_ctx* ctx, void* U, int nsteps, int checkpoi
  * kept, so the sweep may be repeated for another lambda. HYDRO_ESTATE when no checkpointed run exists. */
 int hydro_adjoint_sweep(hydro_ctx* ctx, void* lambda);
 
+/* Forward run of nsteps steps from U (advanced in place to U^N) for a reverse sweep on a binomial
+ * checkpoint schedule (revolve: Griewank & Walther, ACM TOMS 26, 2000) under a memory budget: only U^0
+ * and the recorded dt / alphas are kept; the next hydro_adjoint_sweep reverses the run with `snapshots`
+ * (0 .. 4096) further state slots, recomputing forward segments from the nearest stored state, and takes
+ * the least recomputation that budget allows (with s slots and t sweeps over the run, C(s + t, s) steps can
+ * be reversed). Device memory: snapshots + 2 states. *sweep_forward_steps (may be NULL) receives the
+ * forward steps the sweep will recompute. The adjoint steps see the same states as under
+ * hydro_forward_checkpointed, so the gradient is the same, bit for bit. HYDRO_EINVAL for bad arguments or a
+ * characteristic-scheme context. */
+int hydro_forward_revolve(hydro_ctx* ctx, void* U, int nsteps, int snapshots, long long* sweep_forward_steps);
+
 /* ---- batched ensembles ------------------------------------------------------------------------ */
 
 /* Advance nmembers independent grids (each with its own context, all of one dtype and nfields) by

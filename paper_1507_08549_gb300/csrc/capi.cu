@@ -97,6 +97,12 @@ struct hydro_ctx {
   void* seg = nullptr;
   size_t seg_cap = 0;
   int ck_nsteps = -1, ck_every = 0;
+  // binomial (revolve) schedule: ck_mode 1 keeps only U^0 (slot 0 of rv_slots) and reverses with
+  // rv_snapshots further state slots plus one recomputation buffer
+  int ck_mode = 0;
+  int rv_snapshots = 0;
+  void* rv_slots = nullptr;
+  size_t rv_cap = 0;
   // characteristic scheme: padded D = dF/dx + dG/dy of the 4 hydro fields, written per stage
   void* char_div = nullptr;
   // FP64 grids with fewer tiles than half the SMs: the same D, written per stage by a field-split launch
@@ -651,6 +657,7 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->adj_acc);
   cudaFree(c->ckpt);
   cudaFree(c->seg);
+  cudaFree(c->rv_slots);
   cudaFree(c->front);
   cudaFree(c->front_count);
   cudaFree(c->char_div);
@@ -1318,6 +1325,113 @@ int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
   }
   c->ck_nsteps = nsteps;
   c->ck_every = every;
+  c->ck_mode = 0;
+  return HYDRO_OK;
+}
+
+// ---- binomial checkpointing (revolve; Griewank 1992, Griewank & Walther 2000)
+//
+// Reversing n steps from a stored state with s free state slots: store the state at some m in a free
+// slot, reverse [m, n) with s - 1 free slots, then [0, m) with s; with no free slot every step's state is
+// recomputed from the start (n (n - 1) / 2 forward steps). With c = s + 1 slots counting the start's and
+// t the least number of sweeps with C(c + t, c) >= n, the fewest forward steps any such schedule needs is
+// P(n, s) = t n - C(c + 1 + t - 1, t - 1) (Griewank's bound); the split taken at each level is the m that
+// minimises m + P(n - m, s - 1) + P(m, s), so the whole schedule attains P(n, s).
+
+static long long rv_binom(int c, int t) {  // C(c + t, t), exact while it fits (saturates at 2^62)
+  long long b = 1;
+  const int k_max = std::min(c, t), big = std::max(c, t);
+  for (int k = 1; k <= k_max; ++k) {
+    if (b > (1LL << 62) / (big + k)) return 1LL << 62;
+    b = b * (big + k) / k;
+  }
+  return b;
+}
+
+static long long rv_cost(int n, int s) {  // P(n, s)
+  if (n <= 1) return 0;
+  if (s == 0) return (long long)n * (n - 1) / 2;
+  const int c = s + 1;
+  int t = 0;
+  while (rv_binom(c, t) < n) ++t;
+  return (long long)t * n - rv_binom(c + 1, t - 1);
+}
+
+static int rv_split(int n, int s) {  // the checkpoint m (1 .. n-1) for n >= 2 and s >= 1
+  long long best = -1;
+  int bm = 1;
+  for (int m = 1; m < n; ++m) {
+    const long long v = m + rv_cost(n - m, s - 1) + rv_cost(m, s);
+    if (best < 0 || v < best) {
+      best = v;
+      bm = m;
+    }
+  }
+  return bm;
+}
+
+template <typename real>
+static int rv_advance(hydro_ctx* c, real* U, int from, int to, const std::vector<double>& dtl,
+                      const std::vector<double>& al) {
+  for (int st = from; st < to; ++st) {
+    const int rc = step_impl<real>(c, U, 1, nullptr, nullptr, &dtl[st], &al[6 * (size_t)st]);
+    if (rc) return rc;
+  }
+  return HYDRO_OK;
+}
+
+// Reverse steps [a, b): slot `level` holds the state at a, slots level+1 .. nslots-1 are free, tmp is the
+// recomputation buffer.
+template <typename real>
+static int rv_reverse(hydro_ctx* c, real* lam, real* slots, int nslots, real* tmp, int level, int a, int b,
+                      size_t elems, const std::vector<double>& dtl, const std::vector<double>& al) {
+  const size_t state = elems * sizeof(real);
+  real* Ua = slots + elems * (size_t)level;
+  const int n = b - a, s = nslots - 1 - level;
+  if (n == 1) return adjoint_step_impl<real>(c, Ua, lam, dtl[a], &al[6 * (size_t)a]);
+  if (s == 0) {
+    for (int k = b - 1; k >= a; --k) {
+      CK(cudaMemcpyAsync(tmp, Ua, state, cudaMemcpyDeviceToDevice, c->stream));
+      int rc = rv_advance<real>(c, tmp, a, k, dtl, al);
+      if (!rc) rc = adjoint_step_impl<real>(c, tmp, lam, dtl[k], &al[6 * (size_t)k]);
+      if (rc) return rc;
+    }
+    return HYDRO_OK;
+  }
+  const int m = a + rv_split(n, s);
+  real* Um = slots + elems * (size_t)(level + 1);
+  CK(cudaMemcpyAsync(Um, Ua, state, cudaMemcpyDeviceToDevice, c->stream));
+  int rc = rv_advance<real>(c, Um, a, m, dtl, al);
+  if (!rc) rc = rv_reverse<real>(c, lam, slots, nslots, tmp, level + 1, m, b, elems, dtl, al);
+  if (!rc) rc = rv_reverse<real>(c, lam, slots, nslots, tmp, level, a, m, elems, dtl, al);
+  return rc;
+}
+
+int hydro_forward_revolve(hydro_ctx* c, void* U, int nsteps, int snapshots, long long* sweep_forward_steps) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || nsteps < 1 || snapshots < 0 || snapshots > 4096) return fail(c, HYDRO_EINVAL, "bad arguments");
+  if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
+    return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");
+  const size_t state = (size_t)c->nf * c->cfg.nx * c->cfg.ny * c->esize;
+  const size_t need = (size_t)snapshots + 2;  // U^0, the snapshots, the recomputation buffer
+  if (c->rv_cap < need) {
+    cudaFree(c->rv_slots);
+    c->rv_slots = nullptr;
+    c->rv_cap = 0;
+    CK(cudaMalloc(&c->rv_slots, state * need));
+    c->rv_cap = need;
+  }
+  rc = hydro_record(c, nsteps);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->rv_slots, U, state, cudaMemcpyDeviceToDevice, c->stream));
+  double t = 0.0;
+  rc = hydro_step(c, U, nsteps, &t, nullptr);
+  if (rc) return rc;
+  c->ck_nsteps = nsteps;
+  c->ck_mode = 1;
+  c->rv_snapshots = snapshots;
+  if (sweep_forward_steps) *sweep_forward_steps = rv_cost(nsteps, std::min(snapshots, nsteps));
   return HYDRO_OK;
 }
 
@@ -1353,6 +1467,16 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
   if (rc) return rc;
   const size_t elems = (size_t)c->nf * c->cfg.nx * c->cfg.ny;
   const size_t state = elems * sizeof(real);
+  if (c->ck_mode == 1) {  // binomial schedule from U^0
+    real* slots = static_cast<real*>(c->rv_slots);
+    const int nslots = c->rv_snapshots + 1;
+    CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
+    c->defer_status = true;
+    rc = rv_reverse<real>(c, lam, slots, nslots, slots + elems * (size_t)nslots, 0, 0, N, elems, dtl, al);
+    c->defer_status = false;
+    if (rc) return rc;
+    return read_status<real>(c, nullptr, nullptr);
+  }
   if (c->seg_cap < (size_t)every) {
     cudaFree(c->seg);
     c->seg = nullptr;
@@ -1374,7 +1498,8 @@ int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!lambda) return fail(c, HYDRO_EINVAL, "null lambda");
-  if (c->ck_nsteps < 1 || !c->ckpt) return fail(c, HYDRO_ESTATE, "no checkpointed forward run to reverse");
+  if (c->ck_nsteps < 1 || (c->ck_mode == 0 && !c->ckpt) || (c->ck_mode == 1 && !c->rv_slots))
+    return fail(c, HYDRO_ESTATE, "no checkpointed forward run to reverse");
   if (c->cfg.dtype == HYDRO_F64) return sweep_impl<double>(c, (double*)lambda);
   return sweep_impl<float>(c, (float*)lambda);
 }

@@ -44,7 +44,8 @@ class hydro_config(ctypes.Structure):
 EXPORTS = [
     "hydro_init", "hydro_destroy", "hydro_last_error", "hydro_set_stream", "hydro_step", "hydro_step_host",
     "hydro_rhs", "conserved_totals", "hydro_last_totals", "hydro_record", "hydro_get_log", "hydro_step_frozen",
-    "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_batch_step",
+    "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_forward_revolve",
+    "hydro_batch_step",
     "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_batch_autotune",
     "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
@@ -93,6 +94,8 @@ def load(build_if_needed: bool = True):
             "hydro_adjoint_step": ([ctxp, vp, vp, ctypes.c_double, dp], ctypes.c_int),
             "hydro_forward_checkpointed": ([ctxp, vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "hydro_adjoint_sweep": ([ctxp, vp], ctypes.c_int),
+            "hydro_forward_revolve": ([ctxp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
+                                      ctypes.c_int),
             "hydro_batch_step": ([ctypes.POINTER(ctxp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, dp],
                                  ctypes.c_int),
             "hydro_tile_variants": ([ctxp, ip, ip], ctypes.c_int),
@@ -279,6 +282,14 @@ class Hydro:
         self._check(self.lib.hydro_forward_checkpointed(self.ctx, self._ptr(U), int(nsteps), int(checkpoint_every)),
                     "hydro_forward_checkpointed")
 
+    def forward_revolve(self, U, nsteps: int, snapshots: int) -> int:
+        """Forward run for a binomial-schedule reverse sweep with `snapshots` state slots (hydro_forward_revolve);
+        returns the forward steps the next adjoint_sweep will recompute."""
+        n = ctypes.c_longlong(0)
+        self._check(self.lib.hydro_forward_revolve(self.ctx, self._ptr(U), int(nsteps), int(snapshots), ctypes.byref(n)),
+                    "hydro_forward_revolve")
+        return n.value
+
     def adjoint_sweep(self, lam):
         self._check(self.lib.hydro_adjoint_sweep(self.ctx, self._ptr(lam, "lambda")), "hydro_adjoint_sweep")
 
@@ -441,16 +452,20 @@ def _autograd():
     import torch
 
     class HydroRollout(torch.autograd.Function):
-        """U_N = (nsteps SSP-RK3 steps)(U_0) with a discrete-adjoint backward: the forward run keeps
-        checkpoints every ``checkpoint_every`` steps and records dt and the stage alphas; backward
-        replays each segment from its checkpoint and runs the adjoint stages in reverse
-        (hydro_forward_checkpointed / hydro_adjoint_sweep). dt and the alphas are held at their
-        recorded values, so the gradient is that of the frozen map."""
+        """U_N = (nsteps SSP-RK3 steps)(U_0) with a discrete-adjoint backward: the forward run records dt
+        and the stage alphas and keeps checkpoints -- every ``checkpoint_every`` steps (uniform two-level
+        scheme, hydro_forward_checkpointed), or, with ``snapshots`` >= 0, only U_0 with a binomial
+        (revolve) reverse schedule over that many state slots (hydro_forward_revolve); backward recomputes
+        the states it needs and runs the adjoint stages in reverse (hydro_adjoint_sweep). dt and the
+        alphas are held at their recorded values, so the gradient is that of the frozen map."""
 
         @staticmethod
-        def forward(ctx, U0, solver, nsteps, checkpoint_every):
+        def forward(ctx, U0, solver, nsteps, checkpoint_every, snapshots):
             U = U0.detach().clone().contiguous()
-            solver.forward_checkpointed(U, int(nsteps), int(checkpoint_every))
+            if snapshots is not None and snapshots >= 0:
+                solver.forward_revolve(U, int(nsteps), int(snapshots))
+            else:
+                solver.forward_checkpointed(U, int(nsteps), int(checkpoint_every))
             ctx.solver = solver
             return U
 
@@ -458,7 +473,7 @@ def _autograd():
         def backward(ctx, gU):
             lam = gU.detach().to(ctx.solver.torch_dtype).clone().contiguous()
             ctx.solver.adjoint_sweep(lam)
-            return lam, None, None, None
+            return lam, None, None, None, None
 
     return HydroRollout
 
@@ -466,9 +481,10 @@ def _autograd():
 _ROLLOUT = None
 
 
-def rollout(solver: Hydro, U0, nsteps: int, checkpoint_every: int = 0):
-    """Differentiable multi-step rollout through the discrete adjoint (see HydroRollout)."""
+def rollout(solver: Hydro, U0, nsteps: int, checkpoint_every: int = 0, snapshots: int | None = None):
+    """Differentiable multi-step rollout through the discrete adjoint (see HydroRollout): uniform
+    checkpoints every ``checkpoint_every`` steps, or a binomial schedule with ``snapshots`` state slots."""
     global _ROLLOUT
     if _ROLLOUT is None:
         _ROLLOUT = _autograd()
-    return _ROLLOUT.apply(U0, solver, nsteps, checkpoint_every)
+    return _ROLLOUT.apply(U0, solver, nsteps, checkpoint_every, snapshots)

@@ -160,3 +160,56 @@ def test_gradient_matches_oracle_reduced():
     h.adjoint_sweep(L)
     assert _rel_linf(L.cpu().numpy(), ref) <= 1e-12
     h.close()
+
+
+@pytest.mark.parametrize("snapshots", [0, 1, 3, 6])
+def test_revolve_schedule_gives_the_uniform_gradient_bitwise(snapshots, record_property):
+    """Gradient configuration at 64^2, 30 steps: the binomial (revolve) schedule with a few state slots
+    recomputes other forward segments but hands the adjoint steps the same states, so dJ/dU_0 equals the
+    uniform every-10 schedule's bit for bit (FP64), and both equal the oracle's adjoint run to 1e-12."""
+    hydro = _hydro()
+    p, _ = wl.fourier_modes(64, nsteps=30)
+    h = hydro.Hydro(p, dtype="f64")
+    U = h.state(p.U0)
+    h.forward_checkpointed(U, 30, 10)
+    UN = U.clone()
+    rho, mx, my = UN[0], UN[1], UN[2]
+    lamN = UN.new_zeros(UN.shape)
+    dA = p.dx * p.dy
+    lamN[0] = -0.5 * (mx * mx + my * my) / (rho * rho) * dA
+    lamN[1] = mx / rho * dA
+    lamN[2] = my / rho * dA
+    L_uniform = lamN.clone()
+    h.adjoint_sweep(L_uniform)
+    V = h.state(p.U0)
+    nfwd = h.forward_revolve(V, 30, snapshots)
+    assert np.array_equal(V.cpu().numpy(), UN.cpu().numpy())
+    L_rev = lamN.clone()
+    h.adjoint_sweep(L_rev)
+    record_property(f"err:revolve_s{snapshots}_recomputed_steps", float(nfwd))
+    assert np.array_equal(L_rev.cpu().numpy(), L_uniform.cpu().numpy())
+    if snapshots == 3:
+        ref, _, _, _ = oracle.adjoint_run(p, p.U0, 30, lamN.cpu().numpy())
+        assert _rel_linf(L_rev.cpu().numpy(), ref) <= 1e-12
+    # the library's schedule recomputes exactly the optimal number of forward steps (the closed form that
+    # tests/test_revolve_schedule.py pins to a brute-force optimum): 435, 126, 69, 51 for 0, 1, 3, 6 slots
+    assert nfwd == {0: 435, 1: 126, 3: 69, 6: 51}[snapshots]
+    h.close()
+
+
+def test_revolve_rollout_through_autograd():
+    """torch.autograd through the binomial schedule equals the uniform schedule's gradient (FP64, bitwise)."""
+    import torch
+    hydro = _hydro()
+    p, (rho, u, v, pr) = wl.fourier_modes(48, nsteps=12)
+    grads = []
+    for kw in (dict(checkpoint_every=4), dict(snapshots=2)):
+        h = hydro.Hydro(p, dtype="f64")
+        rho_t = torch.tensor(rho, dtype=torch.float64, device="cuda", requires_grad=True)
+        ut, vt, pt = (torch.tensor(a, dtype=torch.float64, device="cuda") for a in (u, v, pr))
+        U0 = torch.stack([rho_t, rho_t * ut, rho_t * vt, pt / 0.4 + 0.5 * rho_t * (ut * ut + vt * vt)])
+        UN = hydro.rollout(h, U0, 12, **kw)
+        (0.5 * (UN[1] ** 2 + UN[2] ** 2) / UN[0]).sum().backward()
+        grads.append(rho_t.grad.cpu().numpy())
+        h.close()
+    assert np.array_equal(grads[0], grads[1])
