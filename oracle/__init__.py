@@ -41,7 +41,7 @@ class _Config(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("geometry", ctypes.c_int), ("gravity", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("nfields", ctypes.c_int),
-        ("flame_speed", ctypes.c_double), ("scheme", ctypes.c_int),
+        ("flame_speed", ctypes.c_double), ("scheme", ctypes.c_int), ("rk_stages", ctypes.c_int),
     ]
 
 
@@ -108,6 +108,7 @@ def _cfg(p) -> _Config:
         c.bc[k] = int(p.bc[k])
     c.nfields, c.flame_speed = int(p.nfields), float(p.flame_speed)
     c.scheme = int(getattr(p, "scheme", 0))
+    c.rk_stages = int(getattr(p, "rk_stages", 3))
     return c
 
 
@@ -181,18 +182,24 @@ def rhs(p, U, ax: float, ay: float) -> np.ndarray:
 
 
 def step(p, U, nsteps: int, t: float = 0.0, log: bool = False):
-    """Advance ``nsteps`` SSP-RK3 steps. Returns (U, t, dt_last) or, with ``log``, also the per-step
-    dt log and the per-stage (alpha_x, alpha_y) log of shape (nsteps, 3, 2)."""
+    """Advance ``nsteps`` steps (SSP-RK3, or the five-stage scheme for ``rk_stages`` = 5). Returns
+    (U, t, dt_last) or, with ``log``, also the per-step dt log and the per-stage (alpha_x, alpha_y) log of
+    shape (nsteps, stages, 2)."""
     U = _state(p, U).copy()
+    ns = _stages(p)
     tt, dl = ctypes.c_double(t), ctypes.c_double(0.0)
     dtl = np.zeros(max(nsteps, 1))
-    al = np.zeros(max(6 * nsteps, 1))
+    al = np.zeros(max(2 * ns * nsteps, 1))
     rc = _load().orc_step(ctypes.byref(_cfg(p)), _ptr(U), int(nsteps), ctypes.byref(tt), ctypes.byref(dl),
                           _ptr(dtl), _ptr(al))
     _check(rc, "step")
     if log:
-        return U, tt.value, dl.value, dtl[:nsteps].copy(), al[: 6 * nsteps].reshape(nsteps, 3, 2).copy()
+        return U, tt.value, dl.value, dtl[:nsteps].copy(), al[: 2 * ns * nsteps].reshape(nsteps, ns, 2).copy()
     return U, tt.value, dl.value
+
+
+def _stages(p) -> int:
+    return 5 if int(getattr(p, "rk_stages", 3)) == 5 else 3
 
 
 def step_frozen(p, U, dt_log, alpha_log) -> np.ndarray:
@@ -200,8 +207,8 @@ def step_frozen(p, U, dt_log, alpha_log) -> np.ndarray:
     U = _state(p, U).copy()
     dtl = np.ascontiguousarray(dt_log, dtype=np.float64).ravel()
     al = np.ascontiguousarray(alpha_log, dtype=np.float64).ravel()
-    if al.size != 6 * dtl.size:
-        raise OracleError("alpha log must hold 6 values per step")
+    if al.size != 2 * _stages(p) * dtl.size:
+        raise OracleError(f"alpha log must hold {2 * _stages(p)} values per step")
     _check(_load().orc_step_frozen(ctypes.byref(_cfg(p)), _ptr(U), int(dtl.size), _ptr(dtl), _ptr(al)),
            "step_frozen")
     return U

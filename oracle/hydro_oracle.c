@@ -65,6 +65,7 @@ int orc_validate(const orc_config* c) {
   if (c->bc[0] == ORC_AXIS && (c->geometry != 1 || c->x0 != 0.0)) return ORC_EINVAL;
   if (c->geometry == 1 && c->x0 < 0.0) return ORC_EINVAL;
   if (c->scheme != 0 && c->scheme != 1) return ORC_EINVAL;
+  if (c->rk_stages != 0 && c->rk_stages != 3 && c->rk_stages != 5) return ORC_EINVAL;
   return ORC_OK;
 }
 
@@ -441,6 +442,59 @@ done:
   return rc;
 }
 
+/* The paper's five-stage, third-order Runge-Kutta scheme (Sec. 2.1). Its coefficients are in a cited
+ * reference, not in the paper; the reading taken is Spiteri & Ruuth's five-stage third-order scheme SSP(5,3)
+ * (SIAM J. Numer. Anal. 40, 2002; the coefficients as tabulated by Ruuth, Math. Comp. 75, 2006), in
+ * Shu-Osher form: u(0) = U^n, u(i) = sum_{k<i} RK5_A[i-1][k] u(k) + dt sum_{k<i} RK5_B[i-1][k] L(u(k)),
+ * U^{n+1} = u(5), every L taken with the Lax-Friedrichs speeds of the state it acts on. */
+static const double RK5_A[5][5] = {
+    {1.0, 0.0, 0.0, 0.0, 0.0},
+    {0.0, 1.0, 0.0, 0.0, 0.0},
+    {0.56656131914033, 0.0, 0.43343868085967, 0.0, 0.0},
+    {0.09299483444413, 0.00002090369620, 0.0, 0.90698426185967, 0.0},
+    {0.00736132260920, 0.20127980325145, 0.00182955389682, 0.0, 0.78952932024253}};
+static const double RK5_B[5][5] = {
+    {0.37726891511710, 0.0, 0.0, 0.0, 0.0},
+    {0.0, 0.37726891511710, 0.0, 0.0, 0.0},
+    {0.0, 0.0, 0.16352294089771, 0.0, 0.0},
+    {0.00071997378654, 0.0, 0.0, 0.34217696850008, 0.0},
+    {0.00277719819460, 0.00001567934613, 0.0, 0.0, 0.29786487010104}};
+
+/* One step of the five-stage scheme with the given dt; alphas from the stage states unless frozen != NULL
+ * (frozen[2 k], frozen[2 k + 1] for L(u(k))); alpha_out (may be NULL) receives the 10 alphas used. */
+static int rk5_step(const orc_config* c, double* U, double dt, const double* frozen, double* alpha_out) {
+  const size_t total = (size_t)c->nfields * c->nx * c->ny;
+  double* u[5] = {NULL, NULL, NULL, NULL, NULL};  /* u(0) .. u(4) */
+  double* L[5] = {NULL, NULL, NULL, NULL, NULL};  /* L(u(0)) .. L(u(4)) */
+  int rc = ORC_OK;
+  for (int k = 0; k < 5; ++k) {
+    u[k] = (double*)malloc(sizeof(double) * total);
+    L[k] = (double*)malloc(sizeof(double) * total);
+    if (!u[k] || !L[k]) { rc = ORC_EINVAL; goto done; }
+  }
+  memcpy(u[0], U, sizeof(double) * total);
+  for (int i = 1; i <= 5; ++i) {
+    double ax, ay;
+    if (frozen) { ax = frozen[2 * (i - 1)]; ay = frozen[2 * (i - 1) + 1]; }
+    else if ((rc = orc_alpha(c, u[i - 1], &ax, &ay))) goto done;
+    if (alpha_out) { alpha_out[2 * (i - 1)] = ax; alpha_out[2 * (i - 1) + 1] = ay; }
+    if ((rc = orc_rhs(c, u[i - 1], ax, ay, L[i - 1]))) goto done;
+    double* out = i < 5 ? u[i] : U;
+    for (size_t q = 0; q < total; ++q) {
+      double v = 0.0, w = 0.0;
+      for (int k = 0; k < i; ++k) {
+        v += RK5_A[i - 1][k] * u[k][q];
+        w += RK5_B[i - 1][k] * L[k][q];
+      }
+      out[q] = v + dt * w;
+    }
+    if (!state_ok(c, out)) { rc = ORC_ENONPHYSICAL; goto done; }
+  }
+done:
+  for (int k = 0; k < 5; ++k) { free(u[k]); free(L[k]); }
+  return rc;
+}
+
 int orc_step(const orc_config* c, double* U, int nsteps, double* t, double* dt_last, double* dt_log,
              double* alpha_log) {
   if (orc_validate(c) || !U || nsteps < 0) return ORC_EINVAL;
@@ -448,7 +502,8 @@ int orc_step(const orc_config* c, double* U, int nsteps, double* t, double* dt_l
     double dt;
     int rc = orc_dt(c, U, &dt);
     if (rc) return rc;
-    rc = rk3_step(c, U, dt, NULL, alpha_log ? alpha_log + 6 * s : NULL);
+    rc = c->rk_stages == 5 ? rk5_step(c, U, dt, NULL, alpha_log ? alpha_log + 10 * s : NULL)
+                           : rk3_step(c, U, dt, NULL, alpha_log ? alpha_log + 6 * s : NULL);
     if (rc) return rc;
     if (dt_log) dt_log[s] = dt;
     if (t) *t += dt;
@@ -461,7 +516,8 @@ int orc_step_frozen(const orc_config* c, double* U, int nsteps, const double* dt
                     const double* alpha_log) {
   if (orc_validate(c) || !U || nsteps < 0 || !dt_log || !alpha_log) return ORC_EINVAL;
   for (int s = 0; s < nsteps; ++s) {
-    int rc = rk3_step(c, U, dt_log[s], alpha_log + 6 * s, NULL);
+    int rc = c->rk_stages == 5 ? rk5_step(c, U, dt_log[s], alpha_log + 10 * s, NULL)
+                               : rk3_step(c, U, dt_log[s], alpha_log + 6 * s, NULL);
     if (rc) return rc;
   }
   return ORC_OK;

@@ -34,6 +34,8 @@ typedef struct {
   double flame_speed;  /* burning speed s_f of the level-set front                            */
   int scheme;          /* 0 component-wise WENO5; 1 characteristic-wise with Roe-averaged       *
                         * eigenvectors (the adjoint covers scheme 0 only)                       */
+  int rk_stages;       /* 3 (or 0): three-stage SSP-RK3; 5: the five-stage third-order scheme    *
+                        * (the adjoint is of the 3-stage one)                                   */
 } orc_config;
 
 int orc_validate(const orc_config* c);
@@ -55,8 +57,9 @@ int orc_dt(const orc_config* c, const double* U, double* dt);
 /* Spatial operator L(U) (flux divergence plus sources, plus the level-set right-hand side). */
 int orc_rhs(const orc_config* c, const double* U, double ax, double ay, double* L);
 
-/* nsteps SSP-RK3 steps, in place. t accumulates dt. If dt_log / alpha_log are non-NULL they receive
- * per step dt (nsteps doubles) and per stage (alpha_x, alpha_y) (6*nsteps doubles). */
+/* nsteps steps (SSP-RK3, or the five-stage scheme with rk_stages = 5), in place. t accumulates dt. If
+ * dt_log / alpha_log are non-NULL they receive per step dt (nsteps doubles) and per stage (alpha_x,
+ * alpha_y) (2 * stages * nsteps doubles). */
 int orc_step(const orc_config* c, double* U, int nsteps, double* t, double* dt_last,
              double* dt_log, double* alpha_log);
 /* Same map with dt and the per-stage alphas frozen at the given logged values. */

@@ -41,6 +41,7 @@ class Problem:
     nfields: int = 4
     flame_speed: float = 0.0
     scheme: int = 0            # 0 component-wise WENO5, 1 characteristic-wise (Roe-averaged eigenvectors)
+    rk_stages: int = 3         # 3: SSP-RK3; 5: the five-stage third-order scheme (Spiteri & Ruuth SSP(5,3))
     nsteps: int = 0            # step count of the workload definition
     seed: int = DEFAULT_SEED
     U0: np.ndarray = field(default=None, repr=False)  # float64 [nfields, ny, nx]

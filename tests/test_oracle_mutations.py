@@ -51,6 +51,8 @@ MUTATIONS = [
      "g[0] += c->gravity * mu[3 * n + k];", "test_oracle_adjoint.py", "rhs_adjoint_dot_product"),
     ("blend_offset", "hydro_oracle_reinit.inc", "const double d0 = 3.0 * delta, w = delta / 3.0;",
      "const double d0 = 2.0 * delta, w = delta / 3.0;", "test_oracle_reinit.py", "blend_weight_properties"),
+    ("rk5_coefficient", "hydro_oracle.c", "{0.0, 0.0, 0.16352294089771, 0.0, 0.0},",
+     "{0.0, 0.0, 0.16552294089771, 0.0, 0.0},", "test_oracle_pins.py", "five_stage_scheme_third_order_in_time"),
     ("roche_sign", "hydro_oracle_poisson.inc", "{ return -grav_const * M / sqrt(r * r + z * z); }",
      "{ return grav_const * M / sqrt(r * r + z * z); }", "test_oracle_poisson.py", "uniform_sphere_potential"),
 ]

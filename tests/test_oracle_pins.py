@@ -223,6 +223,65 @@ def test_third_order_in_time():
     assert 2.8 < math.log2(r) < 3.2, r
 
 
+# The five-stage third-order scheme (the paper's choice, Sec. 2.1), read as Spiteri & Ruuth's SSP(5,3):
+# the published Shu-Osher coefficients (Ruuth 2006), u(i) = sum_k A[i][k] u(k) + dt sum_k B[i][k] L(u(k)).
+SSP53_A = [[1.0], [0.0, 1.0], [0.56656131914033, 0.0, 0.43343868085967],
+           [0.09299483444413, 0.00002090369620, 0.0, 0.90698426185967],
+           [0.00736132260920, 0.20127980325145, 0.00182955389682, 0.0, 0.78952932024253]]
+SSP53_B = [[0.37726891511710], [0.0, 0.37726891511710], [0.0, 0.0, 0.16352294089771],
+           [0.00071997378654, 0.0, 0.0, 0.34217696850008],
+           [0.00277719819460, 0.00001567934613, 0.0, 0.0, 0.29786487010104]]
+
+
+def test_five_stage_tableau_is_third_order_and_not_fourth():
+    """The Shu-Osher coefficients of the five-stage reading, turned into a Butcher tableau, satisfy the four
+    third-order conditions (to the 1e-10 to which the published optimised coefficients are given) and fail
+    the fourth-order ones by O(1e-2): a third-order method, each stage a convex combination (rows sum to 1)."""
+    a = np.zeros((6, 6))  # a[i] = Butcher row of u(i): u(i) = u0 + dt sum_j a[i][j] L(u(j))
+    for i in range(1, 6):
+        A, B = SSP53_A[i - 1], SSP53_B[i - 1]
+        assert sum(A) == pytest.approx(1.0, abs=1e-14)
+        for k in range(i):
+            a[i] += A[k] * a[k]
+            a[i, k] += B[k]
+    b, Am = a[5, :5], a[:5, :5]
+    c = Am.sum(axis=1)
+    for val, ref in ((b.sum(), 1.0), (b @ c, 0.5), (b @ c ** 2, 1 / 3), (b @ Am @ c, 1 / 6)):
+        assert abs(val - ref) < 1e-9
+    assert abs(b @ c ** 3 - 0.25) > 1e-3 and abs(b @ Am @ Am @ c - 1 / 24) > 1e-3
+
+
+def test_five_stage_scheme_third_order_in_time():
+    """The oracle's five-stage step on a fixed grid with dt and the stage alphas frozen: successive halvings
+    of dt shrink the solution change by 2^3, and its result differs from SSP-RK3's by O(dt^3)."""
+    prob = wl.advected_wave(32).with_(rk_stages=5)
+    T = 0.12
+    sols = []
+    for k in range(3):
+        m = 10 * 2 ** k
+        sols.append(oracle.step_frozen(prob, prob.U0, [T / m] * m, [[[3.0, 3.0]] * 5] * m))
+    r = np.abs(sols[0] - sols[1]).max() / np.abs(sols[1] - sols[2]).max()
+    assert 2.8 < math.log2(r) < 3.2, r
+    rk3 = [oracle.step_frozen(wl.advected_wave(32), prob.U0, [T / m] * m, [[[3.0, 3.0]] * 3] * m)
+           for m in (10, 20)]
+    d0, d1 = np.abs(sols[0] - rk3[0]).max(), np.abs(sols[1] - rk3[1]).max()
+    assert 2.5 < math.log2(d0 / d1) < 3.5, (d0, d1)
+
+
+def test_five_stage_scheme_conserves_and_advances_time():
+    """Periodic totals stay at round-off over 30 free steps of the five-stage scheme (every stage is a convex
+    combination of conservative updates), and its dt is the CFL step of the same state as SSP-RK3's."""
+    prob = wl.advected_wave(64).with_(rk_stages=5)
+    U, t, dtl, dts, al = oracle.step(prob, prob.U0, 30, log=True)
+    assert al.shape == (30, 5, 2)
+    m0, m1 = oracle.totals(prob, prob.U0), oracle.totals(prob, U)
+    for f in (0, 1, 2, 3):
+        assert abs(m1[f] - m0[f]) <= 1e-13 * abs(m0[f])
+    assert dts[0] == oracle.dt(prob, prob.U0) and t == pytest.approx(dts.sum(), rel=1e-15)
+    ax, ay = oracle.alpha(prob, prob.U0)
+    assert al[0, 0, 0] == ax and al[0, 0, 1] == ay
+
+
 def test_periodic_conservation_to_roundoff():
     prob = wl.advected_wave(64)
     U, _, _ = oracle.step(prob, prob.U0, 40)
