@@ -684,6 +684,24 @@ def run(args):
                           "dtype": dtype, "over_component": msc / (ms / args.steps)}
         hc.close()
         del Uc
+    five_stage = None
+    if args.workload == "blobs_blast_8192" and not char and not args.no_rk5:
+        # the paper's five-stage third-order scheme (five stage launches per step) on the same state
+        h5 = hydro.Hydro(prob.with_(rk_stages=5), dtype=dtype)
+        U5 = h5.state(prob.U0)
+        h5.step(U5, 1)
+        torch.cuda.synchronize()
+        k5 = max(1, args.rk5_steps)
+        q0_, q1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0_.record()
+        h5.step(U5, k5)
+        q1_.record()
+        torch.cuda.synchronize()
+        ms5 = q0_.elapsed_time(q1_) / k5
+        five_stage = {"ms_per_step": ms5, "value": cells / (ms5 * 1e-3), "unit": "cell-updates/s per 5-stage step",
+                      "steps": k5, "dtype": dtype, "stages": 5, "over_rk3_step": ms5 / (ms / args.steps)}
+        h5.close()
+        del U5
     poisson = poisson_timing(args) if args.workload == "blobs_blast_8192" and not args.no_poisson else None
     configs = config_records(args, local) if args.workload == "blobs_blast_8192" and not args.no_configs else None
     fp64 = None
@@ -717,7 +735,8 @@ def run(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
                 "adjoint": adjoint, "fp64_step": fp64, "reinit": reinit,
-                "characteristic": characteristic, "poisson": poisson, "alu_probe": alu_probe, "configs": configs}
+                "characteristic": characteristic, "five_stage": five_stage, "poisson": poisson, "alu_probe": alu_probe,
+                "configs": configs}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -864,6 +883,8 @@ def main():
     ap.add_argument("--no-char", action="store_true", help="skip the characteristic-scheme timing")
     ap.add_argument("--char-steps", type=int, default=5)
     ap.add_argument("--no-configs", action="store_true", help="skip the timed records of the other configurations")
+    ap.add_argument("--no-rk5", action="store_true", help="skip the five-stage scheme timing")
+    ap.add_argument("--rk5-steps", type=int, default=5)
     ap.add_argument("--poisson-sweeps", type=int, default=2048)
     ap.add_argument("--only-poisson", action="store_true",
                     help="time the self-gravity Poisson solve alone and print its JSON (profiling)")

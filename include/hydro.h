@@ -73,6 +73,10 @@ typedef struct {
   double flame_speed;       /* burning speed s_f of the level-set front (phi > 0 ash)             */
   int dtype;                /* hydro_dtype                                                       */
   int scheme;               /* hydro_scheme: how the hydro fluxes are reconstructed               */
+  int rk_stages;            /* time discretisation: 3 (or 0) the three-stage SSP-RK3; 5 the paper's  *
+                             * five-stage third-order scheme (Sec. 2.1), read as Spiteri & Ruuth's  *
+                             * SSP(5,3). Recording, frozen steps and the adjoint are of the 3-stage *
+                             * scheme (HYDRO_EINVAL on a 5-stage context).                          */
 } hydro_config;
 
 /* Create a context for one grid: validates cfg (HYDRO_EINVAL on a bad field, an unpaired periodic

@@ -26,7 +26,8 @@ namespace {
 
 template <typename real>
 struct Scratch {
-  real alpha[3][2];         // rotating (alpha_x, alpha_y) slots: stage k reads k, writes k+1, clears k+2
+  real alpha[5][2];         // ring of (alpha_x, alpha_y) slots, one per stage of a step: stage k reads k,
+                            // writes k+1, clears k+2 (mod the stage count)
   real smax;                // CFL signal speed of U^n
   real frozen_alpha[3][2];  // frozen runs
   real pad;
@@ -61,10 +62,12 @@ struct hydro_ctx {
   // padded layout (sized for the tallest tile variant so every variant fits)
   int pitch = 0, rows = 0, tiles_x = 0, tiles_y = 0;
   long long fstride = 0;
-  void* buf[3] = {nullptr, nullptr, nullptr};  // A = U^n / U^{n+1}, B = U^(1), C = U^(2)
-  void* tmaps = nullptr;  // device CUtensorMap[3] of A, B, C for the current tile variant's halo box
+  int ns = 3;  // stages per step: 3 (SSP-RK3) or 5 (the five-stage third-order scheme)
+  // A = U^n / U^{n+1}, B = U^(1), C = U^(2) (and D = U^(3), E = U^(4) of the five-stage scheme)
+  void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* tmaps = nullptr;  // device CUtensorMap[ns] of the working states for the current tile variant
   void* scratch = nullptr;
-  void* params = nullptr;  // device GridParams[7]: normal stages 0..2, frozen stages 3..5, rhs 6
+  void* params = nullptr;  // device GridParams[NPARAMS]: stages 0..ns-1, frozen stages P_FROZEN.., rhs P_RHS
   void* host_scratch = nullptr;  // pinned copy of Scratch
   double* partials = nullptr;
   int partial_blocks = 0;
@@ -182,6 +185,10 @@ static int validate_config(const hydro_config* g, std::string* why) {
     *why = "scheme must be HYDRO_SCHEME_COMPONENT or HYDRO_SCHEME_CHARACTERISTIC";
     return HYDRO_EINVAL;
   }
+  if (g->rk_stages != 0 && g->rk_stages != 3 && g->rk_stages != 5) {
+    *why = "rk_stages must be 3 (or 0) or 5";
+    return HYDRO_EINVAL;
+  }
   if (!std::isfinite(g->gravity_y) || !std::isfinite(g->flame_speed) || g->flame_speed < 0.0) {
     *why = "gravity and flame speed must be finite, flame speed >= 0";
     return HYDRO_EINVAL;
@@ -200,6 +207,71 @@ static real* bufp(hydro_ctx* c, int k) {
 }
 
 static int tile_ty(int variant) { return VARIANTS[variant].ty; }
+
+// Device parameter table of a context: the step's stages (up to 5), the three frozen SSP-RK3 stages
+// (recorded replays and the adjoint), the spatial operator.
+constexpr int P_FROZEN = 5, P_RHS = 8, NPARAMS = 9;
+
+// One stage of a step: W = buffer win, output buffer out, and out = a U^n + rx0 B[x0] + rx1 B[x1]
+// + b (W + c dt L(W)) (x0, x1 = -1: no such term).
+struct RkStage {
+  int win, out, x0, x1;
+  double a, b, c, rx0, rx1;
+};
+
+// SSP-RK3 (Sec. 2.1, the original prescription): U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
+// U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2)).
+static const RkStage RK3_STAGES[3] = {{0, 1, -1, -1, 0.0, 1.0, 1.0, 0.0, 0.0},
+                                      {1, 2, -1, -1, 0.75, 0.25, 1.0, 0.0, 0.0},
+                                      {2, 0, -1, -1, 1.0 / 3.0, 2.0 / 3.0, 1.0, 0.0, 0.0}};
+static const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+static const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+// The five-stage third-order scheme (Sec. 2.1), read as Spiteri & Ruuth's SSP(5,3): Shu-Osher form
+// u(i) = sum_k SO_A[i-1][k] u(k) + dt sum_k SO_B[i-1][k] L(u(k)), u(0) = U^n, U^{n+1} = u(5), with the
+// published coefficients. Each stage here applies L to its newest input only: the terms dt L(u0) and
+// dt L(u1) of the later stages are (u1 - u0) / b10 and (u2 - u1) / b21 exactly (stages 1 and 2), so
+// their weights move onto u0, u1, u2 (the moved weights are below 0.01, so the rounding this adds is
+// negligible).
+static const double SO_A[5][5] = {{1.0, 0.0, 0.0, 0.0, 0.0},
+                                  {0.0, 1.0, 0.0, 0.0, 0.0},
+                                  {0.56656131914033, 0.0, 0.43343868085967, 0.0, 0.0},
+                                  {0.09299483444413, 0.00002090369620, 0.0, 0.90698426185967, 0.0},
+                                  {0.00736132260920, 0.20127980325145, 0.00182955389682, 0.0, 0.78952932024253}};
+static const double SO_B[5][5] = {{0.37726891511710, 0.0, 0.0, 0.0, 0.0},
+                                  {0.0, 0.37726891511710, 0.0, 0.0, 0.0},
+                                  {0.0, 0.0, 0.16352294089771, 0.0, 0.0},
+                                  {0.00071997378654, 0.0, 0.0, 0.34217696850008, 0.0},
+                                  {0.00277719819460, 0.00001567934613, 0.0, 0.0, 0.29786487010104}};
+static RkStage rk5_stage(int k) {
+  const double b10 = SO_B[0][0], b21 = SO_B[1][1];
+  switch (k) {
+    case 0: return {0, 1, -1, -1, 0.0, SO_A[0][0], b10, 0.0, 0.0};
+    case 1: return {1, 2, -1, -1, 0.0, SO_A[1][1], b21, 0.0, 0.0};
+    case 2: return {2, 3, -1, -1, SO_A[2][0], SO_A[2][2], SO_B[2][2] / SO_A[2][2], 0.0, 0.0};
+    case 3:
+      return {3, 4, 1, -1, SO_A[3][0] - SO_B[3][0] / b10, SO_A[3][3], SO_B[3][3] / SO_A[3][3],
+              SO_A[3][1] + SO_B[3][0] / b10, 0.0};
+    default:
+      return {4, 0, 1, 2, SO_A[4][0] - SO_B[4][0] / b10, SO_A[4][4], SO_B[4][4] / SO_A[4][4],
+              SO_A[4][1] + SO_B[4][0] / b10 - SO_B[4][1] / b21, SO_A[4][2] + SO_B[4][1] / b21};
+  }
+}
+
+static RkStage rk_stage(const hydro_ctx* c, int k, bool frozen) {
+  return (c->ns == 5 && !frozen) ? rk5_stage(k) : RK3_STAGES[k];
+}
+
+// Launch control of stage k of a step (frozen: of the SSP-RK3 replay).
+static StageCtl stage_ctl(const hydro_ctx* c, int k, bool frozen) {
+  const RkStage r = rk_stage(c, k, frozen);
+  StageCtl ctl{k, 0, r.a, r.b};
+  ctl.rk_c = r.c;
+  ctl.rk_x0 = r.rx0;
+  ctl.rk_x1 = r.rx1;
+  ctl.last = k == (frozen ? 3 : c->ns) - 1;
+  return ctl;
+}
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link against libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -235,7 +307,7 @@ static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorM
 
 // Stage parameters of this context for the current variant.
 template <typename real>
-static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
+static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
   const hydro_config& g = c->cfg;
   Scratch<real>* s = scr<real>(c);
   GridParams<real> base{};
@@ -266,37 +338,39 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   base.ext_div = static_cast<const real*>(c->char_div ? c->char_div : c->split_div);
   real* A = bufp<real>(c, 0);
   real* B = bufp<real>(c, 1);
-  real* C = bufp<real>(c, 2);
-  const real* win[3] = {A, B, C};
-  real* outp[3] = {B, C, A};
   const CUtensorMap* maps = static_cast<const CUtensorMap*>(c->tmaps);
-  for (int k = 0; k < 3; ++k) {
+  auto stage_params = [&](const RkStage& r, int k, int ns) {
     GridParams<real> p = base;
-    p.win = win[k];
-    p.tmap_win = maps + k;
+    p.win = bufp<real>(c, r.win);
+    p.tmap_win = maps + r.win;
     p.tmap_un = maps;
     p.un = A;
-    p.out = outp[k];
+    p.out = bufp<real>(c, r.out);
+    p.ux0 = r.x0 >= 0 ? bufp<real>(c, r.x0) : nullptr;
+    p.ux1 = r.x1 >= 0 ? bufp<real>(c, r.x1) : nullptr;
     p.alpha_in = s->alpha[k];
-    p.alpha_out = s->alpha[(k + 1) % 3];
-    p.alpha_zero = s->alpha[(k + 2) % 3];
+    p.alpha_out = s->alpha[(k + 1) % ns];
+    p.alpha_zero = s->alpha[(k + 2) % ns];
+    if (k == ns - 1 && c->track_totals) p.totals = s->totals;
+    if (k == 1 && c->track_totals) p.totals_reset = s->totals;
+    return p;
+  };
+  for (int k = 0; k < c->ns; ++k) {
+    GridParams<real> p = stage_params(rk_stage(c, k, false), k, c->ns);
     if (c->log_cap > 0) {
       p.dt_log = c->dt_log;
       p.alpha_log = c->alpha_log;
       p.log_count = &s->log_count;
       p.log_cap = c->log_cap;
     }
-    if (k == 2 && c->track_totals) p.totals = s->totals;
-    if (k == 1 && c->track_totals) p.totals_reset = s->totals;
     out[k] = p;
-    GridParams<real> f = p;  // frozen: alphas and dt from the frozen slots
+  }
+  for (int k = c->ns; k < P_FROZEN; ++k) out[k] = out[0];  // unused slots
+  for (int k = 0; k < 3; ++k) {  // frozen SSP-RK3: alphas and dt from the frozen slots
+    GridParams<real> f = stage_params(RK3_STAGES[k], k, 3);
     f.alpha_in = s->frozen_alpha[k];
     f.dt_src = (k == 0) ? &s->frozen_dt : nullptr;
-    f.dt_log = nullptr;
-    f.alpha_log = nullptr;
-    f.log_count = nullptr;
-    f.log_cap = 0;
-    out[3 + k] = f;
+    out[P_FROZEN + k] = f;
   }
   GridParams<real> r = base;  // L(W) of buffer A into buffer B
   r.win = A;
@@ -306,20 +380,20 @@ static void build_params(hydro_ctx* c, GridParams<real> out[7]) {
   r.out = B;
   r.alpha_in = s->frozen_alpha[0];
   r.dt_src = &s->frozen_dt;
-  out[6] = r;
+  out[P_RHS] = r;
 }
 
 template <typename real>
 static int upload_params(hydro_ctx* c) {
-  GridParams<real> p[7];
+  GridParams<real> p[NPARAMS];
   build_params<real>(c, p);
-  alignas(64) CUtensorMap maps[3];
-  for (int k = 0; k < 3; ++k) {
+  alignas(64) CUtensorMap maps[5];
+  for (int k = 0; k < c->ns; ++k) {
     const int rc = encode_state_map<real>(c, c->buf[k], tile_ty(c->variant) + 2 * GY, &maps[k]);
     if (rc) return fail(c, rc, "cuTensorMapEncodeTiled failed for the working states");
   }
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->tmaps, maps, sizeof(CUtensorMap) * c->ns, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
   ++c->params_gen;
   if (c->step_graph) {
@@ -356,8 +430,8 @@ static int wait_stream(hydro_ctx* c) {
 }
 
 template <typename real>
-static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double b, cudaStream_t s) {
-  StageCtl ctl{stage, mode, a, b};
+static int launch_ctl(hydro_ctx* c, int k, const StageCtl& ctl, cudaStream_t s) {
+  const int stage = ctl.stage;
   const int nwork = c->tiles_x * ((c->cfg.ny + tile_ty(c->variant) - 1) / tile_ty(c->variant));
   const GridParams<real>* p = static_cast<const GridParams<real>*>(c->params) + k;
   const bool prof = c->profiling && s == c->stream;
@@ -373,10 +447,12 @@ static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double
     CK(launch_char_div<real>(p, c->cfg.nx, c->cfg.ny, s));
     c->launches++;
   } else if (c->split_div) {  // field split: one CTA per (tile, hydro field) writes the divergence first
-    const StageCtl split{stage, 2, a, b};
+    StageCtl split = ctl;
+    split.mode = 2;
     CK(launch_stage<real>(c->variant, c->nf, p, nullptr, 4 * nwork, split, grid_for(c, 4 * nwork), s));
     c->launches++;
   }
+  (void)stage;
   CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), s));
   if (prof) {
     CK(cudaEventRecord(c->ev[c->ev_used + 1], s));
@@ -386,13 +462,11 @@ static int launch_one(hydro_ctx* c, int k, int stage, int mode, double a, double
   return HYDRO_OK;
 }
 
-static const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
-static const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
-
 template <typename real>
 static int launch_step(hydro_ctx* c, bool frozen, cudaStream_t s) {
-  for (int k = 0; k < 3; ++k) {
-    int rc = launch_one<real>(c, frozen ? 3 + k : k, k, 0, RK_A[k], RK_B[k], s);
+  const int ns = frozen ? 3 : c->ns;
+  for (int k = 0; k < ns; ++k) {
+    int rc = launch_ctl<real>(c, frozen ? P_FROZEN + k : k, stage_ctl(c, k, frozen), s);
     if (rc) return rc;
   }
   return HYDRO_OK;
@@ -425,7 +499,7 @@ static int pack_state(hydro_ctx* c, const real* U, double t0) {
   CK(cudaMemsetAsync(s, 0, c->defer_status ? offsetof(Scratch<real>, err) : offsetof(Scratch<real>, log_count),
                      c->stream));
   GridParams<real> g{};
-  GridParams<real> all[7];
+  GridParams<real> all[NPARAMS];
   build_params<real>(c, all);
   g = all[0];
   g.out = bufp<real>(c, 0);
@@ -471,7 +545,9 @@ static int last_stage_to_host(hydro_ctx* c, real* host_out) {
   const int TY = tile_ty(c->variant);
   const int trows = (g.ny + TY - 1) / TY;
   const int nb = std::min(hydro_ctx::NBANDS, trows);
-  const GridParams<real>* p = static_cast<const GridParams<real>*>(c->params) + 2;
+  const int last = c->ns - 1;
+  const GridParams<real>* p = static_cast<const GridParams<real>*>(c->params) + last;
+  const StageCtl last_ctl = stage_ctl(c, last, false);
   const real* A = bufp<real>(c, 0);
   const size_t es = sizeof(real);
   // an externally formed divergence (characteristic scheme, FP64 field split) first, for the whole grid
@@ -480,13 +556,14 @@ static int last_stage_to_host(hydro_ctx* c, real* host_out) {
     c->launches++;
   } else if (c->split_div) {
     const int nall = c->tiles_x * trows;
-    const StageCtl split{2, 2, RK_A[2], RK_B[2]};
+    StageCtl split = last_ctl;
+    split.mode = 2;
     CK(launch_stage<real>(c->variant, c->nf, p, nullptr, 4 * nall, split, grid_for(c, 4 * nall), c->stream));
     c->launches++;
   }
   for (int b = 0; b < nb; ++b) {
     const int r0 = b * trows / nb, r1 = (b + 1) * trows / nb;
-    StageCtl ctl{2, 0, RK_A[2], RK_B[2]};
+    StageCtl ctl = last_ctl;
     ctl.w0 = r0 * c->tiles_x;
     const int nwork = (r1 - r0) * c->tiles_x;
     CK(launch_stage<real>(c->variant, c->nf, p, nullptr, nwork, ctl, grid_for(c, nwork), c->stream));
@@ -536,8 +613,7 @@ static int step_impl(hydro_ctx* c, real* U, int nsteps, double* t_inout, double*
     if (rc) return rc;
   }
   if (direct) {
-    rc = launch_one<real>(c, 0, 0, 0, RK_A[0], RK_B[0], c->stream);
-    if (!rc) rc = launch_one<real>(c, 1, 1, 0, RK_A[1], RK_B[1], c->stream);
+    for (int k = 0; k + 1 < c->ns && !rc; ++k) rc = launch_ctl<real>(c, k, stage_ctl(c, k, false), c->stream);
     if (!rc) rc = last_stage_to_host<real>(c, host_out);
     if (rc) return rc;
   } else {
@@ -591,7 +667,8 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   c->rows = ((cfg->ny + MAX_TY - 1) / MAX_TY) * MAX_TY + 2 * GY;
   c->fstride = (long long)c->pitch * c->rows;
   const size_t bytes = (size_t)c->nf * c->fstride * c->esize;
-  for (int k = 0; k < 3; ++k) {
+  c->ns = cfg->rk_stages == 5 ? 5 : 3;
+  for (int k = 0; k < c->ns; ++k) {
     if (cudaMalloc(&c->buf[k], bytes) != cudaSuccess) return bail(HYDRO_ECUDA);
     if (cudaMemsetAsync(c->buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   }
@@ -610,9 +687,9 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMemsetAsync(c->scratch, 0, sb, c->stream) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
-  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * 7 : sizeof(GridParams<float>) * 7;
+  const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * NPARAMS : sizeof(GridParams<float>) * NPARAMS;
   if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
-  if (cudaMalloc(&c->tmaps, 3 * sizeof(CUtensorMap)) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMalloc(&c->tmaps, 5 * sizeof(CUtensorMap)) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->partial_blocks = 4 * c->num_sms;
   if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMalloc(&c->d_totals, sizeof(double) * 5) != cudaSuccess) return bail(HYDRO_ECUDA);
@@ -639,7 +716,7 @@ void hydro_destroy(hydro_ctx* c) {
     if (e) cudaEventDestroy(e);
   cudaFree(c->pois);
   if (c->pois_host) cudaFreeHost(c->pois_host);
-  for (int k = 0; k < 3; ++k) cudaFree(c->buf[k]);
+  for (int k = 0; k < 5; ++k) cudaFree(c->buf[k]);
   cudaFree(c->scratch);
   cudaFree(c->params);
   cudaFree(c->tmaps);
@@ -730,9 +807,16 @@ int hydro_step_host(hydro_ctx* c, void* U_host, int nsteps, double* t_inout, dou
   return rc ? rc : rc2;
 }
 
+// Recording, frozen replays and the adjoint are of the three-stage scheme.
+static int require_rk3(hydro_ctx* c) {
+  return c->ns == 3 ? HYDRO_OK
+                    : fail(c, HYDRO_EINVAL, "recording, frozen steps and the adjoint are of the 3-stage scheme");
+}
+
 int hydro_step_frozen(hydro_ctx* c, void* U, int nsteps, const double* dtl, const double* al) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if ((rc = require_rk3(c))) return rc;
   if (!U || nsteps < 0 || (nsteps > 0 && (!dtl || !al))) return fail(c, HYDRO_EINVAL, "bad frozen-step arguments");
   if (c->cfg.dtype == HYDRO_F64) return step_impl<double>(c, (double*)U, nsteps, nullptr, nullptr, dtl, al);
   return step_impl<float>(c, (float*)U, nsteps, nullptr, nullptr, dtl, al);
@@ -746,7 +830,8 @@ static int rhs_impl(hydro_ctx* c, const real* U, double ax, double ay, real* L) 
   const double a6[6] = {ax, ay, ax, ay, ax, ay};
   CK(launch_set_frozen<real>(&s->frozen_dt, 0.0, &s->frozen_alpha[0][0], a6, c->stream));
   c->launches++;
-  rc = launch_one<real>(c, 6, 0, 1, 0.0, 1.0, c->stream);
+  StageCtl rhs_ctl{0, 1, 0.0, 1.0};
+  rc = launch_ctl<real>(c, P_RHS, rhs_ctl, c->stream);
   if (rc) return rc;
   return unpack_state<real>(c, L, 1);
 }
@@ -796,6 +881,7 @@ int hydro_last_totals(hydro_ctx* c, double out[5]) {
 int hydro_record(hydro_ctx* c, int max_steps) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if (max_steps > 0 && (rc = require_rk3(c))) return rc;
   if (max_steps < 0) return fail(c, HYDRO_EINVAL, "negative capacity");
   CK(cudaStreamSynchronize(c->stream));
   cudaFree(c->dt_log);
@@ -977,12 +1063,12 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     c->plan_members.clear();  // no plan until the new one is complete (an error below leaves none)
     c->plan_gens.clear();
     c->plan_nwork = 0;
-    std::vector<GridParams<real>> P(3 * (size_t)n);
+    std::vector<GridParams<real>> P(c->ns * (size_t)n);
     std::vector<WorkItem> W;
     for (int k = 0; k < n; ++k) {
-      GridParams<real> p[7];
+      GridParams<real> p[NPARAMS];
       build_params<real>(m[k], p);
-      for (int s = 0; s < 3; ++s) {
+      for (int s = 0; s < c->ns; ++s) {
         P[(size_t)s * n + k] = p[s];
         P[(size_t)s * n + k].ext_div = nullptr;  // the batched launch computes every field itself
       }
@@ -1030,7 +1116,7 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     hydro_ctx* mk = m[k];
     Scratch<real>* s = scr<real>(mk);
     CK(cudaMemsetAsync(s, 0, offsetof(Scratch<real>, log_count), c->stream));
-    GridParams<real> p[7];
+    GridParams<real> p[NPARAMS];
     build_params<real>(mk, p);
     p[0].out = bufp<real>(mk, 0);
     CK(launch_pack<real>(static_cast<const real*>(U[k]), p[0], mk->nf, s->alpha[0], &s->smax, &s->t_acc,
@@ -1041,8 +1127,8 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
   const GridParams<real>* P = static_cast<const GridParams<real>*>(c->plan_params);
   const WorkItem* W = static_cast<const WorkItem*>(c->plan_work);
   auto launch3 = [&](cudaStream_t s) -> int {
-    for (int k = 0; k < 3; ++k) {
-      StageCtl ctl{k, 0, RK_A[k], RK_B[k]};
+    for (int k = 0; k < c->ns; ++k) {
+      const StageCtl ctl = stage_ctl(c, k, false);
       CK(launch_stage<real>(c->variant, c->nf, P + (size_t)k * n, W, c->plan_nwork, ctl, grid, s));
     }
     return HYDRO_OK;
@@ -1066,7 +1152,7 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
   }
   for (int s = 0; s < nsteps; ++s) {
     CK(cudaGraphLaunch(c->plan_graph, c->stream));
-    c->launches += 3;
+    c->launches += c->ns;
   }
   if (ms_graph) CK(cudaEventRecord(g1, c->stream));
   int worst = HYDRO_OK;
@@ -1106,8 +1192,9 @@ static int batch_check(hydro_ctx* const* members, void* const* U, int n) {
   hydro_ctx* c = members[0];
   for (int k = 0; k < n; ++k) {
     if (!members[k] || !U[k]) return fail(c, HYDRO_EINVAL, "null member or state");
-    if (members[k]->cfg.dtype != c->cfg.dtype || members[k]->nf != c->nf || members[k]->device != c->device)
-      return fail(c, HYDRO_EINVAL, "members must share dtype, nfields and device");
+    if (members[k]->cfg.dtype != c->cfg.dtype || members[k]->nf != c->nf || members[k]->device != c->device ||
+        members[k]->ns != c->ns)
+      return fail(c, HYDRO_EINVAL, "members must share dtype, nfields, time scheme and device");
     if (members[k]->cfg.scheme != HYDRO_SCHEME_COMPONENT)
       return fail(c, HYDRO_EINVAL, "batched steps take component-wise contexts (step characteristic ones one by one)");
   }
@@ -1231,8 +1318,8 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
   Scratch<real>* s = scr<real>(c);
   CK(launch_set_frozen<real>(&s->frozen_dt, dt, &s->frozen_alpha[0][0], alpha, c->stream));
   c->launches++;
-  rc = launch_one<real>(c, 3, 0, 0, RK_A[0], RK_B[0], c->stream);
-  if (!rc) rc = launch_one<real>(c, 4, 1, 0, RK_A[1], RK_B[1], c->stream);
+  rc = launch_ctl<real>(c, P_FROZEN + 0, stage_ctl(c, 0, true), c->stream);
+  if (!rc) rc = launch_ctl<real>(c, P_FROZEN + 1, stage_ctl(c, 1, true), c->stream);
   if (rc) return rc;
   real* nu[2] = {static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1])};
   rc = copy_in<real>(c, nu[0], lam);
@@ -1287,6 +1374,7 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
 int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, const double alpha[6]) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if ((rc = require_rk3(c))) return rc;
   if (!U_n || !lambda || !alpha || !(dt >= 0.0)) return fail(c, HYDRO_EINVAL, "bad adjoint arguments");
   if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
     return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");
@@ -1300,6 +1388,7 @@ int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, c
 int hydro_forward_checkpointed(hydro_ctx* c, void* U, int nsteps, int every) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if ((rc = require_rk3(c))) return rc;
   if (!U || nsteps < 1) return fail(c, HYDRO_EINVAL, "bad arguments");
   if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
     return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");
@@ -1410,6 +1499,7 @@ static int rv_reverse(hydro_ctx* c, real* lam, real* slots, int nslots, real* tm
 int hydro_forward_revolve(hydro_ctx* c, void* U, int nsteps, int snapshots, long long* sweep_forward_steps) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if ((rc = require_rk3(c))) return rc;
   if (!U || nsteps < 1 || snapshots < 0 || snapshots > 4096) return fail(c, HYDRO_EINVAL, "bad arguments");
   if (c->cfg.scheme != HYDRO_SCHEME_COMPONENT)
     return fail(c, HYDRO_EINVAL, "the discrete adjoint is of the component-wise scheme");

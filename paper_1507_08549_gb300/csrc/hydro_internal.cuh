@@ -43,6 +43,8 @@ struct GridParams {
   const void* tmap_win;  // device CUtensorMap of win: (x, y, field) with one tile's halo box as its box
   const real* un;    // U^n (padded), read when rk_a != 0
   const void* tmap_un;   // device CUtensorMap of un (the same box), for L2 prefetches
+  const real* ux0;   // further stage states the blend adds (five-stage scheme), else null
+  const real* ux1;
   real* out;         // stage output (padded) or L (mode RHS)
   long long fstride; // elements between field planes
   int nx, ny, pitch;
@@ -74,12 +76,16 @@ struct GridParams {
 
 // Launch-wide stage control.
 struct StageCtl {
-  int stage;      // 0, 1, 2
+  int stage;      // 0 .. stages-1
   int mode;       // 0 RK stage, 1 write L (no blending, no reductions), 2 field split: work item w computes
                   // dF/dx + dG/dy of hydro field w & 3 on tile w >> 2 into ext_div (FP64 grids with few tiles)
-  double rk_a;    // out = a U^n + b (W + dt L)
+  double rk_a;    // out = a U^n + x0 ux0 + x1 ux1 + b (W + c dt L)
   double rk_b;
   int w0 = 0;     // first tile of the launch (row bands of one stage); work items w -> tile w0 + w
+  double rk_c = 1.0;
+  double rk_x0 = 0.0;
+  double rk_x1 = 0.0;
+  int last = 0;   // the step's last stage (writes the next step's CFL speed and the totals)
 };
 
 // Batched launch: a table of (member, tile) work items over an array of member parameters.

@@ -276,6 +276,8 @@ struct Ar<float> {
     const float inner = rb * T::fma_(dt, L, w);
     return use_un ? T::fma_(ra, un, inner) : inner;
   }
+  // a further stage state's term of the five-stage scheme's blend
+  static __device__ __forceinline__ float add_term(float out, float r, float x) { return T::fma_(r, x, out); }
   // cell-centre radius r_i = x0 + (i + 1/2) dx, in FP32
   template <typename G>
   static __device__ __forceinline__ float radius(const G& g, int i) {
@@ -341,6 +343,7 @@ struct Ar<double> {
     const double inner = ml(rb, ad(w, ml(dt, L)));
     return use_un ? ad(ml(ra, un), inner) : inner;
   }
+  static __device__ __forceinline__ double add_term(double out, double r, double x) { return ad(out, ml(r, x)); }
   // cell-centre radius r_i = x0 + (i + 1/2) dx, each operation rounded once
   template <typename G>
   static __device__ __forceinline__ double radius(const G& g, int i) {
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   // stage scalars, formed once per CTA and member (dt needs an FP64 division at stage 0; the FP64 pipe
   // is 1/64 of the FP32 rate, so no per-thread FP64 work stays in the tile loop of the FP32 kernel)
   __shared__ double s_dtd;
-  __shared__ real s_dt, s_ra, s_rb, s_ax, s_ay;
+  __shared__ real s_dt, s_ra, s_rb, s_ax, s_ay, s_rx0, s_rx1;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       T::atomic_max(&g.alpha_out[0], r[0]);
       T::atomic_max(&g.alpha_out[1], r[1]);
     }
-    if (ctl.stage == 2) T::atomic_max(g.smax, r[2]);
+    if (ctl.last) T::atomic_max(g.smax, r[2]);
     if (g.totals) {
       if constexpr (sizeof(real) == 4) {  // the cell volume, applied once
         const double vol = g.geometry == 1 ? 6.283185307179586 * g.dx * g.dy : g.dx * g.dy;
@@ -774,9 +777,11 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         const double d = ctl.stage == 0 ? (g.dt_src ? *g.dt_src : g.cfl_delta / static_cast<double>(*g.smax))
                                         : *g.dt_cur;
         s_dtd = d;
-        s_dt = static_cast<real>(d);
+        s_dt = static_cast<real>(d * ctl.rk_c);  // the stage's multiple of dt (1 in SSP-RK3)
         s_ra = static_cast<real>(ctl.rk_a);
         s_rb = static_cast<real>(ctl.rk_b);
+        s_rx0 = static_cast<real>(ctl.rk_x0);
+        s_rx1 = static_cast<real>(ctl.rk_x1);
         s_ax = g.alpha_in[0];  // the Lax-Friedrichs speeds, written by the previous launch
         s_ay = g.alpha_in[1];
       }
@@ -821,7 +826,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           g.alpha_log[6 * idx + 2 * ctl.stage + 0] = static_cast<double>(ax);
           g.alpha_log[6 * idx + 2 * ctl.stage + 1] = static_cast<double>(ay);
         }
-        if (ctl.stage == 2) *g.log_count = idx + 1;
+        if (ctl.last) *g.log_count = idx + 1;
       }
     }
 
@@ -948,6 +953,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const real dt = s_dt;
       const real ra = s_ra, rb = s_rb;
       const bool use_un = ra != real(0) && ctl.mode == 0;
+      const real rx0 = s_rx0, rx1 = s_rx1;
+      const bool use_x0 = g.ux0 != nullptr && ctl.mode == 0, use_x1 = g.ux1 != nullptr && ctl.mode == 0;
       constexpr int NG = TX / EG;
       for (int it2 = tid; it2 < TY * NG; it2 += NT) {
         const int row = it2 / NG, g4 = it2 - row * NG;
@@ -987,6 +994,20 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
               for (int e = 0; e < EG; ++e) unv[f][e] = real(0);
           }
+          // the five-stage scheme's further stage states (the cell's own values, like U^n)
+          real x0v[NF][EG], x1v[NF][EG];
+          if (use_x0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int e = 0; e < EG; ++e) x0v[f][e] = (e < nvalid) ? g.ux0[f * fs + gbase + e] : real(0);
+          }
+          if (use_x1) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int e = 0; e < EG; ++e) x1v[f][e] = (e < nvalid) ? g.ux1[f * fs + gbase + e] : real(0);
+          }
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             real Uv[EG], Dv[EG];
@@ -1017,6 +1038,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               }
               const real L = (f < 4) ? Ar<real>::lval(Dv[e], S) : -Dv[e];
               o[f][e] = (ctl.mode == 1) ? L : Ar<real>::blend(use_un, ra, rb, un[e], Uv[e], dt, L);
+              if (use_x0) o[f][e] = Ar<real>::add_term(o[f][e], rx0, x0v[f][e]);
+              if (use_x1) o[f][e] = Ar<real>::add_term(o[f][e], rx1, x1v[f][e]);
             }
           }
         }

@@ -38,6 +38,7 @@ class hydro_config(ctypes.Structure):
         ("geometry", ctypes.c_int), ("gravity_y", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("nfields", ctypes.c_int),
         ("flame_speed", ctypes.c_double), ("dtype", ctypes.c_int), ("scheme", ctypes.c_int),
+        ("rk_stages", ctypes.c_int),
     ]
 
 
@@ -137,6 +138,7 @@ def make_config(p, dtype: int) -> hydro_config:
         c.bc[k] = int(p.bc[k])
     c.nfields, c.flame_speed, c.dtype = int(p.nfields), float(p.flame_speed), int(dtype)
     c.scheme = int(getattr(p, "scheme", 0))
+    c.rk_stages = int(getattr(p, "rk_stages", 3))
     return c
 
 

@@ -1,0 +1,116 @@
+"""The five-stage third-order time discretisation (the paper's choice, Sec. 2.1; read as Spiteri & Ruuth's
+SSP(5,3)) on the GPU against the FP64 oracle. The kernels apply L only to each stage's newest input (the
+earlier stages' L terms are rewritten exactly through the stage differences), so FP64 agrees with the
+oracle's literal Shu-Osher evaluation to rounding, held at the 1e-12 relative L-inf bar, not bit for bit;
+FP32 at the relative L1 bars (1e-5 smooth, 1e-4 with shocks or the level set)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_08549_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _hydro():
+    from paper_1507_08549_gb300 import hydro
+    return hydro
+
+
+def rel_linf(a, b):
+    return max(np.abs(a[f] - b[f]).max() / max(np.abs(b[f]).max(), 1e-300) for f in range(b.shape[0]))
+
+
+def rel_l1(a, b):
+    return max(np.abs(a[f] - b[f]).sum() / max(np.abs(b[f]).sum(), 1e-300) for f in range(b.shape[0]))
+
+
+def _run(prob, nsteps, dtype):
+    h = _hydro().Hydro(prob, dtype=dtype)
+    U = h.state(prob.U0)
+    t, dtl = h.step(U, nsteps)
+    out = U.double().cpu().numpy()
+    h.close()
+    return out, t
+
+
+def test_five_stage_advected_wave_matches_oracle(record_property):
+    """128^2 advected wave, 100 steps: FP64 to 1e-12 relative L-inf (and time), FP32 within 1e-5 L1."""
+    prob = wl.advected_wave(128).with_(rk_stages=5)
+    ref, t_ref, _ = oracle.step(prob, prob.U0, 100)
+    got, t = _run(prob, 100, "f64")
+    record_property("err:rk5_f64_rel_linf", rel_linf(got, ref))
+    assert rel_linf(got, ref) <= 1e-12
+    assert abs(t - t_ref) <= 1e-13 * t_ref
+    got32, _ = _run(prob, 100, "f32")
+    record_property("err:rk5_fp32_rel_l1", rel_l1(got32, ref))
+    assert rel_l1(got32, ref) <= 1e-5
+    # a different scheme from SSP-RK3: the two differ by far more than rounding
+    ref3, _, _ = oracle.step(prob.with_(rk_stages=3), prob.U0, 100)
+    assert rel_linf(ref, ref3) > 1e-8
+
+
+def test_five_stage_rz_gravity_level_set_matches_oracle(record_property):
+    """(r,z) Rayleigh-Taylor with gravity and the level set, 128 x 256, 30 steps."""
+    prob = wl.rayleigh_taylor(128, 256, nsteps=30).with_(rk_stages=5)
+    ref, _, _ = oracle.step(prob, prob.U0, 30)
+    got, _ = _run(prob, 30, "f64")
+    assert rel_linf(got, ref) <= 1e-12
+    got32, _ = _run(prob, 30, "f32")
+    record_property("err:rk5_fp32_rel_l1_rt", rel_l1(got32, ref))
+    assert rel_l1(got32, ref) <= 1e-4
+
+
+def test_five_stage_shock_tube_and_host_entry():
+    """Toro test 1 (a shock, a contact and a rarefaction), 60 steps, FP64 against the oracle; the pinned
+    host-buffer entry (last stage in row bands, copied back by the copy engine) gives the device entry's
+    bits and time."""
+    import torch
+    hydro = _hydro()
+    prob = wl.shock_tube(1, nx=400, ny=3).with_(rk_stages=5)
+    ref, _, _ = oracle.step(prob, prob.U0, 60)
+    got, _ = _run(prob, 60, "f64")
+    assert rel_linf(got, ref) <= 1e-12
+    kh = wl.kelvin_helmholtz(64).with_(rk_stages=5)
+    h = hydro.Hydro(kh, dtype="f32")
+    U = h.state(kh.U0)
+    t, _ = h.step(U, 4)
+    pinned = torch.from_numpy(np.ascontiguousarray(kh.U0.astype(np.float32))).pin_memory()
+    th, _ = h.step_host(pinned.numpy(), 4)
+    assert np.array_equal(pinned.numpy(), U.cpu().numpy()) and th == t
+    h.close()
+
+
+def test_five_stage_batched_members_match_oracle():
+    """A batched five-stage ensemble: each member within the FP64 bar of its own oracle run."""
+    hydro = _hydro()
+    members = [p.with_(rk_stages=5) for p in wl.quadrant_ensemble(5, seed=11, sizes=(64, 96), nsteps=8)]
+    hs = [hydro.Hydro(p, dtype="f64") for p in members]
+    Us = [h.state(p.U0) for h, p in zip(hs, members)]
+    t = hydro.hydro_batch_step(hs, Us, 8)
+    for p, U, tm in zip(members, Us, t):
+        ref, t_ref, _ = oracle.step(p, p.U0, 8)
+        assert rel_linf(U.cpu().numpy(), ref) <= 1e-12, p.name
+        assert abs(tm - t_ref) <= 1e-13 * t_ref
+    for h in hs:
+        h.close()
+
+
+def test_five_stage_contexts_refuse_three_stage_only_operations():
+    """Recording, frozen replays and the adjoint are of the three-stage scheme; batches do not mix schemes."""
+    hydro = _hydro()
+    prob = wl.advected_wave(32).with_(rk_stages=5)
+    h = hydro.Hydro(prob, dtype="f64")
+    U = h.state(prob.U0)
+    for call in (lambda: h.record(4), lambda: h.forward_checkpointed(U, 4, 2), lambda: h.forward_revolve(U, 4, 1),
+                 lambda: h.adjoint_step(U, U.clone(), 1e-3, np.ones(6))):
+        with pytest.raises(hydro.HydroError) as e:
+            call()
+        assert e.value.code == hydro.EINVAL
+    h3 = hydro.Hydro(prob.with_(rk_stages=3), dtype="f64")
+    with pytest.raises(hydro.HydroError) as e:
+        hydro.hydro_batch_step([h, h3], [U, h3.state(prob.U0)], 1)
+    assert e.value.code == hydro.EINVAL
+    h.step(U, 2)  # the context stays usable
+    h.close()
+    h3.close()
