@@ -59,6 +59,7 @@ struct hydro_ctx {
   int nf = 4;
   size_t esize = 4;
   int variant = 1;
+  int uploaded_variant = -1;  // the variant the device parameters and tensor maps were built for
   // padded layout (sized for the tallest tile variant so every variant fits)
   int pitch = 0, rows = 0, tiles_x = 0, tiles_y = 0;
   long long fstride = 0;
@@ -395,6 +396,7 @@ static int upload_params(hydro_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(c->tmaps, maps, sizeof(CUtensorMap) * c->ns, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
+  c->uploaded_variant = c->variant;
   ++c->params_gen;
   if (c->step_graph) {
     cudaGraphExecDestroy(c->step_graph);
@@ -1040,9 +1042,10 @@ template <typename real>
 static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, double* t, bool writeback = true,
                       double* ms_graph = nullptr) {
   hydro_ctx* c = m[0];
-  // every member on the first member's tile variant
+  // every member (the first included) on the first member's tile variant, with device parameters and
+  // tensor maps built for it
   for (int k = 0; k < n; ++k) {
-    if (m[k]->variant != c->variant) {
+    if (m[k]->variant != c->variant || m[k]->uploaded_variant != c->variant) {
       m[k]->variant = c->variant;
       int rc = upload(m[k]);
       if (rc) return fail(c, rc, "member " + std::to_string(k) + ": " + m[k]->err);
@@ -1233,6 +1236,14 @@ int hydro_batch_autotune(hydro_ctx* const* members, void* const* U, int n, int s
           c->variant = v;
           c->batch_waves = w + 1;
           c->batch_layout = l;
+          rc = upload(c);  // the first member's own parameters and tensor maps for this variant
+          if (rc) {
+            c->variant = keep_v;
+            c->batch_waves = keep_w;
+            c->batch_layout = keep_l;
+            upload(c);
+            return rc;
+          }
           // one untimed step (plan, graph), then `steps` timed graph replays; U is only read
           rc = f64 ? batch_impl<double>(members, U, n, 1, nullptr, false) : batch_impl<float>(members, U, n, 1, nullptr, false);
           double g = 0.0;

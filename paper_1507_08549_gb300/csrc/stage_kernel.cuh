@@ -116,18 +116,32 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait on an mbarrier phase: false after `limit` polls (the caller reports ERR_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, unsigned parity, unsigned limit) {
-  for (unsigned it = 0; it < limit; ++it) {
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: false after `limit` polls or `max_ns` nanoseconds, whichever comes
+// first (a poll of try_wait may suspend the thread for a while, so a poll count alone does not bound the
+// time); the caller reports ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, unsigned parity, unsigned limit,
+                                                unsigned long long max_ns = ~0ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0u && global_ns() - t0 > max_ns) return false;
   }
   return false;
 }
 
-// The stage kernel's wait for a tile's copies: ~2^28 polls (seconds) before giving up.
+// The stage kernel's wait for a tile's copies: at most 2^28 polls and 2 seconds before giving up.
 constexpr unsigned TILE_WAIT_POLLS = 1u << 28;
+constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  return mbar_wait_limit(bar, parity, TILE_WAIT_POLLS);
+  return mbar_wait_limit(bar, parity, TILE_WAIT_POLLS, TILE_WAIT_NS);
 }
 
 
@@ -841,8 +855,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       // a copy did not complete: before the CTA leaves (and its shared memory is reused), wait, again
       // with a limit, for the copies it still has in flight (this box and the prefetched next one)
       if (tid == 0) {
-        mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS);
-        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS);
+        mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
       }
       break;
     }
