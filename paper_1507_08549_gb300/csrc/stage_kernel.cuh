@@ -1008,20 +1008,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
               for (int e = 0; e < EG; ++e) unv[f][e] = real(0);
           }
-          // the five-stage scheme's further stage states (the cell's own values, like U^n)
-          real x0v[NF][EG], x1v[NF][EG];
-          if (use_x0) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-#pragma unroll
-              for (int e = 0; e < EG; ++e) x0v[f][e] = (e < nvalid) ? g.ux0[f * fs + gbase + e] : real(0);
-          }
-          if (use_x1) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-#pragma unroll
-              for (int e = 0; e < EG; ++e) x1v[f][e] = (e < nvalid) ? g.ux1[f * fs + gbase + e] : real(0);
-          }
+
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             real Uv[EG], Dv[EG];
@@ -1052,8 +1039,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               }
               const real L = (f < 4) ? Ar<real>::lval(Dv[e], S) : -Dv[e];
               o[f][e] = (ctl.mode == 1) ? L : Ar<real>::blend(use_un, ra, rb, un[e], Uv[e], dt, L);
-              if (use_x0) o[f][e] = Ar<real>::add_term(o[f][e], rx0, x0v[f][e]);
-              if (use_x1) o[f][e] = Ar<real>::add_term(o[f][e], rx1, x1v[f][e]);
+            }
+            // the five-stage scheme's further stage states (the cell's own values, like U^n)
+            if (use_x0) {
+#pragma unroll
+              for (int e = 0; e < EG; ++e)
+                if (e < nvalid) o[f][e] = Ar<real>::add_term(o[f][e], rx0, g.ux0[f * fs + gbase + e]);
+            }
+            if (use_x1) {
+#pragma unroll
+              for (int e = 0; e < EG; ++e)
+                if (e < nvalid) o[f][e] = Ar<real>::add_term(o[f][e], rx1, g.ux1[f * fs + gbase + e]);
             }
           }
         }
