@@ -66,7 +66,9 @@ struct hydro_ctx {
   int ns = 3;  // stages per step: 3 (SSP-RK3) or 5 (the five-stage third-order scheme)
   // A = U^n / U^{n+1}, B = U^(1), C = U^(2) (and D = U^(3), E = U^(4) of the five-stage scheme)
   void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  void* tmaps = nullptr;  // device CUtensorMap[ns] of the working states for the current tile variant
+  // device CUtensorMap[6]: the working states' halo boxes for the current tile variant (0 .. ns-1) and,
+  // at TMAP_UN_INTERIOR, state A's tile interiors (the L2 prefetch of U^n for the blend)
+  void* tmaps = nullptr;
   void* scratch = nullptr;
   void* params = nullptr;  // device GridParams[NPARAMS]: stages 0..ns-1, frozen stages P_FROZEN.., rhs P_RHS
   void* host_scratch = nullptr;  // pinned copy of Scratch
@@ -212,6 +214,7 @@ static int tile_ty(int variant) { return VARIANTS[variant].ty; }
 // Device parameter table of a context: the step's stages (up to 5), the three frozen SSP-RK3 stages
 // (recorded replays and the adjoint), the spatial operator.
 constexpr int P_FROZEN = 5, P_RHS = 8, NPARAMS = 9;
+constexpr int TMAP_UN_INTERIOR = 5, NTMAPS = 6;
 
 // One stage of a step: W = buffer win, output buffer out, and out = a U^n + rx0 B[x0] + rx1 B[x1]
 // + b (W + c dt L(W)) (x0, x1 = -1: no such term).
@@ -292,12 +295,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tile boxes start at column tx * 60 (240 tx bytes in FP32, 480 tx in FP64: 16-byte aligned) and never
 // leave the allocation (pitch and rows cover whole tiles plus the halo).
 template <typename real>
-static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorMap* out) {
+static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorMap* out, int box_w = BOX_W) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (!fn) return HYDRO_ECUDA;
   const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->rows, (cuuint64_t)c->nf};
   const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(real), (cuuint64_t)c->fstride * sizeof(real)};
-  const cuuint32_t box[3] = {(cuuint32_t)BOX_W, (cuuint32_t)box_h, (cuuint32_t)c->nf};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)c->nf};
   const cuuint32_t estride[3] = {1, 1, 1};
   const CUresult r =
       fn(out, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -344,7 +347,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
     GridParams<real> p = base;
     p.win = bufp<real>(c, r.win);
     p.tmap_win = maps + r.win;
-    p.tmap_un = maps;
+    p.tmap_un = maps + TMAP_UN_INTERIOR;
     p.un = A;
     p.out = bufp<real>(c, r.out);
     p.ux0 = r.x0 >= 0 ? bufp<real>(c, r.x0) : nullptr;
@@ -376,7 +379,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
   GridParams<real> r = base;  // L(W) of buffer A into buffer B
   r.win = A;
   r.tmap_win = maps;
-  r.tmap_un = maps;
+  r.tmap_un = maps + TMAP_UN_INTERIOR;
   r.un = A;
   r.out = B;
   r.alpha_in = s->frozen_alpha[0];
@@ -388,13 +391,16 @@ template <typename real>
 static int upload_params(hydro_ctx* c) {
   GridParams<real> p[NPARAMS];
   build_params<real>(c, p);
-  alignas(64) CUtensorMap maps[5];
+  alignas(64) CUtensorMap maps[NTMAPS];
   for (int k = 0; k < c->ns; ++k) {
     const int rc = encode_state_map<real>(c, c->buf[k], tile_ty(c->variant) + 2 * GY, &maps[k]);
     if (rc) return fail(c, rc, "cuTensorMapEncodeTiled failed for the working states");
   }
+  // A's tile interiors: box (60, TY, nf) at padded column tx * 60 + 4 (16-byte aligned), row ty * TY + 3
+  if (encode_state_map<real>(c, c->buf[0], tile_ty(c->variant), &maps[TMAP_UN_INTERIOR], TILE_X))
+    return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled failed for the U^n interiors");
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(c->tmaps, maps, sizeof(CUtensorMap) * c->ns, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));
   c->uploaded_variant = c->variant;
   ++c->params_gen;
@@ -691,7 +697,7 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   if (cudaMallocHost(&c->host_scratch, sb) != cudaSuccess) return bail(HYDRO_ECUDA);
   const size_t pb = c->esize == 8 ? sizeof(GridParams<double>) * NPARAMS : sizeof(GridParams<float>) * NPARAMS;
   if (cudaMalloc(&c->params, pb) != cudaSuccess) return bail(HYDRO_ECUDA);
-  if (cudaMalloc(&c->tmaps, 5 * sizeof(CUtensorMap)) != cudaSuccess) return bail(HYDRO_ECUDA);
+  if (cudaMalloc(&c->tmaps, NTMAPS * sizeof(CUtensorMap)) != cudaSuccess) return bail(HYDRO_ECUDA);
   c->partial_blocks = 4 * c->num_sms;
   if (cudaMalloc(&c->partials, sizeof(double) * 5 * c->partial_blocks) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaMalloc(&c->d_totals, sizeof(double) * 5) != cudaSuccess) return bail(HYDRO_ECUDA);

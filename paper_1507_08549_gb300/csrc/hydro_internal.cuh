@@ -42,7 +42,7 @@ struct GridParams {
   const real* win;   // stage input W (padded)
   const void* tmap_win;  // device CUtensorMap of win: (x, y, field) with one tile's halo box as its box
   const real* un;    // U^n (padded), read when rk_a != 0
-  const void* tmap_un;   // device CUtensorMap of un (the same box), for L2 prefetches
+  const void* tmap_un;   // device CUtensorMap of un's tile interiors (box 60 x TY x nfields), for L2 prefetches
   const real* ux0;   // further stage states the blend adds (five-stage scheme), else null
   const real* ux1;
   real* out;         // stage output (padded) or L (mode RHS)

@@ -681,7 +681,8 @@ struct Tile {
 
 // Issue the TMA copy of one tile's halo box (one thread): arm the barrier with the box's bytes, then one
 // tensor copy of the (68, TY + 6, NF) box at padded column tx * 60, row ty * TY. With prefetch_un, the
-// same box of U^n is prefetched into L2 for the tile's per-cell phase. m may point to shared memory.
+// tile's own cells of U^n (a (60, TY, NF) box) are prefetched into L2 for the tile's per-cell phase. m may
+// point to shared memory.
 template <typename real>
 __device__ __forceinline__ void issue_box(const GridParams<real>* m, int tile, int TY, real* box, uint64_t* bar,
                                           unsigned bytes, bool prefetch_un) {
@@ -690,7 +691,7 @@ __device__ __forceinline__ void issue_box(const GridParams<real>* m, int tile, i
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   mbar_arrive_expect_tx(bar, bytes);
   tma_load_3d(box, map, tx * TILE_X, ty * TY, 0, bar);
-  if (prefetch_un) tma_prefetch_l2_3d(m->tmap_un, tx * TILE_X, ty * TY, 0);
+  if (prefetch_un) tma_prefetch_l2_3d(m->tmap_un, tx * TILE_X + GX, ty * TY + GY, 0);  // the tile's own cells
 }
 
 // ------------------------------------------------------------------------------ the stage kernel
