@@ -228,7 +228,16 @@ def run_reference(args):
 # capture, averaged over the three stage launches of one RK3 step, per cell), valid only for the kernel
 # source it was captured on: `stage_traffic_per_cell` returns None once stage_kernel.cuh has changed
 # (its SHA-256 differs from the one recorded here).
-STAGE_TRAFFIC = {"stage_kernel_sha256": None, "bytes_per_cell_launch_f32_nf5": None, "capture": None}
+STAGE_TRAFFIC = {
+    "stage_kernel_sha256": "3ecb04bbfd58fa70cd3a6353f41a3f3f4e02cd1a2aff6cd61e28e979d8bc2a0a",
+    # stages 1-3 of one step of the 8192^2 blobs + blast state (5 fields, FP32, tile 60 x 15 / 320 threads):
+    # reads 1817.6, 3303.1, 3169.9 MB, writes 1311.2, 1327.4, 1307.6 MB
+    "bytes_per_cell_launch_f32_nf5": (1817.590016 + 3303.054848 + 3169.940224 + 1311.191552 + 1327.38688
+                                      + 1307.610112) * 1e6 / 3.0 / (8192 * 8192),
+    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
+               "-k regex:stage_kernel -s 9 -c 3 python bench.py --workload blobs_blast_8192 --steps 2 --warmup 3 "
+               "--quick --no-cpu-baseline (1 pass per launch)",
+}
 
 
 def stage_kernel_sha256() -> str:

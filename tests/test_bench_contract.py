@@ -210,3 +210,14 @@ def test_crop_keeps_rows_and_columns_apart():
     oracle.step(sub, sub.U0, 1)  # a consistent problem the oracle accepts
     line = bench.cpu_baseline(p.with_(nx=24, ny=10), seconds=0.05)
     assert line["kind"] == "oracle" and line["sample"].startswith("24x10 crop")
+
+
+def test_traffic_figure_is_tied_to_the_kernel_source(monkeypatch):
+    """The measured DRAM traffic per stage launch is reported only for the stage-kernel source it was
+    captured on: a changed source (another SHA-256) gives null, so a stale capture is never reported."""
+    sys.path.insert(0, ROOT)
+    import bench
+    per_cell = bench.stage_traffic_per_cell()
+    assert per_cell is not None and 53.0 < per_cell < 80.0  # algorithmic 160/3 = 53.3 bytes per cell and launch
+    monkeypatch.setattr(bench, "stage_kernel_sha256", lambda: "0" * 64)
+    assert bench.stage_traffic_per_cell() is None
