@@ -139,6 +139,9 @@ def test_forward_path_times_again_after_a_rejected_clock_record(monkeypatch, cap
         def tile_variants(self):
             return 1, 0
 
+        def autotune(self, U, steps=3):
+            return [0.5]
+
         def tile_info(self, v):
             return {"variant": v}
 
