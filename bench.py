@@ -225,18 +225,20 @@ def run_reference(args):
 
 
 # Measured DRAM traffic of the stage kernel (dram__bytes_read.sum + dram__bytes_write.sum from one ncu
-# capture, averaged over the three stage launches of one RK3 step, per cell), valid only for the kernel
-# source it was captured on: `stage_traffic_per_cell` returns None once stage_kernel.cuh has changed
-# (its SHA-256 differs from the one recorded here).
+# capture, averaged over the three stage launches of one RK3 step, per cell), per tile shape, valid only for
+# the kernel source it was captured on: `stage_traffic_per_cell` returns None once stage_kernel.cuh has
+# changed (its SHA-256 differs from the one recorded here) or for a tile shape without a capture.
 STAGE_TRAFFIC = {
     "stage_kernel_sha256": "3ecb04bbfd58fa70cd3a6353f41a3f3f4e02cd1a2aff6cd61e28e979d8bc2a0a",
-    # stages 1-3 of one step of the 8192^2 blobs + blast state (5 fields, FP32, tile 60 x 15 / 320 threads):
-    # reads 1817.6, 3303.1, 3169.9 MB, writes 1311.2, 1327.4, 1307.6 MB
-    "bytes_per_cell_launch_f32_nf5": (1817.590016 + 3303.054848 + 3169.940224 + 1311.191552 + 1327.38688
-                                      + 1307.610112) * 1e6 / 3.0 / (8192 * 8192),
+    # bytes per cell and launch of the 8192^2 blobs + blast state (5 fields, FP32), by tile "TXxTY"
+    "bytes_per_cell_launch_f32_nf5": {
+        # reads 1817.6, 3303.1, 3169.9 MB, writes 1311.2, 1327.4, 1307.6 MB
+        "60x15": (1817.590016 + 3303.054848 + 3169.940224 + 1311.191552 + 1327.38688 + 1307.610112) * 1e6
+        / 3.0 / (8192 * 8192),
+    },
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
                "-k regex:stage_kernel -s 9 -c 3 python bench.py --workload blobs_blast_8192 --steps 2 --warmup 3 "
-               "--quick --no-cpu-baseline (1 pass per launch)",
+               "--quick --no-cpu-baseline --variant V (1 pass per launch)",
 }
 
 
@@ -247,13 +249,12 @@ def stage_kernel_sha256() -> str:
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def stage_traffic_per_cell():
-    """Measured bytes per cell and stage launch of the current stage kernel source, else None."""
-    if STAGE_TRAFFIC["bytes_per_cell_launch_f32_nf5"] is None:
-        return None
+def stage_traffic_per_cell(tile: str = "60x15"):
+    """Measured bytes per cell and stage launch of the current stage kernel source with tile shape
+    "TXxTY", else None."""
     if stage_kernel_sha256() != STAGE_TRAFFIC["stage_kernel_sha256"]:
         return None
-    return STAGE_TRAFFIC["bytes_per_cell_launch_f32_nf5"]
+    return STAGE_TRAFFIC["bytes_per_cell_launch_f32_nf5"].get(tile)
 
 
 # FP32 arithmetic operations per cell and RK stage (one per rounded operation, a fused multiply-add counted
@@ -591,7 +592,7 @@ def run(args):
     value = replica_rate(cells * args.steps, ms * 1e-3, world)
     F, B = prob.nfields, (8 if dtype == "f64" else 4)
     traffic = None
-    per_cell = stage_traffic_per_cell()
+    per_cell = stage_traffic_per_cell(f"{info['tile_x']}x{info['tile_y']}")
     if dtype == "f32" and F == 5 and args.workload.startswith("blobs_blast") and per_cell is not None:
         # measured average traffic of a stage launch per cell of this kernel source, times cells
         traffic = per_cell * cells

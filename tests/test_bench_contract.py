@@ -220,7 +220,8 @@ def test_traffic_figure_is_tied_to_the_kernel_source(monkeypatch):
     captured on: a changed source (another SHA-256) gives null, so a stale capture is never reported."""
     sys.path.insert(0, ROOT)
     import bench
-    per_cell = bench.stage_traffic_per_cell()
+    per_cell = bench.stage_traffic_per_cell("60x15")
     assert per_cell is not None and 53.0 < per_cell < 80.0  # algorithmic 160/3 = 53.3 bytes per cell and launch
+    assert bench.stage_traffic_per_cell("61x17") is None  # no capture for that tile shape
     monkeypatch.setattr(bench, "stage_kernel_sha256", lambda: "0" * 64)
-    assert bench.stage_traffic_per_cell() is None
+    assert bench.stage_traffic_per_cell("60x15") is None
