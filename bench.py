@@ -235,6 +235,9 @@ STAGE_TRAFFIC = {
         # reads 1817.6, 3303.1, 3169.9 MB, writes 1311.2, 1327.4, 1307.6 MB
         "60x15": (1817.590016 + 3303.054848 + 3169.940224 + 1311.191552 + 1327.38688 + 1307.610112) * 1e6
         / 3.0 / (8192 * 8192),
+        # reads 1356.7, 2710.4, 2706.5 MB, writes 1300.8, 1314.3, 1298.1 MB
+        "60x30": (1356.706304 + 2710.400768 + 2706.529024 + 1300.84352 + 1314.285824 + 1298.128896) * 1e6
+        / 3.0 / (8192 * 8192),
     },
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
                "-k regex:stage_kernel -s 9 -c 3 python bench.py --workload blobs_blast_8192 --steps 2 --warmup 3 "

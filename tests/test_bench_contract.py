@@ -143,7 +143,7 @@ def test_forward_path_times_again_after_a_rejected_clock_record(monkeypatch, cap
             return [0.5]
 
         def tile_info(self, v):
-            return {"variant": v}
+            return {"variant": v, "tile_x": 60, "tile_y": 15, "threads": 320}
 
         def close(self):
             pass
