@@ -428,18 +428,24 @@ struct Ar<double> {
 //
 // One line of K cells: points m = 0 .. K+5 (cells -3 .. K+2 of the run), faces f = 0 .. K (left face
 // of cell f). Writes (or adds) D[k] = (fhat_{k+1/2} - fhat_{k-1/2}) / h for k = 0 .. K-1, where
-// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). Strides are runtime
-// values so the x and y passes run the same instructions.
+// fhat = W(f+ at the 5 points left-biased) + W(f- at the 5 points right-biased). The FP32 lines take their
+// strides (points S, velocities VS, outputs DS) and the accumulate flag either as compile-time values (one
+// instance per pass: every shared-memory access an immediate offset from the line's base pointers; used where
+// one CTA per SM keeps the instruction footprint of the two instances affordable) or at run time (template
+// values 0 and -1: one instance serves both passes).
 //
 // FP32 works on g+- = F +- alpha U = 2 f+- (the 1/2 goes into the final difference; eps scales by 4 with
 // the squared differences, so the weights are those of f+-) through the triplet form above, and forms
 // every flux kind as (U + c_E p) v_n + c_A p (c_E = 1 for energy, c_A = 1 for the normal momentum; the
 // mass flux is rho v_n), so the line has no flux-kind branches.
-template <int K>
+template <int K, int CS = 0, int CVS = 0, int CDS = 0, int CACC = -1>
 __device__ __forceinline__ void hydro_line_tri(const float* __restrict__ Uc, const float* __restrict__ vel,
-                                               const float* __restrict__ pr, int S, int VS, int kind, float alpha,
-                                               float rd, float* __restrict__ dst, int DS, bool accumulate) {
+                                               const float* __restrict__ pr, int S_rt, int VS_rt, int kind,
+                                               float alpha, float rd, float* __restrict__ dst, int DS_rt,
+                                               bool acc_rt) {
   using T = RT<float>;
+  const int S = CS ? CS : S_rt, VS = CVS ? CVS : VS_rt, DS = CDS ? CDS : DS_rt;
+  const bool accumulate = CACC >= 0 ? CACC != 0 : acc_rt;
   constexpr float EPS = 4e-6f * TRI_EPS_SCALE;
   const float rdh = T::mul_(0.5f, rd);
   const float cE = kind == 3 ? 1.0f : 0.0f, cA = kind == 1 ? 1.0f : 0.0f;
@@ -506,9 +512,10 @@ __device__ __forceinline__ void hydro_line_f64(const double* __restrict__ Uc, co
 // m = 0 .. K+5: differences d_n = (phi_{n+1} - phi_n) / h, n = 0 .. K+4; cell k takes
 // phi^- = W(d_k .. d_{k+4}) and phi^+ = W(d_{k+5} .. d_{k+1}), stored to om[k*DS], op[k*DS]. FP32 forms
 // each difference triplet's smoothness data once for both derivatives.
-template <int K>
-__device__ __forceinline__ void phi_line_tri(const float* __restrict__ ph, int S, float rd, float* __restrict__ om,
-                                             float* __restrict__ op, int DS) {
+template <int K, int CS = 0, int CDS = 0>
+__device__ __forceinline__ void phi_line_tri(const float* __restrict__ ph, int S_rt, float rd, float* __restrict__ om,
+                                             float* __restrict__ op, int DS_rt) {
+  const int S = CS ? CS : S_rt, DS = CDS ? CDS : DS_rt;
   constexpr float EPS = 1e-6f * TRI_EPS_SCALE;
   float d[K + 5];
   Tri32 tl[K + 5], tr[K + 5];
@@ -723,6 +730,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
 
+  // compile-time line strides where one CTA runs per SM (its warps share one phase's code, so the two
+  // instances' instruction footprint costs less than the address arithmetic they save: 2.87 -> 2.78 ms per
+  // 8192^2 launch of the 640-thread variant; with two CTAs per SM the runtime-stride line measured faster)
+  constexpr bool kCts = NT >= 640;
   // the tensor copies write 128-byte aligned buffers: a launch that finds its dynamic shared memory
   // elsewhere reports it and returns before any copy (the same address for every thread)
   if ((smem_u32(smem_raw) & 127u) != 0u) {
@@ -918,17 +929,33 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const real* Uc = sU + (c * H + brow) * W + bcol;
           const real* Xc = sU + ((xp ? 1 : 2) * H + brow) * W + bcol;
           const real* vel = xp ? su + trow * W + bcol : sv + brow * TX + tcol;
-          if constexpr (sizeof(real) == 4)
-            hydro_line_tri<K>(Uc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd,
-                              sD + (c * TY + trow) * TX + tcol, DS, !xp);
-          else
+          if constexpr (sizeof(real) == 4) {
+            if constexpr (kCts) {
+              if (xp)
+                hydro_line_tri<K, 1, 1, 1, 0>(Uc, vel, sp + brow * W + bcol, 1, 1, kind, alpha, rd,
+                                              sD + (c * TY + trow) * TX + tcol, 1, false);
+              else
+                hydro_line_tri<K, W, TX, TX, 1>(Uc, vel, sp + brow * W + bcol, W, TX, kind, alpha, rd,
+                                                sD + (c * TY + trow) * TX + tcol, TX, true);
+            } else {
+              hydro_line_tri<K>(Uc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, rd,
+                                sD + (c * TY + trow) * TX + tcol, DS, !xp);
+            }
+          } else
             hydro_line_f64<K>(Uc, Xc, vel, sp + brow * W + bcol, S, xp ? 1 : TX, kind, alpha, h,
                               sD + (c * TY + trow) * TX + tcol, DS, !xp);
         } else {
           real* om = sX + ((xp ? 0 : 2) * TY + trow) * TX + tcol;
-          if constexpr (sizeof(real) == 4)
-            phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
-          else
+          if constexpr (sizeof(real) == 4) {
+            if constexpr (kCts) {
+              if (xp)
+                phi_line_tri<K, 1, 1>(sU + (4 * H + brow) * W + bcol, 1, rd, om, om + TY * TX, 1);
+              else
+                phi_line_tri<K, W, TX>(sU + (4 * H + brow) * W + bcol, W, rd, om, om + TY * TX, TX);
+            } else {
+              phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
+            }
+          } else
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
         }
       }
