@@ -66,8 +66,8 @@ struct hydro_ctx {
   int ns = 3;  // stages per step: 3 (SSP-RK3) or 5 (the five-stage third-order scheme)
   // A = U^n / U^{n+1}, B = U^(1), C = U^(2) (and D = U^(3), E = U^(4) of the five-stage scheme)
   void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  // device CUtensorMap[6]: the working states' halo boxes for the current tile variant (0 .. ns-1) and,
-  // at TMAP_UN_INTERIOR, state A's tile interiors (the L2 prefetch of U^n for the blend)
+  // device CUtensorMap[NTMAPS]: the working states' halo boxes for the current tile variant (0 .. ns-1)
+  // and, from TMAP_INTERIOR on, the same states' tile interiors (U^n for the blend, the tensor stores)
   void* tmaps = nullptr;
   void* scratch = nullptr;
   void* params = nullptr;  // device GridParams[NPARAMS]: stages 0..ns-1, frozen stages P_FROZEN.., rhs P_RHS
@@ -214,7 +214,7 @@ static int tile_ty(int variant) { return VARIANTS[variant].ty; }
 // Device parameter table of a context: the step's stages (up to 5), the three frozen SSP-RK3 stages
 // (recorded replays and the adjoint), the spatial operator.
 constexpr int P_FROZEN = 5, P_RHS = 8, NPARAMS = 9;
-constexpr int TMAP_UN_INTERIOR = 5, NTMAPS = 6;
+constexpr int TMAP_INTERIOR = 5, NTMAPS = 10;
 
 // One stage of a step: W = buffer win, output buffer out, and out = a U^n + rx0 B[x0] + rx1 B[x1]
 // + b (W + c dt L(W)) (x0, x1 = -1: no such term).
@@ -340,6 +340,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
   base.t_acc = &s->t_acc;
   base.err = &s->err;
   base.ext_div = static_cast<const real*>(c->char_div ? c->char_div : c->split_div);
+  base.tmap_ty = tile_ty(c->variant);
   real* A = bufp<real>(c, 0);
   real* B = bufp<real>(c, 1);
   const CUtensorMap* maps = static_cast<const CUtensorMap*>(c->tmaps);
@@ -347,9 +348,10 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
     GridParams<real> p = base;
     p.win = bufp<real>(c, r.win);
     p.tmap_win = maps + r.win;
-    p.tmap_un = maps + TMAP_UN_INTERIOR;
+    p.tmap_un = maps + TMAP_INTERIOR;
     p.un = A;
     p.out = bufp<real>(c, r.out);
+    p.tmap_out = maps + TMAP_INTERIOR + r.out;
     p.ux0 = r.x0 >= 0 ? bufp<real>(c, r.x0) : nullptr;
     p.ux1 = r.x1 >= 0 ? bufp<real>(c, r.x1) : nullptr;
     p.alpha_in = s->alpha[k];
@@ -379,9 +381,10 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
   GridParams<real> r = base;  // L(W) of buffer A into buffer B
   r.win = A;
   r.tmap_win = maps;
-  r.tmap_un = maps + TMAP_UN_INTERIOR;
+  r.tmap_un = maps + TMAP_INTERIOR;
   r.un = A;
   r.out = B;
+  r.tmap_out = maps + TMAP_INTERIOR + 1;
   r.alpha_in = s->frozen_alpha[0];
   r.dt_src = &s->frozen_dt;
   out[P_RHS] = r;
@@ -391,14 +394,15 @@ template <typename real>
 static int upload_params(hydro_ctx* c) {
   GridParams<real> p[NPARAMS];
   build_params<real>(c, p);
-  alignas(64) CUtensorMap maps[NTMAPS];
+  alignas(64) CUtensorMap maps[NTMAPS] = {};
   for (int k = 0; k < c->ns; ++k) {
     const int rc = encode_state_map<real>(c, c->buf[k], tile_ty(c->variant) + 2 * GY, &maps[k]);
     if (rc) return fail(c, rc, "cuTensorMapEncodeTiled failed for the working states");
   }
-  // A's tile interiors: box (60, TY, nf) at padded column tx * 60 + 4 (16-byte aligned), row ty * TY + 3
-  if (encode_state_map<real>(c, c->buf[0], tile_ty(c->variant), &maps[TMAP_UN_INTERIOR], TILE_X))
-    return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled failed for the U^n interiors");
+  // the tile interiors: box (60, TY, nf) at padded column tx * 60 + 4 (16-byte aligned), row ty * TY + 3
+  for (int k = 0; k < c->ns; ++k)
+    if (encode_state_map<real>(c, c->buf[k], tile_ty(c->variant), &maps[TMAP_INTERIOR + k], TILE_X))
+      return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled failed for the tile interiors");
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));

@@ -42,7 +42,9 @@ struct GridParams {
   const real* win;   // stage input W (padded)
   const void* tmap_win;  // device CUtensorMap of win: (x, y, field) with one tile's halo box as its box
   const real* un;    // U^n (padded), read when rk_a != 0
-  const void* tmap_un;   // device CUtensorMap of un's tile interiors (box 60 x TY x nfields), for L2 prefetches
+  const void* tmap_un;   // device CUtensorMap of un's tile interiors (box 60 x TY x nfields)
+  const void* tmap_out;  // device CUtensorMap of out's tile interiors (the tensor store of a whole tile)
+  int tmap_ty;           // the tile height the tensor maps' boxes were built for
   const real* ux0;   // further stage states the blend adds (five-stage scheme), else null
   const real* ux1;
   real* out;         // stage output (padded) or L (mode RHS)

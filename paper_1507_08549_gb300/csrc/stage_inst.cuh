@@ -13,7 +13,7 @@ namespace {
 template <typename real, int NF, int V>
 struct VariantLaunch {
   static constexpr int TY = VARIANTS[V].ty, NT = VARIANTS[V].threads;
-  static constexpr size_t SMEM = Tile<real, NF, TY>::BYTES;
+  static constexpr size_t SMEM = Tile<real, NF, TY, un_in_smem<real>(NT)>::BYTES;
   static cudaError_t configure() {
     static cudaError_t once = [] {
       cudaError_t e = cudaFuncSetAttribute(stage_kernel<real, NF, TY, NT>,

@@ -99,6 +99,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
       : "memory");
 }
 
+// Tensor store of one box of a 3-D tensor map from shared memory (src 128-byte aligned), tracked by the
+// issuing thread's bulk async-group: commit after issuing, then wait until the source has been read
+// (before the buffer is written again) or until the writes are done (before the CTA exits).
+__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
+               "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // L2 prefetch of one box of a 3-D tensor map (no shared memory, no completion to wait for).
 __device__ __forceinline__ void tma_prefetch_l2_3d(const void* tmap, int x, int y, int z) {
   asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tmap), "r"(x), "r"(y),
@@ -658,7 +670,13 @@ __device__ __forceinline__ void write_ghost_images(real* out, long long fs, int 
 
 // ------------------------------------------------------------------------------ tile geometry
 
-template <typename real, int NF, int TY>
+// The FP32 kernel of one CTA per SM (640 threads, 60 x 30 tiles) has the shared memory to hold the tile's
+// own cells of U^n: a TMA copy issued at the start of each tile, read by the per-cell phase (the other
+// variants prefetch those cells into L2 instead).
+template <typename real>
+__host__ __device__ constexpr bool un_in_smem(int threads) { return sizeof(real) == 4 && threads >= 640; }
+
+template <typename real, int NF, int TY, bool UNS = false>
 struct Tile {
   static constexpr int TX = TILE_X, W = BOX_W, H = TY + 6, K = RUN, NQ = TX / RUN;
   static constexpr int NQY = TY / RUN;                   // y runs per column
@@ -673,14 +691,18 @@ struct Tile {
   static constexpr int OFF_PU = OFF_U1 + BOX_PAD;       // [TY][W]      u on the tile rows
   static constexpr int OFF_PV = OFF_PU + TY * W;        // [H][TX]      v on the tile columns
   static constexpr int OFF_PP = OFF_PV + H * TX;        // [H][W]       p
-  static constexpr int OFF_D = OFF_PP + H * W;          // [NF][TY][TX] dF/dx + dG/dy (and H_hat)
+  // [NF][TY][TX] dF/dx + dG/dy, then the tile's outputs (the tensor store's source: 128-byte aligned)
+  static constexpr int OFF_D = (((OFF_PP + H * W) * (int)sizeof(real) + 127) / 128) * 128 / (int)sizeof(real);
   static constexpr int OFF_X = OFF_D + NF * TY * TX;    // [4][TY][TX]  phi_x^-, phi_x^+, phi_y^-, phi_y^+
-  static constexpr int ELEMS = OFF_X + (NF == 5 ? 4 * TY * TX : 0);
+  static constexpr int END_X = OFF_X + (NF == 5 ? 4 * TY * TX : 0);
+  static constexpr int OFF_UN = ((END_X * (int)sizeof(real) + 127) / 128) * 128 / (int)sizeof(real);  // [NF][TY][TX]
+  static constexpr int ELEMS = UNS ? OFF_UN + NF * TY * TX : END_X;
+  static constexpr unsigned UN_BYTES = NF * TY * TX * sizeof(real);
   // per-warp running slots (<= 20 warps): 3 maxima and 5 totals; FP32 adds 5 compensation terms (16 floats)
   static constexpr int RED_STRIDE = sizeof(real) == 4 ? 16 : 8;
   static constexpr int RED_ELEMS = 20 * RED_STRIDE;
   static constexpr size_t RED_OFF = ((ELEMS * sizeof(real) + 15) / 16) * 16;
-  static constexpr size_t BYTES = RED_OFF + RED_ELEMS * sizeof(real) + 32;
+  static constexpr size_t BYTES = RED_OFF + RED_ELEMS * sizeof(real) + 32;  // + 3 mbarriers
   static constexpr unsigned BOX_BYTES = BOX * sizeof(real);
   static_assert(TX % RUN == 0 && TY % RUN == 0, "tiles are whole runs");
   static_assert(TX % EG == 0, "tile rows are whole cell groups");
@@ -708,7 +730,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     stage_kernel(const GridParams<real>* __restrict__ members, const WorkItem* __restrict__ work, int nwork,
                  StageCtl ctl) {
   using T = RT<real>;
-  using TL = Tile<real, NF, TY>;
+  constexpr bool kUnSmem = un_in_smem<real>(NT);
+  using TL = Tile<real, NF, TY, kUnSmem>;
   constexpr int TX = TL::TX, W = TL::W, H = TL::H, K = TL::K, NQ = TL::NQ;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -719,7 +742,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   real* sD = sm + TL::OFF_D;
   real* sX = sm + TL::OFF_X;
   real* red = reinterpret_cast<real*>(smem_raw + TL::RED_OFF);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_ELEMS);  // two barriers, one per box buffer
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + TL::RED_ELEMS);  // one barrier per box buffer, one for U^n
+  real* sUn = sm + TL::OFF_UN;
   __shared__ GridParams<real> g;
   __shared__ int s_abort;
   // stage scalars, formed once per CTA and member (dt needs an FP64 division at stage 0; the FP64 pipe
@@ -743,14 +767,17 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     s_abort = 0;
   }
   for (int k = tid; k < TL::RED_ELEMS; k += NT) red[k] = real(0);
   __syncthreads();
 
   // the blend of stages 2 and 3 reads U^n in the per-cell phase: its tile box is prefetched into L2 with
-  // the halo box
-  const bool prefetch_un = ctl.mode == 0 && ctl.rk_a != 0.0;
+  // the halo box, or (one CTA per SM, FP32) copied into shared memory at the start of the tile
+  const bool blend_un = ctl.mode == 0 && ctl.rk_a != 0.0;
+  const bool prefetch_un = blend_un && !kUnSmem;
+  unsigned un_parity = 0u;
   // prologue: the first work item's box
   if (tid == 0 && static_cast<int>(blockIdx.x) < nwork) {
     const int w0 = blockIdx.x;
@@ -872,6 +899,13 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       }
       break;
     }
+    // the tile's own cells of U^n (its reads by the previous tile ended at the barrier above)
+    const bool maps_fit = g.tmap_ty == TY;  // the interior maps' boxes are this kernel's tiles
+    const bool un_copy = kUnSmem && blend_un && maps_fit;
+    if (un_copy && tid == 0) {
+      mbar_arrive_expect_tx(&bar[2], TL::UN_BYTES);
+      tma_load_3d(sUn, g.tmap_un, x0 + GX, y0 + GY, 0, &bar[2]);
+    }
 
     // ---- B. primitive variables
     const real gm1 = g.gm1;
@@ -887,6 +921,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       if (irow) su[(row - 3) * W + col] = u;
       if (icol) sv[row * TX + (col - 4)] = v;
     }
+    if (tid == 0) bulk_wait_read_all();  // the previous tile's tensor store has read sD
     __syncthreads();
 
     // ---- C/D. x pass then y pass through the same line code: items (field, line, run of 15 cells)
@@ -974,6 +1009,16 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
     }
 
     // ---- E. per cell: sources, RK blend, stores, ghost images, reductions
+    // a whole tile inside the grid leaves through one tensor store of its outputs (written over its own
+    // D values in sD); a ragged tile is stored cell by cell (a store of its box would reach the ghost frame)
+    const bool tile_store = split_field < 0 && maps_fit && x0 + TX <= g.nx && y0 + TY <= g.ny;
+    if (un_copy) {  // each thread waits for the U^n copy itself (its writes become visible)
+      if (!mbar_wait_bounded(&bar[2], un_parity)) {
+        atomicOr(g.err, ERR_TIMEOUT);
+        s_abort = 1;  // this tile's outputs are void; the CTA leaves at the end of the tile
+      }
+      un_parity ^= 1u;
+    }
     real amx = real(0), amy = real(0), smx = real(0);
     // totals: FP64 per cell in the FP64 kernel; the FP32 kernel sums U_f (times r in (r,z)) over a thread's
     // cells and then over its warp in FP32, the warp partials over the CTA's tiles as compensated FP32
@@ -994,7 +1039,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       const bool rz = g.geometry == 1;
       const real dt = s_dt;
       const real ra = s_ra, rb = s_rb;
-      const bool use_un = ra != real(0) && ctl.mode == 0;
+      const bool use_un = blend_un;
       const real rx0 = s_rx0, rx1 = s_rx1;
       const bool use_x0 = g.ux0 != nullptr && ctl.mode == 0, use_x1 = g.ux1 != nullptr && ctl.mode == 0;
       constexpr int NG = TX / EG;
@@ -1020,7 +1065,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           }
           // every U^n value of the group is loaded before any is used: one memory latency, not one per field
           real unv[NF][EG];
-          if (use_un) {
+          if (un_copy) {  // columns past the grid hold ghost or fill values, never stored
+#pragma unroll
+            for (int f = 0; f < NF; ++f) loadg<EG>(sUn + (f * TY + row) * TX + tcol, unv[f]);
+          } else if (use_un) {
             if (nvalid == EG) {
 #pragma unroll
               for (int f = 0; f < NF; ++f) loadg<EG>(g.un + f * fs + gbase, unv[f]);
@@ -1081,16 +1129,22 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             }
           }
         }
-        // stores into the padded working state
+        // the outputs: over the cells' own D values in sD (the tile's tensor store), or cell by cell into
+        // the padded working state
+        if (tile_store) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          real* dstp = g.out + f * fs + gbase;
-          if (nvalid == EG) {
-            storeg<EG>(dstp, o[f]);
-          } else {
+          for (int f = 0; f < NF; ++f) storeg<EG>(sD + (f * TY + row) * TX + tcol, o[f]);
+        } else {
 #pragma unroll
-            for (int e = 0; e < EG; ++e)
-              if (e < nvalid) dstp[e] = o[f][e];
+          for (int f = 0; f < NF; ++f) {
+            real* dstp = g.out + f * fs + gbase;
+            if (nvalid == EG) {
+              storeg<EG>(dstp, o[f]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < EG; ++e)
+                if (e < nvalid) dstp[e] = o[f][e];
+            }
           }
         }
         if (ctl.mode == 1) continue;
@@ -1174,10 +1228,24 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
       }
     }
-    // the next copy overwrites the box: everyone is done reading it (generic proxy) before TMA writes
+    // the outputs in sD (generic-proxy writes) become visible to the tensor store, and the next copy
+    // overwrites the box: everyone is done reading it (generic proxy) before TMA writes
+    if (tile_store) fence_proxy_async_smem();
     __syncthreads();
     fence_proxy_async_smem();
+    if (tile_store && tid == 0) {
+      tma_store_3d(g.tmap_out, sD, x0 + GX, y0 + GY, 0);
+      bulk_commit();
+    }
+    if (kUnSmem && s_abort) {  // the U^n copy did not complete: wait (with a limit) for the copies in flight
+      if (tid == 0) {
+        mbar_wait_limit(&bar[2], un_parity ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
+      }
+      break;
+    }
   }
+  if (tid == 0) bulk_wait_all();  // the tensor stores are complete before the CTA exits
   if (cur_member >= 0) flush();
 }
 
