@@ -789,6 +789,13 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   unsigned parity[2] = {0u, 0u};
   int cur_member = -1;
   int it = 0;
+  // The one-CTA-per-SM variant pipelines the per-cell phase of a tile with the next tile's box wait and
+  // primitives (no barrier between them: the per-cell phase reads only the tile's box, sD, sX and the U^n
+  // buffer, which also receives its outputs): the previous tile's tensor store and the next box are issued
+  // after the primitives' barrier, and the tile's U^n copy after the store has read the buffer.
+  bool prev_store = false;  // the previous tile's outputs wait in sUn for their tensor store
+  const void* prev_map = nullptr;
+  int prev_x = 0, prev_y = 0;
   // Reductions of the outputs (next stage's alpha, next step's dt, totals) accumulate per warp in
   // red[warp * RED_STRIDE + slot] across this CTA's tiles of one member (each tile: a warp shuffle, lane 0
   // updates its slots) and are flushed by each warp's lane 0 -- one atomic per slot, no barrier -- when
@@ -841,9 +848,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       __syncthreads();
       cur_member = member;
     }
-    // prefetch the next item's box into the other buffer (free since the previous tile ended)
+    // prefetch the next item's box into the other buffer (free since the previous tile ended; pipelined:
+    // after the primitives' barrier)
     const int wn = w + gridDim.x;
-    if (tid == 0 && wn < nwork) {
+    if (!kUnSmem && tid == 0 && wn < nwork) {
       const int mn = work ? work[wn].member : 0;
       // the member's parameters come from the shared copy when the next item is of the same member
       issue_box<real>(mn == member ? &g : members + mn,
@@ -889,23 +897,21 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       s_abort = 1;
     }
     parity[b] ^= 1u;
-    __syncthreads();
-    if (s_abort) {
-      // a copy did not complete: before the CTA leaves (and its shared memory is reused), wait, again
-      // with a limit, for the copies it still has in flight (this box and the prefetched next one)
-      if (tid == 0) {
-        mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
-        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
+    if constexpr (!kUnSmem) {
+      __syncthreads();
+      if (s_abort) {
+        // a copy did not complete: before the CTA leaves (and its shared memory is reused), wait, again
+        // with a limit, for the copies it still has in flight (this box and the prefetched next one)
+        if (tid == 0) {
+          mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+          if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
+        }
+        break;
       }
-      break;
     }
-    // the tile's own cells of U^n (its reads by the previous tile ended at the barrier above)
     const bool maps_fit = g.tmap_ty == TY;  // the interior maps' boxes are this kernel's tiles
+    // the tile's own cells of U^n, copied during the x pass
     const bool un_copy = kUnSmem && blend_un && maps_fit;
-    if (un_copy && tid == 0) {
-      mbar_arrive_expect_tx(&bar[2], TL::UN_BYTES);
-      tma_load_3d(sUn, g.tmap_un, x0 + GX, y0 + GY, 0, &bar[2]);
-    }
 
     // ---- B. primitive variables
     const real gm1 = g.gm1;
@@ -921,8 +927,35 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
       if (irow) su[(row - 3) * W + col] = u;
       if (icol) sv[row * TX + (col - 4)] = v;
     }
-    if (tid == 0) bulk_wait_read_all();  // the previous tile's tensor store has read sD
-    __syncthreads();
+    if constexpr (kUnSmem) {
+      if (prev_store) fence_proxy_async_smem();  // the previous tile's outputs, for its tensor store
+      __syncthreads();
+      if (s_abort) {
+        // a copy did not complete: wait (with a limit) for the copies in flight -- this box, or the
+        // previous tile's U^n -- before the CTA leaves; nothing else has been issued since
+        if (tid == 0) {
+          mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+          mbar_wait_limit(&bar[2], un_parity ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+        }
+        prev_store = false;
+        break;
+      }
+      if (tid == 0) {
+        fence_proxy_async_smem();  // everyone's reads of the previous tile's box and of sUn come first
+        if (prev_store) {
+          tma_store_3d(prev_map, sUn, prev_x, prev_y, 0);
+          bulk_commit();
+        }
+        if (wn < nwork) {
+          const int mn = work ? work[wn].member : 0;
+          issue_box<real>(mn == member ? &g : members + mn, work ? work[wn].tile : ctl.w0 + wn, TY,
+                          sm + (b ? TL::OFF_U0 : TL::OFF_U1), &bar[b ^ 1], TL::BOX_BYTES, false);
+        }
+      }
+    } else {
+      if (tid == 0) bulk_wait_read_all();  // the previous tile's tensor store has read sD
+      __syncthreads();
+    }
 
     // ---- C/D. x pass then y pass through the same line code: items (field, line, run of 15 cells)
     // Items [c per_c, (c+1) per_c) of both passes carry field c. When every item has its own thread, the
@@ -994,6 +1027,13 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             phi_line_f64<K>(sU + (4 * H + brow) * W + bcol, S, h, om, om + TY * TX, DS);
         }
       }
+      if (kUnSmem && xp && tid == 0) {
+        bulk_wait_read_all();  // the previous tile's tensor store has read sUn
+        if (un_copy) {
+          mbar_arrive_expect_tx(&bar[2], TL::UN_BYTES);
+          tma_load_3d(sUn, g.tmap_un, x0 + GX, y0 + GY, 0, &bar[2]);
+        }
+      }
       if (xp && kFieldSync && split_field < 0) {
         const int cm = tid / TL::XI_PER_C;  // the field whose lines this thread carries in both passes
         switch (cm) {  // warp-uniform
@@ -1057,11 +1097,23 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
             for (int e = 0; e < EG; ++e) rr[e] = Ar<real>::radius(g, ib + e);
           }
-          const bool need_prims = rz || grav != real(0) || NF == 5;
-          if (need_prims) {
-            loadg<EG>(su + row * W + scol, u4);
-            loadg<EG>(sv + srow * TX + tcol, v4);
-            loadg<EG>(sp + srow * W + scol, p4);
+          const bool sources = rz || grav != real(0);
+          if constexpr (kUnSmem) {  // pipelined: the next tile's primitives overwrite su, sv, sp meanwhile,
+                                    // so the cell's own come from its box values (the same operations)
+            if (sources || NF == 5) {
+#pragma unroll
+              for (int e = 0; e < EG; ++e) {
+                const int c0 = srow * W + scol + e;
+                Ar<real>::prims(sU[0 * H * W + c0], sU[1 * H * W + c0], sU[2 * H * W + c0], sU[3 * H * W + c0], gm1,
+                                u4[e], v4[e], p4[e]);
+              }
+            }
+          } else {
+            if (sources || NF == 5) {  // the level set's Hamiltonian needs u and v, the sources p as well
+              loadg<EG>(su + row * W + scol, u4);
+              loadg<EG>(sv + srow * TX + tcol, v4);
+            }
+            if (sources) loadg<EG>(sp + srow * W + scol, p4);
           }
           // every U^n value of the group is loaded before any is used: one memory latency, not one per field
           real unv[NF][EG];
@@ -1131,9 +1183,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
         // the outputs: over the cells' own D values in sD (the tile's tensor store), or cell by cell into
         // the padded working state
-        if (tile_store) {
+        if (tile_store) {  // pipelined: over the cell's own U^n values in sUn, read above by this thread
 #pragma unroll
-          for (int f = 0; f < NF; ++f) storeg<EG>(sD + (f * TY + row) * TX + tcol, o[f]);
+          for (int f = 0; f < NF; ++f) storeg<EG>((kUnSmem ? sUn : sD) + (f * TY + row) * TX + tcol, o[f]);
         } else {
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
@@ -1187,11 +1239,19 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
 
     // this tile's warp reductions into the warp's running slots
     if (ctl.mode == 0) {
+      if constexpr (sizeof(real) == 4) {
+        // the speed maxima are +0 .. +inf (fmax drops NaNs), whose bit patterns order as unsigned integers:
+        // one warp reduction instruction each
+        amx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(amx)));
+        amy = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(amy)));
+        smx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smx)));
+      } else {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        amx = fmax(amx, __shfl_xor_sync(0xffffffffu, amx, o));
-        amy = fmax(amy, __shfl_xor_sync(0xffffffffu, amy, o));
-        smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
+        for (int o = 16; o > 0; o >>= 1) {
+          amx = fmax(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+          amy = fmax(amy, __shfl_xor_sync(0xffffffffu, amy, o));
+          smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
+        }
       }
       const bool want_tot = g.totals != nullptr;
       if (want_tot) {
@@ -1228,21 +1288,35 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
         }
       }
     }
-    // the outputs in sD (generic-proxy writes) become visible to the tensor store, and the next copy
-    // overwrites the box: everyone is done reading it (generic proxy) before TMA writes
-    if (tile_store) fence_proxy_async_smem();
-    __syncthreads();
-    fence_proxy_async_smem();
-    if (tile_store && tid == 0) {
-      tma_store_3d(g.tmap_out, sD, x0 + GX, y0 + GY, 0);
-      bulk_commit();
-    }
-    if (kUnSmem && s_abort) {  // the U^n copy did not complete: wait (with a limit) for the copies in flight
-      if (tid == 0) {
-        mbar_wait_limit(&bar[2], un_parity ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
-        if (wn < nwork) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
+    if constexpr (kUnSmem) {  // no barrier: the tensor store is issued after the next tile's primitives
+      prev_store = tile_store;
+      prev_map = g.tmap_out;
+      prev_x = x0 + GX;
+      prev_y = y0 + GY;
+    } else {
+      // the outputs in sD (generic-proxy writes) become visible to the tensor store: each writer fences,
+      // then the barrier. The next copy overwrites the box that everyone has read: the barrier orders those
+      // reads before the issuing thread's fence, which orders them before its copies.
+      if (tile_store) fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) fence_proxy_async_smem();
+      if (tile_store && tid == 0) {
+        tma_store_3d(g.tmap_out, sD, x0 + GX, y0 + GY, 0);
+        bulk_commit();
       }
-      break;
+    }
+  }
+  if constexpr (kUnSmem) {  // the last tile's tensor store, or (after a failed copy) the copies in flight
+    if (prev_store) fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (s_abort) {
+        mbar_wait_limit(&bar[2], un_parity ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+      } else if (prev_store) {
+        fence_proxy_async_smem();
+        tma_store_3d(prev_map, sUn, prev_x, prev_y, 0);
+        bulk_commit();
+      }
     }
   }
   if (tid == 0) bulk_wait_all();  // the tensor stores are complete before the CTA exits
