@@ -263,7 +263,8 @@ int hydro_batch_step(hydro_ctx* const* members, void* const* U, int nmembers, in
 
 /* Number of tile variants and the current one; select a variant (0 .. n-1) for this context
  * (HYDRO_EINVAL for no such variant or one that does not fit on the device). A new context starts with
- * variant 2 (60 x 30 cells, 640 threads) for FP32 grids of at least one such tile per SM, else 1. */
+ * variant 2 (60 x 30 cells, 640 threads) for component-wise FP32 grids of at least one such tile per SM,
+ * else 1. */
 int hydro_tile_variants(hydro_ctx* ctx, int* n, int* current);
 int hydro_set_tile_variant(hydro_ctx* ctx, int variant);
 /* Describe a variant: tile width and height in cells, threads per CTA, shared memory bytes. */

@@ -711,11 +711,15 @@ int hydro_init(const hydro_config* cfg, void* stream, hydro_ctx** out) {
   for (int b = 0; b < hydro_ctx::NBANDS; ++b)
     if (cudaEventCreateWithFlags(&c->band_ev[b], cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
   if (cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess) return bail(HYDRO_ECUDA);
-  // default tile shape: FP32 grids with at least one 60 x 30 tile per SM take that variant (one CTA of
-  // 640 threads per SM: 2.53 against 3.00 ms per 8192^2 stage, 0.325 against 0.339 ms per 1024 x 2048
-  // step); others 60 x 15 with 320 threads. hydro_autotune measures instead of guessing.
+  // default tile shape: component-wise FP32 grids with at least one 60 x 30 tile per SM take that variant
+  // (one CTA of 640 threads per SM: 2.53 against 3.00 ms per 8192^2 stage, 0.325 against 0.339 ms per
+  // 1024 x 2048 step); others 60 x 15 with 320 threads (the characteristic scheme's stage, whose hydro
+  // divergence comes from its own kernel, measured 2 % faster there). hydro_autotune measures instead.
   const long long tiles30 = (long long)c->tiles_x * ((cfg->ny + 29) / 30);
-  c->variant = (cfg->dtype == HYDRO_F32 && stage_ctas_per_sm<float>(2, c->nf) >= 1 && tiles30 >= c->num_sms) ? 2 : 1;
+  c->variant = (cfg->dtype == HYDRO_F32 && cfg->scheme == HYDRO_SCHEME_COMPONENT &&
+                stage_ctas_per_sm<float>(2, c->nf) >= 1 && tiles30 >= c->num_sms)
+                   ? 2
+                   : 1;
   if (upload(c) != HYDRO_OK) return bail(HYDRO_ECUDA);
   *out = c;
   return HYDRO_OK;
