@@ -354,6 +354,8 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
     p.tmap_out = maps + TMAP_INTERIOR + r.out;
     p.ux0 = r.x0 >= 0 ? bufp<real>(c, r.x0) : nullptr;
     p.ux1 = r.x1 >= 0 ? bufp<real>(c, r.x1) : nullptr;
+    p.tmap_ux0 = r.x0 >= 0 ? maps + TMAP_INTERIOR + r.x0 : nullptr;
+    p.tmap_ux1 = r.x1 >= 0 ? maps + TMAP_INTERIOR + r.x1 : nullptr;
     p.alpha_in = s->alpha[k];
     p.alpha_out = s->alpha[(k + 1) % ns];
     p.alpha_zero = s->alpha[(k + 2) % ns];

@@ -47,6 +47,8 @@ struct GridParams {
   int tmap_ty;           // the tile height the tensor maps' boxes were built for
   const real* ux0;   // further stage states the blend adds (five-stage scheme), else null
   const real* ux1;
+  const void* tmap_ux0;  // their tile-interior tensor maps (L2 prefetches), else null
+  const void* tmap_ux1;
   real* out;         // stage output (padded) or L (mode RHS)
   long long fstride; // elements between field planes
   int nx, ny, pitch;

@@ -708,6 +708,15 @@ struct Tile {
   static_assert(TX % EG == 0, "tile rows are whole cell groups");
 };
 
+// The five-stage scheme's further stage states that a tile's blend adds (its own cells): into L2, when the
+// interior maps' boxes are the launch's tiles.
+template <typename real>
+__device__ __forceinline__ void prefetch_stage_terms(const GridParams<real>* m, int x, int y, int TY) {
+  if (m->tmap_ty != TY) return;
+  if (m->tmap_ux0) tma_prefetch_l2_3d(m->tmap_ux0, x, y, 0);
+  if (m->tmap_ux1) tma_prefetch_l2_3d(m->tmap_ux1, x, y, 0);
+}
+
 // Issue the TMA copy of one tile's halo box (one thread): arm the barrier with the box's bytes, then one
 // tensor copy of the (68, TY + 6, NF) box at padded column tx * 60, row ty * TY. With prefetch_un, the
 // tile's own cells of U^n (a (60, TY, NF) box) are prefetched into L2 for the tile's per-cell phase. m may
@@ -721,6 +730,7 @@ __device__ __forceinline__ void issue_box(const GridParams<real>* m, int tile, i
   mbar_arrive_expect_tx(bar, bytes);
   tma_load_3d(box, map, tx * TILE_X, ty * TY, 0, bar);
   if (prefetch_un) tma_prefetch_l2_3d(m->tmap_un, tx * TILE_X + GX, ty * TY + GY, 0);  // the tile's own cells
+  prefetch_stage_terms(m, tx * TILE_X + GX, ty * TY + GY, TY);
 }
 
 // ------------------------------------------------------------------------------ the stage kernel
