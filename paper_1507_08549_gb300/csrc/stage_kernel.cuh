@@ -768,6 +768,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
   // instances' instruction footprint costs less than the address arithmetic they save: 2.87 -> 2.78 ms per
   // 8192^2 launch of the 640-thread variant; with two CTAs per SM the runtime-stride line measured faster)
   constexpr bool kCts = NT >= 640;
+  // the 60x30 variant's level-set warps, whose lines are shorter than the hydro ones, also form the
+  // Hamiltonian of their y-pass cells (after a barrier among themselves between their two passes); the
+  // per-cell phase then reads it instead of the four one-sided derivatives and u, v
+  constexpr bool kPhiH = kUnSmem && NF == 5;
   // the tensor copies write 128-byte aligned buffers: a launch that finds its dynamic shared memory
   // elsewhere reports it and returns before any copy (the same address for every thread)
   if ((smem_u32(smem_raw) & 127u) != 0u) {
@@ -1028,8 +1032,19 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
             if constexpr (kCts) {
               if (xp)
                 phi_line_tri<K, 1, 1>(sU + (4 * H + brow) * W + bcol, 1, rd, om, om + TY * TX, 1);
-              else
+              else {
                 phi_line_tri<K, W, TX>(sU + (4 * H + brow) * W + bcol, W, rd, om, om + TY * TX, TX);
+                if constexpr (kPhiH) {
+                  const real sf = g.flame_speed;
+#pragma unroll
+                  for (int k = 0; k < K; ++k) {
+                    const int idx = (trow + k) * TX + tcol;
+                    sX[idx] = Ar<real>::hamiltonian(su[(trow + k) * W + tcol + 4], sv[(trow + k + 3) * TX + tcol], sf,
+                                                    sX[idx], sX[TY * TX + idx], sX[2 * TY * TX + idx],
+                                                    sX[3 * TY * TX + idx]);
+                  }
+                }
+              }
             } else {
               phi_line_tri<K>(sU + (4 * H + brow) * W + bcol, S, rd, om, om + TY * TX, DS);
             }
@@ -1051,7 +1066,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           case 1: named_barrier_sync<2>(TL::XI_PER_C); break;
           case 2: named_barrier_sync<3>(TL::XI_PER_C); break;
           case 3: named_barrier_sync<4>(TL::XI_PER_C); break;
-          default: break;
+          default:
+            if constexpr (kPhiH) named_barrier_sync<5>(TL::XI_PER_C);  // the level set's two passes
+            break;
         }
       } else {
         __syncthreads();
@@ -1110,7 +1127,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
           const bool sources = rz || grav != real(0);
           if constexpr (kUnSmem) {  // pipelined: the next tile's primitives overwrite su, sv, sp meanwhile,
                                     // so the cell's own come from its box values (the same operations)
-            if (sources || NF == 5) {
+            if (sources || (NF == 5 && !kPhiH)) {
 #pragma unroll
               for (int e = 0; e < EG; ++e) {
                 const int c0 = srow * W + scol + e;
@@ -1158,6 +1175,8 @@ __global__ void __launch_bounds__(NT, (NT <= 320 && sizeof(real) == 4 ? 2 : 1))
               } else {
                 loadg<EG>(sD + (f * TY + row) * TX + tcol, Dv);
               }
+            } else if constexpr (kPhiH) {  // level set: its Hamiltonian, formed in the y pass
+              loadg<EG>(sX + (0 * TY + row) * TX + tcol, Dv);
             } else {  // level set: the local Lax-Friedrichs Hamiltonian from the four one-sided derivatives
               real xm[EG], xq[EG], ym[EG], yq[EG];
               loadg<EG>(sX + (0 * TY + row) * TX + tcol, xm);
