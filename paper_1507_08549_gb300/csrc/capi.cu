@@ -19,6 +19,7 @@
 #include "../../include/hydro.h"
 #include "hydro_internal.cuh"
 #include "adjoint_kernel.cuh"
+#include "char_kernel.cuh"
 
 using namespace hydro;
 
@@ -214,7 +215,7 @@ static int tile_ty(int variant) { return VARIANTS[variant].ty; }
 // Device parameter table of a context: the step's stages (up to 5), the three frozen SSP-RK3 stages
 // (recorded replays and the adjoint), the spatial operator.
 constexpr int P_FROZEN = 5, P_RHS = 8, NPARAMS = 9;
-constexpr int TMAP_INTERIOR = 5, NTMAPS = 10;
+constexpr int TMAP_INTERIOR = 5, TMAP_CHAR = 10, NTMAPS = 15;
 
 // One stage of a step: W = buffer win, output buffer out, and out = a U^n + rx0 B[x0] + rx1 B[x1]
 // + b (W + c dt L(W)) (x0, x1 = -1: no such term).
@@ -295,12 +296,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tile boxes start at column tx * 60 (240 tx bytes in FP32, 480 tx in FP64: 16-byte aligned) and never
 // leave the allocation (pitch and rows cover whole tiles plus the halo).
 template <typename real>
-static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorMap* out, int box_w = BOX_W) {
+static int encode_state_map(hydro_ctx* c, const void* base, int box_h, CUtensorMap* out, int box_w = BOX_W,
+                            int box_z = 0) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (!fn) return HYDRO_ECUDA;
   const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->rows, (cuuint64_t)c->nf};
   const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(real), (cuuint64_t)c->fstride * sizeof(real)};
-  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)c->nf};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)(box_z > 0 ? box_z : c->nf)};
   const cuuint32_t estride[3] = {1, 1, 1};
   const CUresult r =
       fn(out, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -352,6 +354,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
     p.un = A;
     p.out = bufp<real>(c, r.out);
     p.tmap_out = maps + TMAP_INTERIOR + r.out;
+    p.tmap_char = c->char_div ? maps + TMAP_CHAR + r.win : nullptr;
     p.ux0 = r.x0 >= 0 ? bufp<real>(c, r.x0) : nullptr;
     p.ux1 = r.x1 >= 0 ? bufp<real>(c, r.x1) : nullptr;
     p.tmap_ux0 = r.x0 >= 0 ? maps + TMAP_INTERIOR + r.x0 : nullptr;
@@ -387,6 +390,7 @@ static void build_params(hydro_ctx* c, GridParams<real> out[NPARAMS]) {
   r.un = A;
   r.out = B;
   r.tmap_out = maps + TMAP_INTERIOR + 1;
+  r.tmap_char = c->char_div ? maps + TMAP_CHAR : nullptr;
   r.alpha_in = s->frozen_alpha[0];
   r.dt_src = &s->frozen_dt;
   out[P_RHS] = r;
@@ -405,6 +409,11 @@ static int upload_params(hydro_ctx* c) {
   for (int k = 0; k < c->ns; ++k)
     if (encode_state_map<real>(c, c->buf[k], tile_ty(c->variant), &maps[TMAP_INTERIOR + k], TILE_X))
       return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled failed for the tile interiors");
+  // the characteristic kernel's boxes: (CHAR_BOX_W, CBH, 4 hydro fields) at padded column 32 bx, row CY by
+  if (c->char_div)
+    for (int k = 0; k < c->ns; ++k)
+      if (encode_state_map<real>(c, c->buf[k], CharTile<real>::CBH, &maps[TMAP_CHAR + k], CHAR_BOX_W, 4))
+        return fail(c, HYDRO_ECUDA, "cuTensorMapEncodeTiled failed for the characteristic boxes");
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->params, p, sizeof(p), cudaMemcpyHostToDevice));

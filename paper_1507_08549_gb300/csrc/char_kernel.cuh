@@ -14,9 +14,11 @@
 //
 // char_div_kernel writes D = dF/dx + dG/dy of the four hydro components for one stage input into a
 // padded buffer laid out like the states; the stage kernel then takes D from there instead of its own
-// component-wise passes (the level set, sources, RK blend and reductions are unchanged). One CTA of 256
-// threads holds a 32 x 16 (FP32) or 32 x 8 (FP64) tile with a 3-cell halo in shared memory; one thread per
-// face computes the face flux (x faces, then y faces), then one thread per cell differences them.
+// component-wise passes (the level set, sources, RK blend and reductions are unchanged). Persistent CTAs
+// of 256 threads walk 32 x 16 (FP32) or 32 x 8 (FP64) tiles; each tile's box with its 3-cell halo arrives
+// by one TMA tensor copy into one of two staging buffers (the next tile's copy is in flight while the
+// current one is computed); one thread per face computes the face flux (x faces, then y faces), then one
+// thread per cell differences them.
 //
 // FP64: every operation the plain definition writes, in its order, rounded once (products by the 0 and 1
 // entries of R and L included), so D is reproducible bit for bit by a sequential implementation.
@@ -37,6 +39,10 @@ struct CharTile {
   static constexpr int CBH = CY + 6;
 };
 
+// The staging box of a tile: CHAR_BOX_W = 40 padded columns from 32 bx (cells 32 bx - 4 .. 32 bx + 35; a TMA
+// box starts on a 16-byte boundary), CBH rows from CY by, the 4 hydro fields.
+constexpr int CHAR_BOX_W = 40;
+
 template <typename real>
 struct CharSmem {
   static constexpr int CY = CharTile<real>::CY, CBH = CharTile<real>::CBH;
@@ -44,6 +50,17 @@ struct CharSmem {
   real u[CBH][CBW], v[CBH][CBW], p[CBH][CBW];
   real FX[4][CY][CX + 1];   // x-face fluxes, face f left of tile column f
   real FY[4][CY + 1][CX];   // y-face fluxes, face f below tile row f
+};
+
+// dynamic shared memory: CharSmem | staging box 0 | staging box 1 | 2 mbarriers (128-byte aligned parts)
+template <typename real>
+struct CharLayout {
+  static constexpr int CBH = CharTile<real>::CBH;
+  static constexpr unsigned BOX_BYTES = 4u * CBH * CHAR_BOX_W * sizeof(real);
+  static constexpr size_t STAGE_OFF = ((sizeof(CharSmem<real>) + 127) / 128) * 128;
+  static constexpr size_t STAGE_STRIDE = ((BOX_BYTES + 127) / 128) * 128;
+  static constexpr size_t BAR_OFF = STAGE_OFF + 2 * STAGE_STRIDE;
+  static constexpr size_t BYTES = BAR_OFF + 16;
 };
 
 // operation policy: FP64 rounds each written operation once; FP32 lets the compiler fuse
@@ -179,68 +196,120 @@ __device__ __forceinline__ bool char_face(const CharSmem<real>& S, int dir, int 
   return true;
 }
 
-// D = dF/dx + dG/dy of the hydro components of the stage input p->win into p->ext_div (padded layout).
+// D = dF/dx + dG/dy of the hydro components of the stage input p->win into p->ext_div (padded layout), over
+// tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the tiles_x-wide tile grid.
 template <typename real>
-__global__ void __launch_bounds__(CHAR_THREADS) char_div_kernel(const GridParams<real>* __restrict__ pp) {
-  __shared__ CharSmem<real> S;
+__device__ __forceinline__ void char_issue_box(const GridParams<real>& g, int w, int tiles_x, real* dst, uint64_t* bar) {
+  constexpr int CY = CharTile<real>::CY;
+  mbar_arrive_expect_tx(bar, CharLayout<real>::BOX_BYTES);
+  tma_load_3d(dst, g.tmap_char, (w % tiles_x) * CX, (w / tiles_x) * CY, 0, bar);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(CHAR_THREADS) char_div_kernel(const GridParams<real>* __restrict__ pp, int tiles_x,
+                                                               int ntiles) {
+  using L = CharLayout<real>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  CharSmem<real>& S = *reinterpret_cast<CharSmem<real>*>(smem_raw);
+  real* stage = reinterpret_cast<real*>(smem_raw + L::STAGE_OFF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + L::BAR_OFF);
+  __shared__ int s_abort;
   const GridParams<real>& g = *pp;
   const int nx = g.nx, ny = g.ny, pitch = g.pitch;
   const long long fs = g.fstride;
-  const long long rows_alloc = fs / pitch;
   constexpr int CY = CharTile<real>::CY, CBH = CharTile<real>::CBH;
-  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * CY;
+  constexpr int SSTR = static_cast<int>(L::STAGE_STRIDE / sizeof(real));
   const int tid = threadIdx.x;
   const real gm1 = g.gm1;
-  // box cell (r, c) is grid cell (x0 - 3 + c, y0 - 3 + r): padded element (y0 + r) * pitch + (x0 + 1 + c)
-  for (int idx = tid; idx < CBH * CBW; idx += CHAR_THREADS) {
-    const int r = idx / CBW, c = idx - r * CBW;
-    const long long row = y0 + r, col = x0 + 1 + c;
-    const bool in = row < rows_alloc && col < pitch;
-    const long long e = row * pitch + col;
-    real U[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      U[f] = in ? g.win[f * fs + e] : real(0);
-      S.U[f][r][c] = U[f];
-    }
-    real u = real(0), v = real(0), p = real(0);
-    if (in && U[0] != real(0)) Ar<real>::prims(U[0], U[1], U[2], U[3], gm1, u, v, p);
-    S.u[r][c] = u;
-    S.v[r][c] = v;
-    S.p[r][c] = p;
+  // the tensor copies write 128-byte aligned buffers (the same address for every thread)
+  if ((smem_u32(smem_raw) & 127u) != 0u) {
+    if (tid == 0 && static_cast<int>(blockIdx.x) < ntiles) atomicOr(g.err, ERR_LAYOUT);
+    return;
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_abort = 0;
   }
   __syncthreads();
+  if (tid == 0 && static_cast<int>(blockIdx.x) < ntiles) char_issue_box(g, blockIdx.x, tiles_x, stage, &bar[0]);
   const real ax = g.alpha_in[0], ay = g.alpha_in[1];
-  bool bad = false;
-  // x faces: tile row fr, face fc (left of tile column fc); needed for rows < ny and faces <= nx - x0
-  for (int it = tid; it < CY * (CX + 1); it += CHAR_THREADS) {
-    const int fr = it / (CX + 1), fc = it - fr * (CX + 1);
-    real o[4] = {real(0), real(0), real(0), real(0)};
-    if (y0 + fr < ny && x0 + fc <= nx) bad |= !char_face(S, 0, fr + 3, fc + 2, ax, gm1, o);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) S.FX[f][fr][fc] = o[f];
-  }
-  // y faces: face fr below tile row fr, tile column fc
-  for (int it = tid; it < (CY + 1) * CX; it += CHAR_THREADS) {
-    const int fr = it / CX, fc = it - fr * CX;
-    real o[4] = {real(0), real(0), real(0), real(0)};
-    if (x0 + fc < nx && y0 + fr <= ny) bad |= !char_face(S, 1, fr + 2, fc + 3, ay, gm1, o);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) S.FY[f][fr][fc] = o[f];
-  }
-  if (bad) atomicOr(g.err, ERR_NONPHYSICAL);
-  __syncthreads();
-  for (int cell = tid; cell < CY * CX; cell += CHAR_THREADS) {
-    const int tr = cell / CX, tc = cell - tr * CX;
-    const int i = x0 + tc, j = y0 + tr;
-    if (i < nx && j < ny) {
-      const long long e = static_cast<long long>(j + GY) * pitch + i + GX;
-      real* D = const_cast<real*>(g.ext_div);
+  unsigned parity[2] = {0u, 0u};
+  int it = 0;
+  for (int w = blockIdx.x; w < ntiles; w += gridDim.x, ++it) {
+    const int b = it & 1;
+    const real* box = stage + b * SSTR;
+    // the next tile's box into the other buffer, whose reads (the previous tile's primitives) ended at a
+    // barrier: the issuing thread's proxy fence orders them before the copy
+    const int wn = w + gridDim.x;
+    if (tid == 0 && wn < ntiles) {
+      fence_proxy_async_smem();
+      char_issue_box(g, wn, tiles_x, stage + (b ^ 1) * SSTR, &bar[b ^ 1]);
+    }
+    const int x0 = (w % tiles_x) * CX, y0 = (w / tiles_x) * CY;
+    if (!mbar_wait_bounded(&bar[b], parity[b])) {
+      atomicOr(g.err, ERR_TIMEOUT);
+      s_abort = 1;
+    }
+    parity[b] ^= 1u;
+    // box cell (r, c) is grid cell (x0 - 3 + c, y0 - 3 + r): staging column c + 1 (outside the allocation
+    // the copy reads zeros, and such points get no primitives)
+    for (int idx = tid; idx < CBH * CBW; idx += CHAR_THREADS) {
+      const int r = idx / CBW, c = idx - r * CBW;
+      real U[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const real dxf = Ar<real>::divided(S.FX[f][tr][tc + 1], S.FX[f][tr][tc], g.rdx, g.dx);
-        const real dyf = Ar<real>::divided(S.FY[f][tr + 1][tc], S.FY[f][tr][tc], g.rdy, g.dy);
-        D[f * fs + e] = Ar<real>::sum(dxf, dyf);
+        U[f] = box[(f * CBH + r) * CHAR_BOX_W + c + 1];
+        S.U[f][r][c] = U[f];
+      }
+      real u = real(0), v = real(0), p = real(0);
+      if (U[0] != real(0)) Ar<real>::prims(U[0], U[1], U[2], U[3], gm1, u, v, p);
+      S.u[r][c] = u;
+      S.v[r][c] = v;
+      S.p[r][c] = p;
+    }
+    __syncthreads();
+    if (s_abort) {
+      // a copy did not complete: wait (with a limit) for the copies in flight -- this box and the next --
+      // before the CTA leaves
+      if (tid == 0) {
+        mbar_wait_limit(&bar[b], parity[b] ^ 1u, TILE_WAIT_POLLS, TILE_WAIT_NS);
+        if (wn < ntiles) mbar_wait_limit(&bar[b ^ 1], parity[b ^ 1], TILE_WAIT_POLLS, TILE_WAIT_NS);
+      }
+      break;
+    }
+    bool bad = false;
+    // x faces: tile row fr, face fc (left of tile column fc); needed for rows < ny and faces <= nx - x0
+    for (int it2 = tid; it2 < CY * (CX + 1); it2 += CHAR_THREADS) {
+      const int fr = it2 / (CX + 1), fc = it2 - fr * (CX + 1);
+      real o[4] = {real(0), real(0), real(0), real(0)};
+      if (y0 + fr < ny && x0 + fc <= nx) bad |= !char_face(S, 0, fr + 3, fc + 2, ax, gm1, o);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.FX[f][fr][fc] = o[f];
+    }
+    // y faces: face fr below tile row fr, tile column fc
+    for (int it2 = tid; it2 < (CY + 1) * CX; it2 += CHAR_THREADS) {
+      const int fr = it2 / CX, fc = it2 - fr * CX;
+      real o[4] = {real(0), real(0), real(0), real(0)};
+      if (x0 + fc < nx && y0 + fr <= ny) bad |= !char_face(S, 1, fr + 2, fc + 3, ay, gm1, o);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.FY[f][fr][fc] = o[f];
+    }
+    if (bad) atomicOr(g.err, ERR_NONPHYSICAL);
+    __syncthreads();
+    // the differences read only FX and FY, which the next tile writes after its primitives' barrier
+    for (int cell = tid; cell < CY * CX; cell += CHAR_THREADS) {
+      const int tr = cell / CX, tc = cell - tr * CX;
+      const int i = x0 + tc, j = y0 + tr;
+      if (i < nx && j < ny) {
+        const long long e = static_cast<long long>(j + GY) * pitch + i + GX;
+        real* D = const_cast<real*>(g.ext_div);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const real dxf = Ar<real>::divided(S.FX[f][tr][tc + 1], S.FX[f][tr][tc], g.rdx, g.dx);
+          const real dyf = Ar<real>::divided(S.FY[f][tr + 1][tc], S.FY[f][tr][tc], g.rdy, g.dy);
+          D[f * fs + e] = Ar<real>::sum(dxf, dyf);
+        }
       }
     }
   }

@@ -45,6 +45,7 @@ struct GridParams {
   const void* tmap_un;   // device CUtensorMap of un's tile interiors (box 60 x TY x nfields)
   const void* tmap_out;  // device CUtensorMap of out's tile interiors (the tensor store of a whole tile)
   int tmap_ty;           // the tile height the tensor maps' boxes were built for
+  const void* tmap_char; // device CUtensorMap of win with the characteristic kernel's box, else null
   const real* ux0;   // further stage states the blend adds (five-stage scheme), else null
   const real* ux1;
   const void* tmap_ux0;  // their tile-interior tensor maps (L2 prefetches), else null

@@ -128,8 +128,24 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
 template <>
 cudaError_t launch_char_div<HYDRO_REAL>(const GridParams<HYDRO_REAL>* p_dev, int nx, int ny, cudaStream_t s) {
   constexpr int CY = CharTile<HYDRO_REAL>::CY;
-  const dim3 grid((nx + CX - 1) / CX, (ny + CY - 1) / CY);
-  char_div_kernel<HYDRO_REAL><<<grid, CHAR_THREADS, 0, s>>>(p_dev);
+  constexpr int SMEM = static_cast<int>(CharLayout<HYDRO_REAL>::BYTES);
+  // persistent CTAs: as many as are resident at once (the dynamic shared memory and the registers decide)
+  static const int resident = []() -> int {
+    int d = 0, n = 0, per = 0;
+    if (cudaFuncSetAttribute(char_div_kernel<HYDRO_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
+            cudaSuccess ||
+        cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, char_div_kernel<HYDRO_REAL>, CHAR_THREADS, SMEM) !=
+            cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    return n * per;
+  }();
+  if (resident < 1) return cudaErrorInvalidConfiguration;
+  const int tiles_x = (nx + CX - 1) / CX, ntiles = tiles_x * ((ny + CY - 1) / CY);
+  const int grid = ntiles < resident ? ntiles : resident;
+  char_div_kernel<HYDRO_REAL><<<grid, CHAR_THREADS, SMEM, s>>>(p_dev, tiles_x, ntiles);
   return cudaGetLastError();
 }
 
