@@ -8,25 +8,27 @@
 namespace hydro {
 
 // Grid-stride over the cells (a few blocks per SM); one block-level reduction and one atomic per slot
-// and block at the end, so the global maxima see a few thousand atomics, not one per warp.
+// and block at the end, so the global maxima see a few thousand atomics, not one per warp. Block `block`
+// of `nblocks` takes cells block * 256 + threadIdx.x, step nblocks * 256.
 template <typename real, int NF>
-__global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, GridParams<real> g,
-                                                   real* alpha_slot, real* smax_slot, double* t_acc, double t0) {
+__device__ __forceinline__ void pack_range(const real* __restrict__ U, const GridParams<real>& g, real* out,
+                                           real* alpha_slot, real* smax_slot, double* t_acc, double t0, int block,
+                                           int nblocks) {
   __shared__ real sred[8][3];
-  if (blockIdx.x == 0 && threadIdx.x == 0 && t_acc) *t_acc = t0;
+  if (block == 0 && threadIdx.x == 0 && t_acc) *t_acc = t0;
   real amx = real(0), amy = real(0), smx = real(0);
   const long long n = static_cast<long long>(g.nx) * g.ny;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+  const long long stride = static_cast<long long>(nblocks) * blockDim.x;
+  for (long long k = static_cast<long long>(block) * blockDim.x + threadIdx.x; k < n; k += stride) {
     const int j = static_cast<int>(k / g.nx), i = static_cast<int>(k - static_cast<long long>(j) * g.nx);
     real val[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) val[f] = U[f * n + k];
     const long long off = static_cast<long long>(j + GY) * g.pitch + i + GX;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) g.out[f * g.fstride + off] = val[f];
+    for (int f = 0; f < NF; ++f) out[f * g.fstride + off] = val[f];
     if (i < 3 || i >= g.nx - 3 || j < 3 || j >= g.ny - 3)
-      write_ghost_images<real, NF>(g.out, g.fstride, g.pitch, g.nx, g.ny, g.bc, i, j, val);
+      write_ghost_images<real, NF>(out, g.fstride, g.pitch, g.nx, g.ny, g.bc, i, j, val);
     real p, sx, sy, sm;
     Ar<real>::speeds(val[0], val[1], val[2], val[3], g.gamma, g.gm1, p, sx, sy, sm);
     bool ok = val[0] > real(0) && p > real(0) && RT<real>::finite(val[3]) && RT<real>::finite(val[1]) &&
@@ -56,6 +58,41 @@ __global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, G
     if (threadIdx.x == 0 && alpha_slot) RT<real>::atomic_max(&alpha_slot[0], m);
     if (threadIdx.x == 1 && alpha_slot) RT<real>::atomic_max(&alpha_slot[1], m);
     if (threadIdx.x == 2 && smax_slot) RT<real>::atomic_max(smax_slot, m);
+  }
+}
+
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) pack_kernel(const real* __restrict__ U, GridParams<real> g,
+                                                   real* alpha_slot, real* smax_slot, double* t_acc, double t0) {
+  pack_range<real, NF>(U, g, g.out, alpha_slot, smax_slot, t_acc, t0, blockIdx.x, gridDim.x);
+}
+
+// Batched ensembles: member blockIdx.y, with its first-stage parameters P[m], packs its caller state U[m]
+// into its buffer A (the stage's U^n) and reduces into its own slots; one launch for all members.
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) batch_pack_kernel(const GridParams<real>* __restrict__ P,
+                                                         const real* const* __restrict__ U,
+                                                         const double* __restrict__ t0) {
+  const int m = blockIdx.y;
+  const GridParams<real>& g = P[m];
+  pack_range<real, NF>(U[m], g, const_cast<real*>(g.un), const_cast<real*>(g.alpha_in), g.smax, g.t_acc, t0[m],
+                       blockIdx.x, gridDim.x);
+}
+
+// ... and copies member blockIdx.y's buffer A back into its caller state U[m] (interior cells).
+template <typename real, int NF>
+__global__ void __launch_bounds__(256) batch_unpack_kernel(const GridParams<real>* __restrict__ P,
+                                                           real* const* __restrict__ U) {
+  const int m = blockIdx.y;
+  const GridParams<real>& g = P[m];
+  const long long n = static_cast<long long>(g.nx) * g.ny;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  real* dst = U[m];
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const int j = static_cast<int>(k / g.nx), i = static_cast<int>(k - static_cast<long long>(j) * g.nx);
+    const long long off = static_cast<long long>(j + GY) * g.pitch + i + GX;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dst[f * n + k] = g.un[f * g.fstride + off];
   }
 }
 

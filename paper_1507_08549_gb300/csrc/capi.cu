@@ -141,6 +141,11 @@ struct hydro_ctx {
   void* plan_work = nullptr;    // device WorkItem[nwork]
   int plan_nwork = 0;
   cudaGraphExec_t plan_graph = nullptr;
+  // a batch call's per-member arguments (caller state and scratch pointers, start times) and the gathered
+  // scratch records, on the device and in pinned host memory, for up to bio_cap members
+  void* bio_dev = nullptr;
+  void* bio_host = nullptr;
+  int bio_cap = 0;
   // batch plan shape chosen by hydro_batch_autotune (on the first member): persistent CTAs in
   // batch_waves waves of (CTAs per SM x SMs), work-list layout (BatchLayout)
   int batch_waves = 1, batch_layout = 0;
@@ -758,6 +763,8 @@ void hydro_destroy(hydro_ctx* c) {
   cudaFree(c->alpha_log);
   cudaFree(c->plan_params);
   cudaFree(c->plan_work);
+  cudaFree(c->bio_dev);
+  cudaFreeHost(c->bio_host);
   cudaFree(c->adj_nu[0]);
   cudaFree(c->adj_nu[1]);
   cudaFree(c->adj_mu);
@@ -1144,19 +1151,38 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
     c->plan_waves = c->batch_waves;
     c->plan_layout = c->batch_layout;
   }
-  for (int k = 0; k < n; ++k) {
-    hydro_ctx* mk = m[k];
-    Scratch<real>* s = scr<real>(mk);
-    CK(cudaMemsetAsync(s, 0, offsetof(Scratch<real>, log_count), c->stream));
-    GridParams<real> p[NPARAMS];
-    build_params<real>(mk, p);
-    p[0].out = bufp<real>(mk, 0);
-    CK(launch_pack<real>(static_cast<const real*>(U[k]), p[0], mk->nf, s->alpha[0], &s->smax, &s->t_acc,
-                         t ? t[k] : 0.0, c->stream));
-    c->launches++;
-  }
   const int grid = c->plan_grid;
   const GridParams<real>* P = static_cast<const GridParams<real>*>(c->plan_params);
+  // the members' arguments in one upload; their scratch records zeroed and their states packed (buffer A,
+  // with the first stage's reductions) by one launch each for all members
+  constexpr size_t SB = sizeof(Scratch<real>);  // one record per member, back to back
+  const size_t args_bytes = 3 * sizeof(void*) * (size_t)n;
+  if (c->bio_cap < n) {
+    cudaFree(c->bio_dev);
+    cudaFreeHost(c->bio_host);
+    c->bio_dev = c->bio_host = nullptr;
+    c->bio_cap = 0;
+    CK(cudaMalloc(&c->bio_dev, args_bytes + SB * n));
+    CK(cudaMallocHost(&c->bio_host, args_bytes + SB * n));
+    c->bio_cap = n;
+  }
+  CK(cudaStreamSynchronize(c->stream));  // the pinned arguments of an earlier call are no longer in use
+  void** hptr = static_cast<void**>(c->bio_host);
+  long long max_cells = 0;
+  for (int k = 0; k < n; ++k) {
+    hptr[k] = U[k];
+    hptr[n + k] = m[k]->scratch;
+    reinterpret_cast<double*>(hptr + 2 * n)[k] = t ? t[k] : 0.0;
+    max_cells = std::max(max_cells, (long long)m[k]->cfg.nx * m[k]->cfg.ny);
+  }
+  void** dptr = static_cast<void**>(c->bio_dev);
+  unsigned char* gather_dev = static_cast<unsigned char*>(c->bio_dev) + args_bytes;
+  const unsigned char* gather_host = static_cast<const unsigned char*>(c->bio_host) + args_bytes;
+  CK(cudaMemcpyAsync(dptr, hptr, args_bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_batch_scratch(dptr + n, n, (int)offsetof(Scratch<real>, log_count), nullptr, c->stream));
+  CK(launch_batch_pack<real>(P, reinterpret_cast<const real* const*>(dptr), reinterpret_cast<const double*>(dptr + 2 * n),
+                             n, c->nf, max_cells, c->stream));
+  c->launches += 2;
   const WorkItem* W = static_cast<const WorkItem*>(c->plan_work);
   auto launch3 = [&](cudaStream_t s) -> int {
     for (int k = 0; k < c->ns; ++k) {
@@ -1188,19 +1214,17 @@ static int batch_impl(hydro_ctx* const* m, void* const* U, int n, int nsteps, do
   }
   if (ms_graph) CK(cudaEventRecord(g1, c->stream));
   int worst = HYDRO_OK;
-  for (int k = 0; k < n; ++k) {
-    hydro_ctx* mk = m[k];
-    // members' unpack and status copies go on the batch stream
-    cudaStream_t keep = mk->stream;
-    mk->stream = c->stream;
-    int rc = writeback ? unpack_state<real>(mk, static_cast<real*>(U[k]), 0) : HYDRO_OK;
-    if (!rc) {
-      CK(cudaMemcpyAsync(mk->host_scratch, mk->scratch, sizeof(Scratch<real>), cudaMemcpyDeviceToHost, c->stream));
-    }
-    mk->stream = keep;
-    if (rc) return fail(c, rc, mk->err);
+  // every member's state back into its caller buffer, and every scratch record into one host copy
+  if (writeback) {
+    CK(launch_batch_unpack<real>(P, reinterpret_cast<real* const*>(dptr), n, c->nf, max_cells, c->stream));
+    c->launches++;
   }
+  CK(launch_batch_scratch(dptr + n, n, (int)SB, gather_dev, c->stream));
+  c->launches++;
+  CK(cudaMemcpyAsync(const_cast<unsigned char*>(gather_host), gather_dev, SB * n, cudaMemcpyDeviceToHost, c->stream));
   int rc = wait_stream(c);
+  if (!rc)
+    for (int k = 0; k < n; ++k) std::memcpy(m[k]->host_scratch, gather_host + SB * k, sizeof(Scratch<real>));
   if (ms_graph) {
     float ms = 0.f;
     if (!rc) cudaEventElapsedTime(&ms, g0, g1);

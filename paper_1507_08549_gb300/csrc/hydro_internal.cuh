@@ -115,6 +115,16 @@ int stage_ctas_per_sm(int variant, int nfields);
 template <typename real>
 cudaError_t launch_pack(const real* U, const GridParams<real>& g, int nfields, real* alpha_slot, real* smax_slot,
                         double* t_acc, double t0, cudaStream_t s);
+// Batched ensembles, one launch each over n members: pack every caller state U[m] with its first-stage
+// parameters P[m] (into buffer A, reductions into its slots, *t_acc = t0[m]); unpack buffer A into U[m];
+// zero (dst == null) or gather into dst the first `bytes` of every member's scratch record.
+template <typename real>
+cudaError_t launch_batch_pack(const GridParams<real>* P, const real* const* U, const double* t0, int n, int nfields,
+                              long long max_cells, cudaStream_t s);
+template <typename real>
+cudaError_t launch_batch_unpack(const GridParams<real>* P, real* const* U, int n, int nfields, long long max_cells,
+                                cudaStream_t s);
+cudaError_t launch_batch_scratch(void* const* scratch, int n, int bytes, unsigned char* dst, cudaStream_t s);
 // Write frozen dt and stage alphas into device slots (frozen runs, adjoint).
 template <typename real>
 cudaError_t launch_set_frozen(double* dt_slot, double dt, real* alpha_slots, const double* alpha6, cudaStream_t s);

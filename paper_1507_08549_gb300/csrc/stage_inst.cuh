@@ -125,6 +125,58 @@ cudaError_t launch_totals<HYDRO_REAL>(const HYDRO_REAL* U, int nx, int ny, int n
   return cudaGetLastError();
 }
 
+namespace {
+// blocks per member of the batched pack and unpack: enough for the largest member, about 8 per SM in all
+inline int batch_blocks(int n, long long max_cells) {
+  int dev = 0, sms = 132;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (max_cells + 255) / 256, cap = (8LL * sms + n - 1) / n;
+  return static_cast<int>(want < cap ? (want > 0 ? want : 1) : (cap > 0 ? cap : 1));
+}
+}  // namespace
+
+template <>
+cudaError_t launch_batch_pack<HYDRO_REAL>(const GridParams<HYDRO_REAL>* P, const HYDRO_REAL* const* U,
+                                          const double* t0, int n, int nfields, long long max_cells, cudaStream_t s) {
+  const dim3 grid(batch_blocks(n, max_cells), n);
+  if (nfields == 5)
+    batch_pack_kernel<HYDRO_REAL, 5><<<grid, 256, 0, s>>>(P, U, t0);
+  else
+    batch_pack_kernel<HYDRO_REAL, 4><<<grid, 256, 0, s>>>(P, U, t0);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_batch_unpack<HYDRO_REAL>(const GridParams<HYDRO_REAL>* P, HYDRO_REAL* const* U, int n, int nfields,
+                                            long long max_cells, cudaStream_t s) {
+  const dim3 grid(batch_blocks(n, max_cells), n);
+  if (nfields == 5)
+    batch_unpack_kernel<HYDRO_REAL, 5><<<grid, 256, 0, s>>>(P, U);
+  else
+    batch_unpack_kernel<HYDRO_REAL, 4><<<grid, 256, 0, s>>>(P, U);
+  return cudaGetLastError();
+}
+
+#if HYDRO_REAL_IS_FLOAT  // precision-independent: in one translation unit only
+// Byte-wise copies between the members' scratch records (blockIdx.x = member) and one contiguous array:
+// zero the first `bytes` of each (dst == null), or gather `bytes` of each into dst[m * bytes].
+__global__ void __launch_bounds__(128) batch_scratch_kernel(void* const* __restrict__ scratch, int bytes,
+                                                            unsigned char* __restrict__ dst) {
+  unsigned char* s = static_cast<unsigned char*>(scratch[blockIdx.x]);
+  for (int i = threadIdx.x; i < bytes; i += blockDim.x) {
+    if (dst)
+      dst[static_cast<long long>(blockIdx.x) * bytes + i] = s[i];
+    else
+      s[i] = 0;
+  }
+}
+
+cudaError_t launch_batch_scratch(void* const* scratch, int n, int bytes, unsigned char* dst, cudaStream_t s) {
+  batch_scratch_kernel<<<n, 128, 0, s>>>(scratch, bytes, dst);
+  return cudaGetLastError();
+}
+#endif
+
 template <>
 cudaError_t launch_char_div<HYDRO_REAL>(const GridParams<HYDRO_REAL>* p_dev, int nx, int ny, cudaStream_t s) {
   constexpr int CY = CharTile<HYDRO_REAL>::CY;

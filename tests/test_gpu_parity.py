@@ -463,6 +463,7 @@ def test_batched_ensemble_ctas_cross_members(record_property):
     walks a contiguous run of several tiles that crosses member boundaries (slot flush, parameter
     reload): 44 members drawn from {128, 256}^2 plus one 512^2 member, 6 steps, every member against
     the oracle -- FP64 bit for bit, FP32 at the shock bar."""
+    import torch
     hydro = _hydro()
     members = wl.quadrant_ensemble(44, seed=20150731, sizes=(128, 256), nsteps=6)
     members += [p.with_(name="quadrant_big_" + p.name) for p in wl.quadrant_ensemble(1, seed=5, sizes=(512,), nsteps=6)]
@@ -487,6 +488,16 @@ def test_batched_ensemble_ctas_cross_members(record_property):
                 assert abs(tm - t_ref) <= 1e-5 * t_ref
         if dt == "f32":
             record_property("err:fp32_rel_l1_ensemble45_worst", worst)
+            # the same batch in the 60 x 30 variant (one CTA per SM, the per-cell phase of each tile beside
+            # the next tile's primitives, member changes inside each CTA's run): the same bits
+            h2 = [hydro.Hydro(p, dtype=dt) for p in members]
+            U2 = [h.state(p.U0) for h, p in zip(h2, members)]
+            h2[0].set_tile_variant(2)  # a batch runs in its first member's variant
+            t2 = hydro.hydro_batch_step(h2, U2, nsteps)
+            for p, a, b, ta, tb in zip(members, Us, U2, t, t2):
+                assert torch.equal(a, b) and ta == tb, p.name
+            for h in h2:
+                h.close()
         for h in hs:
             h.close()
 
