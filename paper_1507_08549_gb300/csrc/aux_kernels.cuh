@@ -96,6 +96,26 @@ __global__ void __launch_bounds__(256) batch_unpack_kernel(const GridParams<real
   }
 }
 
+// Copy the interior of a padded state to an unpadded one (to_padded = false) or back, every field in one
+// launch: element k of the unpadded [nf][ny][nx] array is cell (k mod nx, (k / nx) mod ny) of field
+// k / (nx ny).
+template <typename real>
+__global__ void __launch_bounds__(256) copy_state_kernel(real* __restrict__ dst, const real* __restrict__ src, int nx,
+                                                         int ny, int nf, int pitch, long long fstride, bool to_padded) {
+  const long long plane = static_cast<long long>(nx) * ny, n = plane * nf;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const int f = static_cast<int>(k / plane);
+    const long long r = k - f * plane;
+    const int j = static_cast<int>(r / nx), i = static_cast<int>(r - static_cast<long long>(j) * nx);
+    const long long e = f * fstride + static_cast<long long>(j + GY) * pitch + i + GX;
+    if (to_padded)
+      dst[e] = src[k];
+    else
+      dst[k] = src[e];
+  }
+}
+
 template <typename real>
 __global__ void set_frozen_kernel(double* dt_slot, double dt, real* alpha_slots, double a0, double a1, double a2,
                                   double a3, double a4, double a5) {

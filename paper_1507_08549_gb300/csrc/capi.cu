@@ -538,13 +538,8 @@ static int pack_state(hydro_ctx* c, const real* U, double t0) {
 
 template <typename real>
 static int unpack_state(hydro_ctx* c, real* U, int k) {
-  const hydro_config& g = c->cfg;
-  for (int f = 0; f < c->nf; ++f) {
-    const real* src = bufp<real>(c, k) + f * c->fstride + (long long)GY * c->pitch + GX;
-    real* dst = U + (size_t)f * g.nx * g.ny;
-    CK(cudaMemcpy2DAsync(dst, sizeof(real) * g.nx, src, sizeof(real) * c->pitch, sizeof(real) * g.nx, g.ny,
-                         cudaMemcpyDeviceToDevice, c->stream));
-  }
+  CK(launch_copy_state<real>(U, bufp<real>(c, k), c->cfg.nx, c->cfg.ny, c->nf, c->pitch, c->fstride, false, c->stream));
+  c->launches++;
   return HYDRO_OK;
 }
 
@@ -1354,21 +1349,15 @@ static int ensure_adjoint_buffers(hydro_ctx* c) {
 // caller-layout <-> padded-interior copies of a full state-shaped array
 template <typename real>
 static int copy_in(hydro_ctx* c, real* padded, const real* U) {
-  const hydro_config& g = c->cfg;
-  for (int f = 0; f < c->nf; ++f)
-    CK(cudaMemcpy2DAsync(padded + f * c->fstride + (long long)GY * c->pitch + GX, sizeof(real) * c->pitch,
-                         U + (size_t)f * g.nx * g.ny, sizeof(real) * g.nx, sizeof(real) * g.nx, g.ny,
-                         cudaMemcpyDeviceToDevice, c->stream));
+  CK(launch_copy_state<real>(padded, U, c->cfg.nx, c->cfg.ny, c->nf, c->pitch, c->fstride, true, c->stream));
+  c->launches++;
   return HYDRO_OK;
 }
 
 template <typename real>
 static int copy_out(hydro_ctx* c, real* U, const real* padded) {
-  const hydro_config& g = c->cfg;
-  for (int f = 0; f < c->nf; ++f)
-    CK(cudaMemcpy2DAsync(U + (size_t)f * g.nx * g.ny, sizeof(real) * g.nx,
-                         padded + f * c->fstride + (long long)GY * c->pitch + GX, sizeof(real) * c->pitch,
-                         sizeof(real) * g.nx, g.ny, cudaMemcpyDeviceToDevice, c->stream));
+  CK(launch_copy_state<real>(U, padded, c->cfg.nx, c->cfg.ny, c->nf, c->pitch, c->fstride, false, c->stream));
+  c->launches++;
   return HYDRO_OK;
 }
 

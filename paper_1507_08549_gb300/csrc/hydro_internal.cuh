@@ -125,6 +125,10 @@ template <typename real>
 cudaError_t launch_batch_unpack(const GridParams<real>* P, real* const* U, int n, int nfields, long long max_cells,
                                 cudaStream_t s);
 cudaError_t launch_batch_scratch(void* const* scratch, int n, int bytes, unsigned char* dst, cudaStream_t s);
+// Copy every field's interior between a padded state and an unpadded [nf][ny][nx] one (one launch).
+template <typename real>
+cudaError_t launch_copy_state(real* dst, const real* src, int nx, int ny, int nf, int pitch, long long fstride,
+                              bool to_padded, cudaStream_t s);
 // Write frozen dt and stage alphas into device slots (frozen runs, adjoint).
 template <typename real>
 cudaError_t launch_set_frozen(double* dt_slot, double dt, real* alpha_slots, const double* alpha6, cudaStream_t s);

@@ -136,6 +136,17 @@ inline int batch_blocks(int n, long long max_cells) {
 }  // namespace
 
 template <>
+cudaError_t launch_copy_state<HYDRO_REAL>(HYDRO_REAL* dst, const HYDRO_REAL* src, int nx, int ny, int nf, int pitch,
+                                          long long fstride, bool to_padded, cudaStream_t s) {
+  int dev = 0, sms = 132;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (static_cast<long long>(nx) * ny * nf + 255) / 256;
+  const int grid = static_cast<int>(want < 8LL * sms ? want : 8LL * sms);
+  copy_state_kernel<HYDRO_REAL><<<grid, 256, 0, s>>>(dst, src, nx, ny, nf, pitch, fstride, to_padded);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_batch_pack<HYDRO_REAL>(const GridParams<HYDRO_REAL>* P, const HYDRO_REAL* const* U,
                                           const double* t0, int n, int nfields, long long max_cells, cudaStream_t s) {
   const dim3 grid(batch_blocks(n, max_cells), n);
