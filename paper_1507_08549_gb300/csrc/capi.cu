@@ -98,6 +98,7 @@ struct hydro_ctx {
   void* adj_nu[2] = {nullptr, nullptr};
   void* adj_mu = nullptr;
   void* adj_hb = nullptr;
+  int adj_in = 0;  // during a reverse sweep: 0 (adj_nu[0]) or 2 (adj_acc), the buffer holding the cotangent
   void* adj_acc = nullptr;
   void* ckpt = nullptr;
   size_t ckpt_cap = 0;
@@ -1362,11 +1363,12 @@ static int copy_out(hydro_ctx* c, real* U, const real* padded) {
 }
 
 template <typename real>
-static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt, const double* alpha) {
-  int rc = ensure_adjoint_buffers(c);
-  if (rc) return rc;
+// One adjoint step on padded cotangents (zero ghost frames): the cotangent of U^{n+1} in nu0, which is
+// then reused as scratch; the result (dJ/dU^n) in acc; nu1 a third buffer for the middle stage.
+static int adjoint_step_bufs(hydro_ctx* c, const real* Un, real* nu0, real* nu1, real* acc, double dt,
+                             const double* alpha) {
   // stage states U^n (A), U^(1) (B), U^(2) (C) with the frozen alphas and dt
-  rc = pack_state<real>(c, Un, 0.0);
+  int rc = pack_state<real>(c, Un, 0.0);
   if (rc) return rc;
   Scratch<real>* s = scr<real>(c);
   CK(launch_set_frozen<real>(&s->frozen_dt, dt, &s->frozen_alpha[0][0], alpha, c->stream));
@@ -1374,14 +1376,12 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
   rc = launch_ctl<real>(c, P_FROZEN + 0, stage_ctl(c, 0, true), c->stream);
   if (!rc) rc = launch_ctl<real>(c, P_FROZEN + 1, stage_ctl(c, 1, true), c->stream);
   if (rc) return rc;
-  real* nu[2] = {static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1])};
-  rc = copy_in<real>(c, nu[0], lam);
-  if (rc) return rc;
+  real* nu[2] = {nu0, nu1};
   const hydro_config& g = c->cfg;
   AdjParams<real> P{};
   P.mu = static_cast<real*>(c->adj_mu);
   P.hb = static_cast<real*>(c->adj_hb);
-  P.acc = static_cast<real*>(c->adj_acc);
+  P.acc = acc;
   P.fstride = c->fstride;
   P.nx = g.nx;
   P.ny = g.ny;
@@ -1419,9 +1419,32 @@ static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt,
     CK(launch_adjoint_stage<real>(P, c->nf, c->stream, &nl));
     c->launches += nl;
   }
-  rc = copy_out<real>(c, lam, static_cast<const real*>(c->adj_acc));
+  return HYDRO_OK;
+}
+
+// One adjoint step with an unpadded cotangent lam (in: of U^{n+1}; out: of U^n).
+template <typename real>
+static int adjoint_step_impl(hydro_ctx* c, const real* Un, real* lam, double dt, const double* alpha) {
+  int rc = ensure_adjoint_buffers(c);
+  if (rc) return rc;
+  real* acc = static_cast<real*>(c->adj_acc);
+  rc = copy_in<real>(c, static_cast<real*>(c->adj_nu[0]), lam);
+  if (!rc) rc = adjoint_step_bufs<real>(c, Un, static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1]), acc,
+                                        dt, alpha);
+  if (!rc) rc = copy_out<real>(c, lam, acc);
   if (rc) return rc;
   return c->defer_status ? HYDRO_OK : read_status<real>(c, nullptr, nullptr);
+}
+
+// A reverse sweep keeps its cotangent padded between steps: buffers adj_nu[0] and adj_acc alternate as the
+// step's input and result (c->adj_in names the one holding the current cotangent), adj_nu[1] is the third.
+template <typename real>
+static int sweep_step(hydro_ctx* c, const real* Un, double dt, const double* alpha) {
+  real* B[3] = {static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1]), static_cast<real*>(c->adj_acc)};
+  const int in = c->adj_in, out = 2 - in;
+  const int rc = adjoint_step_bufs<real>(c, Un, B[in], B[1], B[out], dt, alpha);
+  c->adj_in = out;
+  return rc;
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const void* U_n, void* lambda, double dt, const double alpha[6]) {
@@ -1530,12 +1553,12 @@ static int rv_reverse(hydro_ctx* c, real* lam, real* slots, int nslots, real* tm
   const size_t state = elems * sizeof(real);
   real* Ua = slots + elems * (size_t)level;
   const int n = b - a, s = nslots - 1 - level;
-  if (n == 1) return adjoint_step_impl<real>(c, Ua, lam, dtl[a], &al[6 * (size_t)a]);
+  if (n == 1) return sweep_step<real>(c, Ua, dtl[a], &al[6 * (size_t)a]);
   if (s == 0) {
     for (int k = b - 1; k >= a; --k) {
       CK(cudaMemcpyAsync(tmp, Ua, state, cudaMemcpyDeviceToDevice, c->stream));
       int rc = rv_advance<real>(c, tmp, a, k, dtl, al);
-      if (!rc) rc = adjoint_step_impl<real>(c, tmp, lam, dtl[k], &al[6 * (size_t)k]);
+      if (!rc) rc = sweep_step<real>(c, tmp, dtl[k], &al[6 * (size_t)k]);
       if (rc) return rc;
     }
     return HYDRO_OK;
@@ -1594,7 +1617,7 @@ static int sweep_segments(hydro_ctx* c, real* lam, real* seg, int nseg, int ever
       if (rc) return rc;
     }
     for (int st = s1 - 1; st >= s0; --st) {
-      rc = adjoint_step_impl<real>(c, seg + elems * (st - s0), lam, dtl[st], &al[6 * (size_t)st]);
+      rc = sweep_step<real>(c, seg + elems * (st - s0), dtl[st], &al[6 * (size_t)st]);
       if (rc) return rc;
     }
   }
@@ -1610,15 +1633,23 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
   if (rc) return rc;
   const size_t elems = (size_t)c->nf * c->cfg.nx * c->cfg.ny;
   const size_t state = elems * sizeof(real);
+  // the cotangent stays padded for the whole sweep (copied in here, out at the end)
+  if ((rc = ensure_adjoint_buffers(c))) return rc;
+  if ((rc = copy_in<real>(c, static_cast<real*>(c->adj_nu[0]), lam))) return rc;
+  c->adj_in = 0;
+  auto finish = [&](int r) -> int {
+    c->defer_status = false;
+    if (r) return r;
+    real* B[3] = {static_cast<real*>(c->adj_nu[0]), static_cast<real*>(c->adj_nu[1]), static_cast<real*>(c->adj_acc)};
+    if ((r = copy_out<real>(c, lam, B[c->adj_in]))) return r;
+    return read_status<real>(c, nullptr, nullptr);
+  };
   if (c->ck_mode == 1) {  // binomial schedule from U^0
     real* slots = static_cast<real*>(c->rv_slots);
     const int nslots = c->rv_snapshots + 1;
     CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
     c->defer_status = true;
-    rc = rv_reverse<real>(c, lam, slots, nslots, slots + elems * (size_t)nslots, 0, 0, N, elems, dtl, al);
-    c->defer_status = false;
-    if (rc) return rc;
-    return read_status<real>(c, nullptr, nullptr);
+    return finish(rv_reverse<real>(c, lam, slots, nslots, slots + elems * (size_t)nslots, 0, 0, N, elems, dtl, al));
   }
   if (c->seg_cap < (size_t)every) {
     cudaFree(c->seg);
@@ -1631,10 +1662,7 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
   const int nseg = (N + every - 1) / every;
   CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
   c->defer_status = true;
-  rc = sweep_segments<real>(c, lam, seg, nseg, every, N, elems, state, dtl, al);
-  c->defer_status = false;
-  if (rc) return rc;
-  return read_status<real>(c, nullptr, nullptr);
+  return finish(sweep_segments<real>(c, lam, seg, nseg, every, N, elems, state, dtl, al));
 }
 
 int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
