@@ -263,17 +263,21 @@ __global__ void __launch_bounds__(256) adj_point_kernel(AdjParams<real> P) {
 
 // ---------------------------------------------------------------------------- line adjoints
 
-constexpr int ATX = 32, ATY = 16, ARUN = 8;   // output points per tile, points per line item
-// threads per CTA: one line item each in both passes (NF x 64 items) for FP32, two CTAs per SM
-template <typename real, int NF>
-__host__ __device__ constexpr int adj_threads() { return sizeof(real) == 4 ? NF * 64 : 256; }
+constexpr int ATX = 32, ARUN = 8;   // output columns per tile, points per line item
+// output rows per tile TY: 16 (two CTAs of NF x 64 threads per SM in FP32), or 32 for FP32 grids with at
+// least one such tile per SM (one CTA of NF x 128 threads per SM, every warp in the same phase of the tile, a
+// box of 45 x 44 points for 32 x 32 outputs); FP64 16 rows, 256 threads
+// threads per CTA: one line item each in both passes (NF x 4 TY items) for FP32
+template <typename real, int NF, int TY>
+__host__ __device__ constexpr int adj_threads() { return sizeof(real) == 4 ? NF * 4 * TY : 256; }
 constexpr int AHX = 6;                        // box halo (hydro needs 5, level set 6)
-// box rows of odd length and output rows of ATX + 1: the 16 rows x 2 runs of an x-pass warp fall on 32
-// distinct banks (a warp's two runs are 16 columns apart), and so do the run outputs the lanes write
-constexpr int ABW = ATX + 2 * AHX + 1, ABH = ATY + 2 * AHX, AOS = ATX + 1;
+// box rows of odd length and output rows of ATX + 1: the rows of an x-pass warp (32 rows of one run, or 16
+// rows x 2 runs 16 columns apart) fall on 32 distinct banks, and so do the run outputs the lanes write
+constexpr int ABW = ATX + 2 * AHX + 1, AOS = ATX + 1;
 
-template <typename real, int NF>
+template <typename real, int NF, int TY>
 struct ATile {
+  static constexpr int ATY = TY, ABH = ATY + 2 * AHX;
   static constexpr int BOX = ABW * ABH;
   static constexpr int OFF_W = 0;                        // [NF][ABH][ABW] state
   static constexpr int OFF_P = OFF_W + NF * BOX;         // [3][ABH][ABW]  u, v, p
@@ -569,10 +573,11 @@ __device__ __forceinline__ void adj_phi_line(const real* __restrict__ ph, const 
   }
 }
 
-template <typename real, int NF>
-__global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2 : 1)
+template <typename real, int NF, int TY>
+__global__ void __launch_bounds__(adj_threads<real, NF, TY>(), (sizeof(real) == 4 && TY == 16) ? 2 : 1)
     adj_line_kernel(AdjParams<real> P, int tiles_x) {
-  using TL = ATile<real, NF>;
+  using TL = ATile<real, NF, TY>;
+  constexpr int ATY = TL::ATY;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
   real* sW = sm + TL::OFF_W;
@@ -583,7 +588,7 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
   real* sMB = sm + TL::OFF_MB;
   real* sMU = sm + TL::OFF_MU;
   const int tid = threadIdx.x;
-  constexpr int NT = adj_threads<real, NF>();
+  constexpr int NT = adj_threads<real, NF, TY>();
   const long long fs = P.fstride;
   // output points are padded-grid points: columns 1 .. nx+6 (cells -3 .. nx+2), rows 0 .. ny+5
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
@@ -638,7 +643,8 @@ __global__ void __launch_bounds__(adj_threads<real, NF>(), sizeof(real) == 4 ? 2
       int orow, ocol;  // first output point of the run, tile coordinates
       if (xp) {
         orow = rem % ATY;
-        ocol = (((rem / ATY) & 1) * 2 + (rem / (2 * ATY))) * ARUN;  // a warp's two runs 16 columns apart
+        // a warp holds 32 rows of one run (ATY 32) or 16 rows of two runs 16 columns apart (ATY 16)
+        ocol = (((rem / ATY) & 1) * 2 + (rem / (2 * ATY))) * ARUN;
       } else {
         ocol = rem % ATX;
         orow = (rem / ATX) * ARUN;

@@ -235,24 +235,44 @@ cudaError_t launch_reinit<HYDRO_REAL>(HYDRO_REAL* phi, int nx, int ny, int pitch
 }
 
 namespace {
+// the line adjoint over the tiles of the padded grid (columns 1 .. nx+6, rows 0 .. ny+5) in TY-row tiles
+template <int NF, int TY>
+cudaError_t adj_line(const AdjParams<HYDRO_REAL>& P, cudaStream_t s) {
+  using TL = ATile<HYDRO_REAL, NF, TY>;
+  const int tiles_x = (P.nx + 6 + ATX - 1) / ATX, tiles_y = (P.ny + 6 + TY - 1) / TY;
+  static const cudaError_t cfg = [] {
+    cudaError_t r = cudaFuncSetAttribute(adj_line_kernel<HYDRO_REAL, NF, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::BYTES);
+    if (r != cudaSuccess) (void)cudaGetLastError();
+    return r;
+  }();
+  if (cfg != cudaSuccess) return cfg;
+  adj_line_kernel<HYDRO_REAL, NF, TY><<<tiles_x * tiles_y, adj_threads<HYDRO_REAL, NF, TY>(), TL::BYTES, s>>>(P, tiles_x);
+  return cudaGetLastError();
+}
+
 template <int NF>
 cudaError_t adj_nf(const AdjParams<HYDRO_REAL>& P, cudaStream_t s, int* launches) {
   dim3 pg((P.nx + 255) / 256, P.ny);
   adj_point_kernel<HYDRO_REAL, NF><<<pg, 256, 0, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // tiles over the padded grid: columns 1 .. nx+6, rows 0 .. ny+5
-  const int tiles_x = (P.nx + 6 + ATX - 1) / ATX, tiles_y = (P.ny + 6 + ATY - 1) / ATY;
-  static const cudaError_t cfg = [] {
-    cudaError_t r = cudaFuncSetAttribute(adj_line_kernel<HYDRO_REAL, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ATile<HYDRO_REAL, NF>::BYTES);
-    if (r != cudaSuccess) (void)cudaGetLastError();
-    return r;
+#if HYDRO_REAL_IS_FLOAT
+  // 32-row tiles (one CTA per SM) where the grid has at least one per SM: 45.1 -> 43.8 ms per 8192^2
+  // adjoint step; smaller grids keep two CTAs of 16-row tiles per SM
+  static const int sms = [] {
+    int d = 0, n = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 1 << 30;
+    }
+    return n;
   }();
-  if (cfg != cudaSuccess) return cfg;
-  adj_line_kernel<HYDRO_REAL, NF><<<tiles_x * tiles_y, adj_threads<HYDRO_REAL, NF>(), ATile<HYDRO_REAL, NF>::BYTES, s>>>(
-      P, tiles_x);
-  e = cudaGetLastError();
+  const long long tiles32 = (long long)((P.nx + 6 + ATX - 1) / ATX) * ((P.ny + 6 + 31) / 32);
+  e = tiles32 >= sms ? adj_line<NF, 32>(P, s) : adj_line<NF, 16>(P, s);
+#else
+  e = adj_line<NF, 16>(P, s);
+#endif
   if (e != cudaSuccess) return e;
   adj_blend_kernel<HYDRO_REAL, NF><<<pg, 256, 0, s>>>(P);
   if (launches) *launches += 3;
