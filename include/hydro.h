@@ -266,6 +266,11 @@ int hydro_batch_step(hydro_ctx* const* members, void* const* U, int nmembers, in
  * variant 2 (60 x 30 cells, 640 threads) for component-wise FP32 grids of at least one such tile per SM,
  * else 1. */
 int hydro_tile_variants(hydro_ctx* ctx, int* n, int* current);
+/* Tile rows of the discrete adjoint's line kernel for this context: 16 (two CTAs of 16 x 32 output points
+ * per SM), 32 (FP32 only: one CTA of 32 x 32 per SM), or 0 (the default: 32 in FP32 where the padded grid
+ * holds at least one 32 x 32 tile per SM, else 16). Every choice gives the same bits. HYDRO_EINVAL for
+ * another value. */
+int hydro_set_adjoint_tile_rows(hydro_ctx* ctx, int rows);
 int hydro_set_tile_variant(hydro_ctx* ctx, int variant);
 /* Describe a variant: tile width and height in cells, threads per CTA, shared memory bytes. */
 int hydro_tile_info(hydro_ctx* ctx, int variant, int* tile_x, int* tile_y, int* threads, int* smem_bytes);

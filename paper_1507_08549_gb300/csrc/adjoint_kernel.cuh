@@ -147,6 +147,7 @@ struct AdjParams {
   // the same in the working precision, formed on the host (no FP64 arithmetic in the FP32 kernels)
   real rdx_r, rdy_r, dx_r, x0_r, dt_r, a_r, b_r;
   int acc_mode;      // 0: acc = a nu ; 1: acc += a nu ; 2: acc += out (final stage), write out too
+  int tile_rows;     // line-adjoint tile rows: 16, 32 (FP32 only), or 0 for the size rule
 };
 
 // ---------------------------------------------------------------------------- point terms

@@ -99,6 +99,7 @@ struct hydro_ctx {
   void* adj_mu = nullptr;
   void* adj_hb = nullptr;
   int adj_in = 0;  // during a reverse sweep: 0 (adj_nu[0]) or 2 (adj_acc), the buffer holding the cotangent
+  int adj_rows = 0;  // line-adjoint tile rows (hydro_set_adjoint_tile_rows), 0 for the size rule
   void* adj_acc = nullptr;
   void* ckpt = nullptr;
   size_t ckpt_cap = 0;
@@ -971,6 +972,15 @@ int hydro_set_tile_variant(hydro_ctx* c, int v) {
   return upload(c);
 }
 
+int hydro_set_adjoint_tile_rows(hydro_ctx* c, int rows) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (rows != 0 && rows != 16 && !(rows == 32 && c->cfg.dtype == HYDRO_F32))
+    return fail(c, HYDRO_EINVAL, "adjoint tile rows: 0 (by grid size), 16, or 32 (FP32)");
+  c->adj_rows = rows;
+  return HYDRO_OK;
+}
+
 int hydro_tile_info(hydro_ctx* c, int v, int* tx, int* ty, int* threads, int* smem) {
   if (!c || v < 0 || v >= NUM_VARIANTS) return HYDRO_EINVAL;
   if (tx) *tx = TILE_X;
@@ -1401,6 +1411,7 @@ static int adjoint_step_bufs(hydro_ctx* c, const real* Un, real* nu0, real* nu1,
   P.dx_r = static_cast<real>(P.dx);
   P.x0_r = static_cast<real>(P.x0);
   P.dt_r = static_cast<real>(dt);
+  P.tile_rows = c->adj_rows;
   // reverse stages 2, 1, 0
   const int order[3] = {2, 1, 0};
   for (int q = 0; q < 3; ++q) {

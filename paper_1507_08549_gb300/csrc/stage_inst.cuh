@@ -269,7 +269,8 @@ cudaError_t adj_nf(const AdjParams<HYDRO_REAL>& P, cudaStream_t s, int* launches
     return n;
   }();
   const long long tiles32 = (long long)((P.nx + 6 + ATX - 1) / ATX) * ((P.ny + 6 + 31) / 32);
-  e = tiles32 >= sms ? adj_line<NF, 32>(P, s) : adj_line<NF, 16>(P, s);
+  const bool rows32 = P.tile_rows == 32 || (P.tile_rows == 0 && tiles32 >= sms);
+  e = rows32 ? adj_line<NF, 32>(P, s) : adj_line<NF, 16>(P, s);
 #else
   e = adj_line<NF, 16>(P, s);
 #endif

@@ -47,7 +47,7 @@ EXPORTS = [
     "hydro_rhs", "conserved_totals", "hydro_last_totals", "hydro_record", "hydro_get_log", "hydro_step_frozen",
     "hydro_adjoint_step", "hydro_forward_checkpointed", "hydro_adjoint_sweep", "hydro_forward_revolve",
     "hydro_batch_step",
-    "hydro_tile_variants", "hydro_set_tile_variant", "hydro_tile_info", "hydro_autotune", "hydro_batch_autotune",
+    "hydro_tile_variants", "hydro_set_tile_variant", "hydro_set_adjoint_tile_rows", "hydro_tile_info", "hydro_autotune", "hydro_batch_autotune",
     "hydro_profile",
     "hydro_stage_timing", "hydro_launch_count", "conserved_totals_noalloc", "hydro_reinit",
     "hydro_poisson", "hydro_exact_sum", "hydro_wait_selftest", "hydro_fma_probe",
@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
                                  ctypes.c_int),
             "hydro_tile_variants": ([ctxp, ip, ip], ctypes.c_int),
             "hydro_set_tile_variant": ([ctxp, ctypes.c_int], ctypes.c_int),
+            "hydro_set_adjoint_tile_rows": ([ctxp, ctypes.c_int], ctypes.c_int),
             "hydro_tile_info": ([ctxp, ctypes.c_int, ip, ip, ip, ip], ctypes.c_int),
             "hydro_autotune": ([ctxp, vp, ctypes.c_int, dp], ctypes.c_int),
             "hydro_batch_autotune": ([ctypes.POINTER(ctxp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, dp, ip],
@@ -346,6 +347,10 @@ class Hydro:
 
     def set_tile_variant(self, v: int):
         self._check(self.lib.hydro_set_tile_variant(self.ctx, int(v)), "hydro_set_tile_variant")
+
+    def set_adjoint_tile_rows(self, rows: int):
+        """Line-adjoint tile rows: 16, 32 (FP32), or 0 for the default size rule (hydro_set_adjoint_tile_rows)."""
+        self._check(self.lib.hydro_set_adjoint_tile_rows(self.ctx, int(rows)), "hydro_set_adjoint_tile_rows")
 
     def tile_info(self, v: int):
         a = [ctypes.c_int() for _ in range(4)]
