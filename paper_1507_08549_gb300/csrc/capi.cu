@@ -1559,7 +1559,7 @@ static int rv_advance(hydro_ctx* c, real* U, int from, int to, const std::vector
 // Reverse steps [a, b): slot `level` holds the state at a, slots level+1 .. nslots-1 are free, tmp is the
 // recomputation buffer.
 template <typename real>
-static int rv_reverse(hydro_ctx* c, real* lam, real* slots, int nslots, real* tmp, int level, int a, int b,
+static int rv_reverse(hydro_ctx* c, real* slots, int nslots, real* tmp, int level, int a, int b,
                       size_t elems, const std::vector<double>& dtl, const std::vector<double>& al) {
   const size_t state = elems * sizeof(real);
   real* Ua = slots + elems * (size_t)level;
@@ -1578,8 +1578,8 @@ static int rv_reverse(hydro_ctx* c, real* lam, real* slots, int nslots, real* tm
   real* Um = slots + elems * (size_t)(level + 1);
   CK(cudaMemcpyAsync(Um, Ua, state, cudaMemcpyDeviceToDevice, c->stream));
   int rc = rv_advance<real>(c, Um, a, m, dtl, al);
-  if (!rc) rc = rv_reverse<real>(c, lam, slots, nslots, tmp, level + 1, m, b, elems, dtl, al);
-  if (!rc) rc = rv_reverse<real>(c, lam, slots, nslots, tmp, level, a, m, elems, dtl, al);
+  if (!rc) rc = rv_reverse<real>(c, slots, nslots, tmp, level + 1, m, b, elems, dtl, al);
+  if (!rc) rc = rv_reverse<real>(c, slots, nslots, tmp, level, a, m, elems, dtl, al);
   return rc;
 }
 
@@ -1613,7 +1613,7 @@ int hydro_forward_revolve(hydro_ctx* c, void* U, int nsteps, int snapshots, long
 }
 
 template <typename real>
-static int sweep_segments(hydro_ctx* c, real* lam, real* seg, int nseg, int every, int N, size_t elems, size_t state,
+static int sweep_segments(hydro_ctx* c, real* seg, int nseg, int every, int N, size_t elems, size_t state,
                           const std::vector<double>& dtl, const std::vector<double>& al) {
   int rc = HYDRO_OK;
   for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1660,7 +1660,7 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
     const int nslots = c->rv_snapshots + 1;
     CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
     c->defer_status = true;
-    return finish(rv_reverse<real>(c, lam, slots, nslots, slots + elems * (size_t)nslots, 0, 0, N, elems, dtl, al));
+    return finish(rv_reverse<real>(c, slots, nslots, slots + elems * (size_t)nslots, 0, 0, N, elems, dtl, al));
   }
   if (c->seg_cap < (size_t)every) {
     cudaFree(c->seg);
@@ -1673,7 +1673,7 @@ static int sweep_impl(hydro_ctx* c, real* lam) {
   const int nseg = (N + every - 1) / every;
   CK(cudaMemsetAsync(&scr<real>(c)->err, 0, sizeof(int), c->stream));
   c->defer_status = true;
-  return finish(sweep_segments<real>(c, lam, seg, nseg, every, N, elems, state, dtl, al));
+  return finish(sweep_segments<real>(c, seg, nseg, every, N, elems, state, dtl, al));
 }
 
 int hydro_adjoint_sweep(hydro_ctx* c, void* lambda) {
