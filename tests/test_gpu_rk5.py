@@ -37,8 +37,10 @@ def rel_l1(a, b, gamma=1.4):
     return max(errs)
 
 
-def _run(prob, nsteps, dtype):
+def _run(prob, nsteps, dtype, variant=None):
     h = _hydro().Hydro(prob, dtype=dtype)
+    if variant is not None:
+        h.set_tile_variant(variant)
     U = h.state(prob.U0)
     t, dtl = h.step(U, nsteps)
     out = U.double().cpu().numpy()
@@ -68,9 +70,12 @@ def test_five_stage_rz_gravity_level_set_matches_oracle(record_property):
     ref, _, _ = oracle.step(prob, prob.U0, 30)
     got, _ = _run(prob, 30, "f64")
     assert rel_linf(got, ref) <= 1e-12
-    got32, _ = _run(prob, 30, "f32")
+    got32, _ = _run(prob, 30, "f32", variant=1)
     record_property("err:rk5_fp32_rel_l1_rt", rel_l1(got32, ref, prob.gamma))
     assert rel_l1(got32, ref, prob.gamma) <= 1e-4
+    # the 60 x 30 variant (pipelined tile loop, the further stage states prefetched into L2): the same bits
+    got32v2, _ = _run(prob, 30, "f32", variant=2)
+    assert np.array_equal(got32v2, got32)
 
 
 def test_five_stage_shock_tube_and_host_entry():
