@@ -398,16 +398,19 @@ def test_frozen_replay_reproduces_the_run_and_host_entry():
     h.close()
 
 
-@pytest.mark.parametrize("dt,n,nsteps,scheme", [("f64", 64, 1, 0), ("f32", 61, 5, 0), ("f32", 64, 3, 1),
-                                                 ("f64", 37, 4, 0)])
-def test_pinned_host_entry_matches_device_steps(dt, n, nsteps, scheme):
+@pytest.mark.parametrize("dt,n,nsteps,scheme,variant", [("f64", 64, 1, 0, None), ("f32", 61, 5, 0, None),
+                                                         ("f32", 64, 3, 1, None), ("f64", 37, 4, 0, None),
+                                                         ("f32", 128, 3, 0, 2)])
+def test_pinned_host_entry_matches_device_steps(dt, n, nsteps, scheme, variant):
     """Pinned host buffers are read by the pack kernel and written by the last stage directly over the
-    host link: same bits, time and
-    totals as the device entry point."""
+    host link (the last stage in row bands, each band's copy overlapping the next band): same bits, time
+    and totals as the device entry point, also in the pipelined 60 x 30 variant."""
     import torch
     hydro = _hydro()
     prob = wl.kelvin_helmholtz(n).with_(scheme=scheme)
     h = hydro.Hydro(prob, dtype=dt)
+    if variant is not None:
+        h.set_tile_variant(variant)
     U = h.state(prob.U0)
     t, dl = h.step(U, nsteps)
     tot = h.last_totals()
